@@ -1,0 +1,161 @@
+"""Plain CPU oracle for the swept-rule hot path (TEST INFRASTRUCTURE ONLY).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` /
+``--impl reference`` legs of ``bench.py`` may import this package. The product
+path (``paper_1602_07558_gb300``) never imports it, and this package imports
+nothing from the product path.
+
+Two parts:
+
+* ``swept2d_oracle.c`` -- the plain step-by-step definition (FP64, OpenMP over
+  rows), compiled here with gcc into ``_build/liboracle.so`` and called through
+  ctypes. This is what every GPU parity test compares against: the swept rule
+  reaches exactly the values of plain explicit time marching (Section 4, first
+  paragraph; abstract).
+* ``swept_sim.py`` -- a slow pure-Python walk through the paper's components
+  (Algorithms 1, 2, 3, 5 glued by Algorithm 4), used only to pin the geometric
+  claims of Section 3 (panel sizes, exchange counts, exact partition) on tiny
+  grids. It is never compared with the GPU directly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "swept2d_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, -fopenmp, -ffp-contract=off)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    stale = (not os.path.exists(_LIB_PATH)
+             or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC))
+    if force or stale:
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+               "-ffp-contract=off", "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        d, i, ll, p = ctypes.c_double, ctypes.c_int, ctypes.c_longlong, ctypes.c_void_p
+        lib.oracle_num_threads.restype = i
+        lib.oracle_mix64.argtypes = [ctypes.c_uint64]
+        lib.oracle_mix64.restype = ctypes.c_uint64
+        lib.oracle_heat.argtypes = [i, i, d, ll, p]
+        lib.oracle_increment.argtypes = [i, i, ll, p]
+        lib.oracle_hash.argtypes = [i, i, ll, ll, p]
+        lib.oracle_leveltag.argtypes = [i, i, ll, p]
+        lib.oracle_wide2.argtypes = [i, i, ll, p]
+        lib.oracle_euler_wavespeed.argtypes = [i, i, d, p]
+        lib.oracle_euler_wavespeed.restype = d
+        lib.oracle_euler_setup.argtypes = [i, i, d, d, d, d, p,
+                                           ctypes.POINTER(d), ctypes.POINTER(d)]
+        lib.oracle_euler_rk2.argtypes = [i, i, d, d, d, d, d, d, ll, p]
+        for name in ("oracle_heat", "oracle_increment", "oracle_hash", "oracle_leveltag",
+                     "oracle_wide2", "oracle_euler_setup", "oracle_euler_rk2"):
+            getattr(lib, name).restype = i
+        _lib = lib
+        return lib
+
+
+def num_threads() -> int:
+    return int(_load().oracle_num_threads())
+
+
+def _grid(u, dtype):
+    a = np.ascontiguousarray(np.array(u, dtype=dtype, copy=True))
+    if a.ndim != 2:
+        raise ValueError("expected a (ny, nx) array")
+    return a
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise RuntimeError(f"oracle {what} failed with code {rc}")
+
+
+def heat(u0, r: float, nsteps: int) -> np.ndarray:
+    """Forward-Euler 5-point heat equation, ``nsteps`` steps; returns a new array."""
+    u = _grid(u0, np.float64)
+    ny, nx = u.shape
+    _check(_load().oracle_heat(nx, ny, float(r), int(nsteps), u.ctypes.data), "heat")
+    return u
+
+
+def increment(u0, nsteps: int) -> np.ndarray:
+    u = _grid(u0, np.float64)
+    ny, nx = u.shape
+    _check(_load().oracle_increment(nx, ny, int(nsteps), u.ctypes.data), "increment")
+    return u
+
+
+def mix64(z: int) -> int:
+    """The SplitMix64 output function used by the hash update."""
+    return int(_load().oracle_mix64(ctypes.c_uint64(int(z) & 0xFFFFFFFFFFFFFFFF)))
+
+
+def hash_op(u0, nsub: int, substep0: int = 0) -> np.ndarray:
+    """``nsub`` sub-steps of the 9-neighbour hash update on uint64 words."""
+    a = np.ascontiguousarray(np.asarray(u0))
+    if a.dtype.itemsize != 8:
+        raise ValueError("hash words are 64-bit")
+    u = _grid(a.view(np.uint64), np.uint64)
+    ny, nx = u.shape
+    _check(_load().oracle_hash(nx, ny, int(substep0), int(nsub), u.ctypes.data), "hash")
+    return u
+
+
+def leveltag(u0, nsub: int) -> np.ndarray:
+    u = _grid(u0, np.float64)
+    ny, nx = u.shape
+    _check(_load().oracle_leveltag(nx, ny, int(nsub), u.ctypes.data), "leveltag")
+    return u
+
+
+def wide2(u0, nsteps: int) -> np.ndarray:
+    """Eq. (complex_step) evaluated directly (radius 2) modulo 2^64."""
+    u = _grid(u0, np.uint64)
+    ny, nx = u.shape
+    _check(_load().oracle_wide2(nx, ny, int(nsteps), u.ctypes.data), "wide2")
+    return u
+
+
+def euler_setup(U0, gamma: float, cfl: float, lx: float = 1.0, ly: float = 1.0):
+    """Returns (a, dt): max wave speed of ``U0`` (4, ny, nx) and the fixed CFL step."""
+    U = np.ascontiguousarray(np.asarray(U0, dtype=np.float64))
+    _, ny, nx = U.shape
+    a, dt = ctypes.c_double(), ctypes.c_double()
+    _check(_load().oracle_euler_setup(nx, ny, float(gamma), float(cfl), float(lx), float(ly),
+                                      U.ctypes.data, ctypes.byref(a), ctypes.byref(dt)),
+           "euler_setup")
+    return a.value, dt.value
+
+
+def euler_rk2(U0, gamma: float, dt: float, kappa: float, a: float, nsteps: int,
+              lx: float = 1.0, ly: float = 1.0) -> np.ndarray:
+    """``nsteps`` midpoint-RK2 steps of the Euler system; ``U0`` is (4, ny, nx)."""
+    U = np.ascontiguousarray(np.array(U0, dtype=np.float64, copy=True))
+    if U.ndim != 3 or U.shape[0] != 4:
+        raise ValueError("expected a (4, ny, nx) array")
+    _, ny, nx = U.shape
+    _check(_load().oracle_euler_rk2(nx, ny, float(gamma), float(dt), float(lx), float(ly),
+                                    float(kappa), float(a), int(nsteps), U.ctypes.data),
+           "euler_rk2")
+    return U

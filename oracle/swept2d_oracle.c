@@ -1,0 +1,314 @@
+/*
+ * Plain CPU oracle for explicit time advancing on a doubly periodic 2D grid.
+ *
+ * TEST INFRASTRUCTURE ONLY. Only the tests, __graft_entry__.smoke() and the
+ * cpu_baseline / reference leg of bench.py may load or call this library. The
+ * product path (the CUDA library under paper_1602_07558_gb300/) never links,
+ * imports or calls it, and this file includes no header of that library.
+ *
+ * What it computes. The swept rule of space-time decomposition (Section 3,
+ * Algorithms 1-5) reaches exactly the values of plain step-by-step explicit time
+ * marching: every (point, level) is computed once, from its 9-point neighbourhood
+ * at the level below (Section 4, first paragraph; abstract: "no redundant
+ * computation"). So the oracle is that plain definition, written out:
+ *
+ *     for every sub-step:  v(i,j) = St(u on the 3x3 neighbourhood of (i,j))  for all (i,j)
+ *                          u <- v
+ *
+ * with indices taken modulo nx, ny (doubly periodic grid, Section 2 item 1).
+ * No blocking, no fusion, no reordering: one full sweep per sub-step, rows in
+ * parallel with OpenMP (each output point is written once from the previous
+ * sweep, so the result does not depend on the thread count).
+ *
+ * Conventions: row-major planes, x = i fastest, j = row; "north" = j-1, "south"
+ * = j+1, "west" = i-1, "east" = i+1. Floating point is IEEE binary64, round to
+ * nearest even; this file is compiled with -ffp-contract=off so that only the
+ * fma() calls written below are fused.
+ *
+ * Point updates (the paper's St_k / timestep(i, p), Section 5):
+ *   heat      forward-Euler 5-point heat update, one sub-step per step
+ *   increment the paper's worked example u <- u + 1 (Section 3.1)
+ *   hash      order-sensitive 64-bit mix of the 9 neighbour words and the
+ *             sub-step index (a test update that detects any wrong dependency)
+ *   leveltag  u <- u + 1 if all 9 neighbours hold the same level, else NaN
+ *   wide2     the radius-2 scheme of eq. (complex_step), evaluated directly on
+ *             64-bit integers modulo 2^64 (its 2-sub-step form, eqs. (substep1)-
+ *             (substep2), is what the swept path runs)
+ *   euler     2D compressible Euler, central flux plus scalar dissipation,
+ *             midpoint (2-stage) Runge-Kutta, dt fixed from the initial state
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+static int wrapi(long long i, int n) {
+    long long r = i % n;
+    return (int)(r < 0 ? r + n : r);
+}
+
+int oracle_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* ------------------------------------------------------------------------ heat
+ * u_t = laplace(u), forward Euler with diffusion number r on the 5-point stencil:
+ *     s = (u_E + u_S) + (u_W + u_N)
+ *     d = s - 4 u
+ *     u' = u + r d     (one rounding: fma)
+ * The 9-point neighbourhood of Section 2 contains the 5 points used here. The
+ * paper fixes no evaluation order; this one pairs east with south and west with
+ * north, each pair rounded once. */
+int oracle_heat(int nx, int ny, double r, long long nsteps, double *u) {
+    if (nx < 1 || ny < 1 || nsteps < 0 || !u) return -1;
+    size_t npts = (size_t)nx * ny;
+    double *v = (double *)malloc(npts * sizeof(double));
+    if (!v) return -3;
+    double *a = u, *b = v;
+    for (long long s = 0; s < nsteps; ++s) {
+#pragma omp parallel for schedule(static)
+        for (int j = 0; j < ny; ++j) {
+            int jn = wrapi(j - 1, ny), js = wrapi(j + 1, ny);
+            for (int i = 0; i < nx; ++i) {
+                int iw = wrapi(i - 1, nx), ie = wrapi(i + 1, nx);
+                double c = a[(size_t)j * nx + i];
+                double sum = (a[(size_t)j * nx + ie] + a[(size_t)js * nx + i]) +
+                             (a[(size_t)j * nx + iw] + a[(size_t)jn * nx + i]);
+                double d = sum - 4.0 * c;
+                b[(size_t)j * nx + i] = fma(r, d, c);
+            }
+        }
+        double *t = a; a = b; b = t;
+    }
+    if (a != u) memcpy(u, a, npts * sizeof(double));
+    free(v);
+    return 0;
+}
+
+/* ------------------------------------------------------------------- increment
+ * Section 3.1 worked example: u^{k+1} = u^k + 1. */
+int oracle_increment(int nx, int ny, long long nsteps, double *u) {
+    if (nx < 1 || ny < 1 || nsteps < 0 || !u) return -1;
+    size_t npts = (size_t)nx * ny;
+    for (long long s = 0; s < nsteps; ++s)
+        for (size_t p = 0; p < npts; ++p) u[p] = u[p] + 1.0;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ hash
+ * SplitMix64 output function (Steele, Lea & Flood, OOPSLA 2014; as published
+ * with Vigna's xorshift generators): z ^= z>>30, z *= 0xbf58476d1ce4e5b9,
+ * z ^= z>>27, z *= 0x94d049bb133111eb, z ^= z>>31. */
+static uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+
+uint64_t oracle_mix64(uint64_t z) { return mix64(z); }
+
+/* One sub-step with global index g: h = mix(g + golden); then for the 9
+ * neighbours in row order (north row west..east, own row, south row):
+ * h = mix(h + w). The new word is h. */
+int oracle_hash(int nx, int ny, long long substep0, long long nsub, uint64_t *u) {
+    if (nx < 1 || ny < 1 || nsub < 0 || !u) return -1;
+    size_t npts = (size_t)nx * ny;
+    uint64_t *v = (uint64_t *)malloc(npts * sizeof(uint64_t));
+    if (!v) return -3;
+    uint64_t *a = u, *b = v;
+    for (long long s = 0; s < nsub; ++s) {
+        uint64_t g = (uint64_t)(substep0 + s);
+#pragma omp parallel for schedule(static)
+        for (int j = 0; j < ny; ++j) {
+            for (int i = 0; i < nx; ++i) {
+                uint64_t h = mix64(g + 0x9e3779b97f4a7c15ULL);
+                for (int dj = -1; dj <= 1; ++dj)
+                    for (int di = -1; di <= 1; ++di)
+                        h = mix64(h + a[(size_t)wrapi(j + dj, ny) * nx + wrapi(i + di, nx)]);
+                b[(size_t)j * nx + i] = h;
+            }
+        }
+        uint64_t *t = a; a = b; b = t;
+    }
+    if (a != u) memcpy(u, a, npts * sizeof(uint64_t));
+    free(v);
+    return 0;
+}
+
+/* -------------------------------------------------------------------- leveltag
+ * Each point holds the level it was computed at. A point at level k+1 may only
+ * be computed from 9 neighbours that are all at level k (Section 4, first
+ * paragraph): u' = u + 1 when all 9 equal the centre, NaN otherwise. */
+int oracle_leveltag(int nx, int ny, long long nsub, double *u) {
+    if (nx < 1 || ny < 1 || nsub < 0 || !u) return -1;
+    size_t npts = (size_t)nx * ny;
+    double *v = (double *)malloc(npts * sizeof(double));
+    if (!v) return -3;
+    double *a = u, *b = v;
+    for (long long s = 0; s < nsub; ++s) {
+#pragma omp parallel for schedule(static)
+        for (int j = 0; j < ny; ++j) {
+            for (int i = 0; i < nx; ++i) {
+                double c = a[(size_t)j * nx + i];
+                int same = 1;
+                for (int dj = -1; dj <= 1; ++dj)
+                    for (int di = -1; di <= 1; ++di)
+                        if (!(a[(size_t)wrapi(j + dj, ny) * nx + wrapi(i + di, nx)] == c)) same = 0;
+                b[(size_t)j * nx + i] = same ? c + 1.0 : NAN;
+            }
+        }
+        double *t = a; a = b; b = t;
+    }
+    if (a != u) memcpy(u, a, npts * sizeof(double));
+    free(v);
+    return 0;
+}
+
+/* ----------------------------------------------------------------------- wide2
+ * Eq. (complex_step), evaluated directly with its radius-2 neighbours:
+ *     u^{n+1}_{i,j} = u_{i-2,j} + u_{i+2,j} + u_{i,j-2} + u_{i,j+2} - 4 u_{i,j}
+ * in unsigned 64-bit arithmetic (modulo 2^64, so that long runs stay exact). */
+int oracle_wide2(int nx, int ny, long long nsteps, uint64_t *u) {
+    if (nx < 1 || ny < 1 || nsteps < 0 || !u) return -1;
+    size_t npts = (size_t)nx * ny;
+    uint64_t *v = (uint64_t *)malloc(npts * sizeof(uint64_t));
+    if (!v) return -3;
+    uint64_t *a = u, *b = v;
+    for (long long s = 0; s < nsteps; ++s) {
+#pragma omp parallel for schedule(static)
+        for (int j = 0; j < ny; ++j) {
+            for (int i = 0; i < nx; ++i) {
+                uint64_t c = a[(size_t)j * nx + i];
+                uint64_t w2 = a[(size_t)j * nx + wrapi(i - 2, nx)];
+                uint64_t e2 = a[(size_t)j * nx + wrapi(i + 2, nx)];
+                uint64_t n2 = a[(size_t)wrapi(j - 2, ny) * nx + i];
+                uint64_t s2 = a[(size_t)wrapi(j + 2, ny) * nx + i];
+                b[(size_t)j * nx + i] = w2 + e2 + n2 + s2 - 4u * c;
+            }
+        }
+        uint64_t *t = a; a = b; b = t;
+    }
+    if (a != u) memcpy(u, a, npts * sizeof(uint64_t));
+    free(v);
+    return 0;
+}
+
+/* ----------------------------------------------------------------------- euler
+ * Conserved W = (rho, m = rho u, q = rho v, E), ideal gas:
+ *     iv = 1/rho, u = m iv, v = q iv, ke = 0.5 (m u + q v), p = (gamma-1)(E - ke)
+ *     F(W) = (m, m u + p, q u, (E + p) u)        x-flux
+ *     G(W) = (q, m v, q v + p, (E + p) v)        y-flux
+ * Semi-discrete operator at a point, with the 4 neighbours W_W, W_E, W_N, W_S:
+ *     L_k = (kax ((W_E + W_W) - 2 W) + kay ((W_S + W_N) - 2 W))
+ *           - (cx (F_E - F_W) + cy (G_S - G_N))
+ * Rounding: every "a b + c" written above with a product first is one fused
+ * multiply-add (fma(a, b, c)): m u + q v, m u + p, q v + p, kax lx + kay ly,
+ * cx dF + cy dG, and base + tau L; all other operations round separately.
+ *     cx = 0.5/dx, cy = 0.5/dy, kax = (kappa a)/dx, kay = (kappa a)/dy
+ * (central flux difference plus scalar dissipation with a fixed global wave
+ * speed a). Midpoint Runge-Kutta: U* = U + (0.5 dt) L(U); U <- U + dt L(U*).
+ * Each sub-step is a radius-1 stencil operation with a vector point state
+ * (Section 2, item 2). */
+typedef struct { double cx, cy, kax, kay, gm1; } euler_consts;
+
+static void euler_flux(const double *W, size_t p, size_t np, double gm1, double *F, double *G) {
+    double r = W[p], m = W[np + p], q = W[2 * np + p], E = W[3 * np + p];
+    double iv = 1.0 / r;
+    double u = m * iv, v = q * iv;
+    double ke = 0.5 * fma(m, u, q * v);
+    double pr = gm1 * (E - ke);
+    double Ep = E + pr;
+    F[0] = m; F[1] = fma(m, u, pr); F[2] = q * u; F[3] = Ep * u;
+    G[0] = q; G[1] = m * v; G[2] = fma(q, v, pr); G[3] = Ep * v;
+}
+
+/* out = base + tau * L(W) at every point. */
+static void euler_stage(int nx, int ny, const euler_consts *k, double tau,
+                        const double *W, const double *base, double *out) {
+    size_t np = (size_t)nx * ny;
+#pragma omp parallel for schedule(static)
+    for (int j = 0; j < ny; ++j) {
+        int jn = wrapi(j - 1, ny), js = wrapi(j + 1, ny);
+        for (int i = 0; i < nx; ++i) {
+            int iw = wrapi(i - 1, nx), ie = wrapi(i + 1, nx);
+            size_t pc = (size_t)j * nx + i, pw = (size_t)j * nx + iw, pe = (size_t)j * nx + ie;
+            size_t pn = (size_t)jn * nx + i, ps = (size_t)js * nx + i;
+            double FW[4], GW[4], FE[4], GE[4], FN[4], GN[4], FS[4], GS[4];
+            euler_flux(W, pw, np, k->gm1, FW, GW);
+            euler_flux(W, pe, np, k->gm1, FE, GE);
+            euler_flux(W, pn, np, k->gm1, FN, GN);
+            euler_flux(W, ps, np, k->gm1, FS, GS);
+            for (int c = 0; c < 4; ++c) {
+                double wc = W[c * np + pc];
+                double lx = (W[c * np + pe] + W[c * np + pw]) - 2.0 * wc;
+                double ly = (W[c * np + ps] + W[c * np + pn]) - 2.0 * wc;
+                double diss = fma(k->kax, lx, k->kay * ly);
+                double flux = fma(k->cx, FE[c] - FW[c], k->cy * (GS[c] - GN[c]));
+                double L = diss - flux;
+                out[c * np + pc] = fma(tau, L, base[c * np + pc]);
+            }
+        }
+    }
+}
+
+/* Maximum wave speed a = max over points of max(|u| + c, |v| + c),
+ * c = sqrt(gamma p / rho). */
+double oracle_euler_wavespeed(int nx, int ny, double gamma, const double *U) {
+    size_t np = (size_t)nx * ny;
+    double gm1 = gamma - 1.0, amax = 0.0;
+    for (size_t p = 0; p < np; ++p) {
+        double r = U[p], m = U[np + p], q = U[2 * np + p], E = U[3 * np + p];
+        double iv = 1.0 / r;
+        double u = m * iv, v = q * iv;
+        double ke = 0.5 * fma(m, u, q * v);
+        double pr = gm1 * (E - ke);
+        double c = sqrt((gamma * pr) * iv);
+        double su = fabs(u) + c, sv = fabs(v) + c;
+        double s = su > sv ? su : sv;
+        if (s > amax) amax = s;
+    }
+    return amax;
+}
+
+/* Fixed time step from the CFL number (dt = cfl min(dx,dy) / a), dx = lx/nx,
+ * dy = ly/ny; writes a and dt. */
+int oracle_euler_setup(int nx, int ny, double gamma, double cfl, double lx, double ly,
+                       const double *U, double *a_out, double *dt_out) {
+    if (nx < 1 || ny < 1 || !U) return -1;
+    double dx = lx / nx, dy = ly / ny;
+    double a = oracle_euler_wavespeed(nx, ny, gamma, U);
+    double h = dx < dy ? dx : dy;
+    *a_out = a;
+    *dt_out = (cfl * h) / a;
+    return 0;
+}
+
+/* nsteps of midpoint RK2 on U (4 planes), in place. */
+int oracle_euler_rk2(int nx, int ny, double gamma, double dt, double lx, double ly,
+                     double kappa, double a, long long nsteps, double *U) {
+    if (nx < 1 || ny < 1 || nsteps < 0 || !U) return -1;
+    size_t np = (size_t)nx * ny;
+    double dx = lx / nx, dy = ly / ny;
+    euler_consts k;
+    k.cx = 0.5 / dx; k.cy = 0.5 / dy;
+    k.kax = (kappa * a) / dx; k.kay = (kappa * a) / dy;
+    k.gm1 = gamma - 1.0;
+    double tau0 = 0.5 * dt, tau1 = dt;
+    double *Us = (double *)malloc(4 * np * sizeof(double));
+    double *Un = (double *)malloc(4 * np * sizeof(double));
+    if (!Us || !Un) { free(Us); free(Un); return -3; }
+    for (long long s = 0; s < nsteps; ++s) {
+        euler_stage(nx, ny, &k, tau0, U, U, Us);   /* U* = U + dt/2 L(U)  */
+        euler_stage(nx, ny, &k, tau1, Us, U, Un);  /* U' = U + dt L(U*)   */
+        memcpy(U, Un, 4 * np * sizeof(double));
+    }
+    free(Us); free(Un);
+    return 0;
+}

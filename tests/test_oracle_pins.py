@@ -1,0 +1,284 @@
+"""Pins for the CPU oracle: each test checks it against something other than
+itself -- a closed form, an exact rational computation, an invariant of the
+scheme, a published value, or the paper's own equations -- so that a dropped
+term, a wrong sign, a wrong index or a transposed operand fails at least one.
+"""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from paper_1602_07558_gb300 import inputs
+
+EPS = np.finfo(np.float64).eps
+MASK64 = (1 << 64) - 1
+
+
+# --------------------------------------------------------------------------- heat
+
+@pytest.mark.parametrize("T", [64, 512])
+def test_heat_single_fourier_mode_decays_by_exact_factor(oracle_lib, T):
+    """A single mode sin(2 pi 3 x/64) sin(2 pi 5 y/64) is an eigenvector of the
+    5-point forward-Euler scheme with factor g = 1 - 4 r (sin^2(pi p/N) + sin^2(pi q/N))
+    per step (discrete Fourier analysis); the oracle must follow g^T up to rounding,
+    which the max-norm-stable scheme (r = 0.2 <= 1/4) does not amplify."""
+    n, p, q, r = 64, 3, 5, 0.2
+    u0 = inputs.fourier_mode(n, n, p, q)
+    g = 1.0 - 4.0 * r * (np.sin(np.pi * p / n) ** 2 + np.sin(np.pi * q / n) ** 2)
+    uT = oracle_lib.heat(u0, r, T)
+    err = np.max(np.abs(uT - g ** T * u0))
+    assert err <= 4 * T * EPS * np.max(np.abs(u0))
+    # the decayed amplitude itself (not only the error) is as predicted
+    assert np.max(np.abs(uT)) == pytest.approx(g ** T * np.max(np.abs(u0)), rel=1e-9)
+
+
+def test_heat_conserves_the_grid_sum(oracle_lib):
+    """Sum over the periodic grid of (u_E + u_S + u_W + u_N - 4u) is zero, so the
+    sum is conserved up to rounding."""
+    u0 = inputs.uniform(48, 40, seed=7)
+    T = 200
+    uT = oracle_lib.heat(u0, 0.2, T)
+    assert abs(uT.sum() - u0.sum()) <= T * u0.size * 4 * EPS
+    assert not np.allclose(uT, u0)          # it did diffuse
+
+
+@pytest.mark.parametrize("nx,ny,T", [(4, 4, 12), (6, 8, 10)])
+def test_heat_matches_exact_rational_arithmetic(oracle_lib, nx, ny, T):
+    """Brute force with exact rationals (r taken as the exact value of the double
+    0.2): the oracle differs only by its rounding."""
+    rng = np.random.default_rng(11)
+    u0 = rng.integers(-16, 17, size=(ny, nx)) / 16.0
+    r = Fraction(0.2)
+    u = [[Fraction(float(u0[j, i])) for i in range(nx)] for j in range(ny)]
+    for _ in range(T):
+        u = [[u[j][i] + r * (u[j][(i + 1) % nx] + u[(j + 1) % ny][i] + u[j][(i - 1) % nx]
+                             + u[(j - 1) % ny][i] - 4 * u[j][i])
+              for i in range(nx)] for j in range(ny)]
+    exact = np.array([[float(v) for v in row] for row in u])
+    got = oracle_lib.heat(u0, 0.2, T)
+    assert np.max(np.abs(got - exact)) <= T * 8 * EPS * np.max(np.abs(u0))
+
+
+def test_heat_impulse_response_is_the_five_point_stencil(oracle_lib):
+    """One step from a unit impulse: 1 - 4r at the centre, r at the 4 edge
+    neighbours, exactly 0 at the diagonals and everywhere else."""
+    u0 = np.zeros((9, 11))
+    u0[4, 6] = 1.0
+    u1 = oracle_lib.heat(u0, 0.2, 1)
+    expect = np.zeros_like(u0)
+    expect[4, 6] = 1.0 - 4.0 * 0.2
+    for dj, di in [(0, 1), (0, -1), (1, 0), (-1, 0)]:
+        expect[4 + dj, 6 + di] = 0.2
+    assert np.array_equal(u1, expect)
+
+
+def test_heat_is_translation_and_mirror_equivariant(oracle_lib):
+    """The periodic scheme commutes with shifts and (by commutativity of each
+    rounded addition) with mirroring in x and y, bit for bit."""
+    u0 = inputs.uniform(20, 12, seed=3)
+    uT = oracle_lib.heat(u0, 0.2, 9)
+    shifted = oracle_lib.heat(np.roll(u0, (5, -7), axis=(0, 1)), 0.2, 9)
+    assert np.array_equal(shifted, np.roll(uT, (5, -7), axis=(0, 1)))
+    sq = inputs.uniform(16, 16, seed=4)
+    assert np.array_equal(oracle_lib.heat(sq.T, 0.2, 7), oracle_lib.heat(sq, 0.2, 7).T)
+
+
+# --------------------------------------------------------------------- increment
+
+def test_increment_worked_example(oracle_lib):
+    """Section 3.1: u^0 = 1 everywhere and St: u <- u + 1 gives 1 + T after T steps."""
+    u = oracle_lib.increment(np.ones((8, 8)), 7)
+    assert np.all(u == 8.0)
+
+
+# -------------------------------------------------------------------------- hash
+
+def test_mix64_is_splitmix64(oracle_lib):
+    """SplitMix64 seeded with 0 (state advanced by the golden gamma, then the
+    output function) has the published first outputs below."""
+    golden = 0x9E3779B97F4A7C15
+    expect = [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+    got = [oracle_lib.mix64((k * golden) & MASK64) for k in (1, 2, 3)]
+    assert got == expect
+
+
+@pytest.mark.parametrize("s", [1, 2, 3])
+def test_hash_domain_of_influence_is_the_9_point_square(oracle_lib, s):
+    """Changing one word changes, after s sub-steps, exactly the points within
+    Chebyshev distance s (the domain of influence of a 9-point radius-1 stencil,
+    Section 2 and Section 3), with periodic wrap."""
+    u0 = inputs.random_words(24, 20, seed=5)[0]
+    u1 = u0.copy()
+    j0, i0 = 1, 22                       # near two edges: exercises the wrap
+    u1[j0, i0] ^= np.uint64(1 << 17)
+    a, b = oracle_lib.hash_op(u0, s), oracle_lib.hash_op(u1, s)
+    changed = a != b
+    jj, ii = np.meshgrid(np.arange(20), np.arange(24), indexing="ij")
+    dj = np.minimum((jj - j0) % 20, (j0 - jj) % 20)
+    di = np.minimum((ii - i0) % 24, (i0 - ii) % 24)
+    assert np.array_equal(changed, np.maximum(dj, di) <= s)
+
+
+def test_hash_is_translation_equivariant_and_depends_on_the_substep(oracle_lib):
+    u0 = inputs.random_words(16, 12, seed=6)[0]
+    a = oracle_lib.hash_op(u0, 4, substep0=10)
+    b = oracle_lib.hash_op(np.roll(u0, (3, 5), axis=(0, 1)), 4, substep0=10)
+    assert np.array_equal(b, np.roll(a, (3, 5), axis=(0, 1)))
+    c = oracle_lib.hash_op(u0, 4, substep0=11)
+    assert np.all(a != c)
+
+
+# ---------------------------------------------------------------------- leveltag
+
+def test_leveltag_counts_levels_and_poisons_the_domain_of_influence(oracle_lib):
+    u = oracle_lib.leveltag(np.full((10, 12), 3.0), 6)
+    assert np.all(u == 9.0)
+    u0 = np.zeros((10, 12))
+    u0[5, 0] = 1.0                       # one point at the wrong level
+    u2 = oracle_lib.leveltag(u0, 2)
+    jj, ii = np.meshgrid(np.arange(10), np.arange(12), indexing="ij")
+    dist = np.maximum(np.abs(jj - 5), np.minimum(ii, 12 - ii))
+    assert np.array_equal(np.isnan(u2), dist <= 2)
+    assert np.all(u2[dist > 2] == 2.0)
+
+
+# ------------------------------------------------------------------------- wide2
+
+def test_wide2_impulse_response(oracle_lib):
+    """Eq. (complex_step) on a unit impulse: -4 at the centre, +1 two points away
+    along each axis (modulo 2^64)."""
+    u0 = np.zeros((9, 10), dtype=np.uint64)
+    u0[4, 5] = 1
+    u1 = oracle_lib.wide2(u0, 1)
+    expect = np.zeros_like(u0)
+    expect[4, 5] = np.uint64((1 << 64) - 4)
+    for dj, di in [(0, 2), (0, -2), (2, 0), (-2, 0)]:
+        expect[4 + dj, 5 + di] = 1
+    assert np.array_equal(u1, expect)
+
+
+def test_wide2_equals_the_two_substep_decomposition(oracle_lib):
+    """Eqs. (substep1)-(substep2): pushing (u, u_W, u_E, u_N, u_S) in a first
+    radius-1 sub-step and combining neighbours' components in a second gives
+    eq. (complex_step) (Section 2)."""
+    u = inputs.random_words(14, 11, seed=8)[0]
+    ref = oracle_lib.wide2(u, 5)
+    v = u.copy()
+    with np.errstate(over="ignore"):
+        for _ in range(5):
+            # sub-step 1: component k of the 5-vector (x along axis 1)
+            half = np.stack([v, np.roll(v, 1, axis=1), np.roll(v, -1, axis=1),
+                             np.roll(v, 1, axis=0), np.roll(v, -1, axis=0)])
+            # sub-step 2: west neighbour's 2nd, east's 3rd, north's 4th, south's 5th
+            v = (np.roll(half[1], 1, axis=1) + np.roll(half[2], -1, axis=1)
+                 + np.roll(half[3], 1, axis=0) + np.roll(half[4], -1, axis=0)
+                 - np.uint64(4) * half[0])
+    assert np.array_equal(v, ref)
+
+
+# ------------------------------------------------------------------------- euler
+
+GAMMA, CFL, KAPPA = 1.4, 0.3, 0.5
+
+
+def _euler_state(rho, m, q, p):
+    E = p / (GAMMA - 1.0) + 0.5 * (m * m + q * q) / rho
+    return np.stack([rho, m, q, E]).astype(np.float64)
+
+
+def test_euler_wavespeed_and_dt_closed_form(oracle_lib):
+    """Uniform gas at rest with p = rho = 1: a = sqrt(gamma); moving with
+    u = 0.5: a = 0.5 + sqrt(gamma); dt = cfl min(dx, dy) / a."""
+    ny, nx = 6, 8
+    one = np.ones((ny, nx))
+    a, dt = oracle_lib.euler_setup(_euler_state(one, 0 * one, 0 * one, one), GAMMA, CFL)
+    assert a == pytest.approx(np.sqrt(GAMMA), rel=4 * EPS)
+    assert dt == pytest.approx(CFL * (1.0 / nx) / np.sqrt(GAMMA), rel=8 * EPS)
+    a2, _ = oracle_lib.euler_setup(_euler_state(one, 0.5 * one, 0 * one, one), GAMMA, CFL)
+    assert a2 == pytest.approx(0.5 + np.sqrt(GAMMA), rel=8 * EPS)
+
+
+def test_euler_free_stream_is_preserved_bitwise(oracle_lib):
+    ny, nx = 8, 12
+    one = np.ones((ny, nx))
+    U0 = _euler_state(1.2 * one, 0.3 * one, -0.1 * one, 0.9 * one)
+    a, dt = oracle_lib.euler_setup(U0, GAMMA, CFL)
+    UT = oracle_lib.euler_rk2(U0, GAMMA, dt, KAPPA, a, 25)
+    assert np.array_equal(UT, U0)
+
+
+def test_euler_gas_at_rest_with_uniform_pressure(oracle_lib):
+    """rho = 1 + 0.1 cos(theta x), u = v = 0, p = 1: the fluxes F, G are uniform,
+    so m and q stay exactly 0 and E exactly constant, and rho follows the
+    dissipation alone -- a linear scheme whose Fourier factor per midpoint RK2
+    step is G = 1 + z + z^2/2, z = dt kax (2 cos theta - 2)."""
+    ny, nx, k = 6, 32, 2
+    x = np.arange(nx)
+    theta = 2 * np.pi * k / nx
+    rho = np.tile(1.0 + 0.1 * np.cos(theta * x), (ny, 1))
+    U0 = _euler_state(rho, 0 * rho, 0 * rho, np.ones_like(rho))
+    a, dt = oracle_lib.euler_setup(U0, GAMMA, CFL)
+    T = 60
+    UT = oracle_lib.euler_rk2(U0, GAMMA, dt, KAPPA, a, T)
+    assert np.all(UT[1] == 0.0) and np.all(UT[2] == 0.0)
+    assert np.array_equal(UT[3], U0[3])
+    kax = KAPPA * a * nx
+    z = dt * kax * (2 * np.cos(theta) - 2)
+    G = 1 + z + z * z / 2
+    assert abs(G) < 1.0
+    pred = 1.0 + 0.1 * G ** T * np.cos(theta * x)
+    assert np.max(np.abs(UT[0] - pred[None, :])) < 1e-13
+
+
+def test_euler_linear_acoustics(oracle_lib):
+    """A small perturbation of a gas at rest (rho0 = p0 = 1) follows the
+    linearised scheme: fluxes F ~ A w with A = [[0,1,0],[0,0,g-1],[0,g/(g-1),0]]
+    on w = (rho', m', E'), so per step w^ <- (I + Z + Z^2/2) w^ with
+    Z = dt (kax (2 cos th - 2) I - 2 i cx sin th A). Catches any error in the
+    pressure, the momentum flux or the energy flux."""
+    ny, nx, k, delta, T = 4, 32, 3, 1e-6, 40
+    x = np.arange(nx)
+    theta = 2 * np.pi * k / nx
+    w_hat = np.array([0.7, -0.4, 1.3])
+    c = np.cos(theta * x)
+    rho = np.tile(1.0 + delta * w_hat[0] * c, (ny, 1))
+    m = np.tile(delta * w_hat[1] * c, (ny, 1))
+    E = np.tile(1.0 / (GAMMA - 1.0) + delta * w_hat[2] * c, (ny, 1))
+    U0 = np.stack([rho, m, np.zeros_like(rho), E])
+    a, dt = oracle_lib.euler_setup(U0, GAMMA, CFL)
+    UT = oracle_lib.euler_rk2(U0, GAMMA, dt, KAPPA, a, T)
+    A = np.array([[0, 1, 0], [0, 0, GAMMA - 1], [0, GAMMA / (GAMMA - 1), 0]], dtype=complex)
+    cx, kax = 0.5 * nx, KAPPA * a * nx
+    Z = dt * (kax * (2 * np.cos(theta) - 2) * np.eye(3) - 2j * cx * np.sin(theta) * A)
+    G = np.eye(3) + Z + Z @ Z / 2
+    wT = np.linalg.matrix_power(G, T) @ w_hat
+    pred = np.real(wT[:, None] * np.exp(1j * theta * x)[None, :])      # (3, nx)
+    got = np.stack([UT[0, 0] - 1.0, UT[1, 0], UT[3, 0] - 1.0 / (GAMMA - 1.0)]) / delta
+    assert np.max(np.abs(got - pred)) < 1e-4
+    assert np.all(UT[2] == 0.0)
+    # and the perturbation really moved (it is not the identity map)
+    assert np.max(np.abs(pred - w_hat[:, None] * c[None, :])) > 0.1
+
+
+def test_euler_conserves_all_four_sums(oracle_lib):
+    U0 = inputs.euler_pulse(24, 20, seed=2)
+    a, dt = oracle_lib.euler_setup(U0, GAMMA, CFL)
+    UT = oracle_lib.euler_rk2(U0, GAMMA, dt, KAPPA, a, 50)
+    for c in range(4):
+        scale = np.sum(np.abs(U0[c])) + 1.0
+        assert abs(UT[c].sum() - U0[c].sum()) <= 1e-12 * scale
+    assert np.max(np.abs(UT[1])) > 1e-4      # the pulse set the gas moving
+
+
+def test_euler_transpose_symmetry_on_square_grids(oracle_lib):
+    """Swapping x with y (and m with q) maps the scheme to itself. The fused
+    multiply-adds round the two axes' terms in a fixed order, so the images agree
+    to rounding (any swapped index or axis constant would show at O(1e-3))."""
+    U0 = inputs.euler_pulse(16, 16, seed=9)
+    a, dt = oracle_lib.euler_setup(U0, GAMMA, CFL)
+    UT = oracle_lib.euler_rk2(U0, GAMMA, dt, KAPPA, a, 12)
+    Ut0 = np.stack([U0[0].T, U0[2].T, U0[1].T, U0[3].T])
+    UtT = oracle_lib.euler_rk2(Ut0, GAMMA, dt, KAPPA, a, 12)
+    mirror = np.stack([UT[0].T, UT[2].T, UT[1].T, UT[3].T])
+    assert np.max(np.abs(UtT - mirror)) <= 1e-13
+    assert np.max(np.abs(UT - U0)) > 1e-4
