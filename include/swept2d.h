@@ -1,0 +1,159 @@
+/*
+ * swept2d.h -- C ABI of the GB300 swept-rule library (libswept2d.so).
+ *
+ * Explicit time advancing of a 2D PDE on a doubly periodic Cartesian grid
+ * (Section 2, item 1) by the swept rule of space-time decomposition
+ * (Sections 3-4): the grid is cut into n x n tiles; each half cycle builds an
+ * upward pyramid per tile (Algorithm 1), the longitudinal and latitudinal
+ * bridges between them (Algorithms 2 and 3) and a downward pyramid in the
+ * frame shifted by (n/2, n/2) (Algorithm 5), glued as in Algorithm 4. On the
+ * GPU a tile is one thread block, its local store is shared memory, and the
+ * "network" is a panel buffer in device memory plus a kernel boundary. The
+ * downward pyramid of one half cycle and the upward pyramid of the next act on
+ * the same tile in the same frame, so they run fused in one kernel (the
+ * "octahedron"): two launches per n/2 sub-steps. A plain one-kernel-per-sub-step
+ * path (mode SWEPT2D_NAIVE) uses the same point-update code and gives bitwise
+ * identical results.
+ *
+ * Conventions.
+ *  - State: nvars planes of ny x nx elements, row-major, x fastest. Plane v,
+ *    row j, column i is element v*nx*ny + j*nx + i. "North" is j-1, "south"
+ *    j+1, "west" i-1, "east" i+1; indices wrap modulo nx and ny.
+ *  - One time step = nstages sub-steps; sub-step g (counted from the last
+ *    set_state) applies the point update's stage g mod nstages
+ *    (Section 2, item 2; the paper's timestep(i, p), Section 5).
+ *  - All functions return SWEPT2D_OK (0) or a negative status and never abort.
+ *    On failure, swept2d_last_error() gives a message for that handle.
+ *  - Ownership: the caller owns every pointer it passes and may free it when
+ *    the call returns. The library owns its device state and panel buffers
+ *    (allocated in swept2d_create, freed in swept2d_destroy).
+ *  - Streams: all device work of a handle runs on the CUDA stream given at
+ *    create time (NULL = the legacy default stream). set_state with a host
+ *    source and get_state synchronise that stream; advance does not.
+ *  - A handle is not thread-safe: calls on one handle must not overlap.
+ */
+#ifndef SWEPT2D_H
+#define SWEPT2D_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct swept2d swept2d_t;
+
+/* Status codes. */
+#define SWEPT2D_OK        0
+#define SWEPT2D_EINVAL   (-1)   /* invalid argument (message says which) */
+#define SWEPT2D_ECUDA    (-2)   /* a CUDA call or kernel launch failed */
+#define SWEPT2D_ENOMEM   (-3)   /* device or host allocation failed */
+#define SWEPT2D_ETIMEOUT (-4)   /* a bounded wait gave up (reserved) */
+#define SWEPT2D_ESTATE   (-5)   /* call out of order (e.g. advance before set_state) */
+
+/* Point updates (the paper's St_k; Section 2, Section 5).
+ *  HEAT       nvars 1, nstages 1, dtype F64, params {r}:
+ *             u' = u + r ((u_E + u_S) + (u_W + u_N) - 4u), the last
+ *             multiply-add fused.
+ *  EULER_RK2  nvars 8, nstages 2, dtype F64, params {gamma, cfl, kappa[, lx, ly]}:
+ *             planes 0-3 = (rho, rho u, rho v, E), planes 4-7 = midpoint stage
+ *             U*; central flux plus scalar dissipation kappa*a with a = max wave
+ *             speed of the state given to set_state; dt = cfl*min(dx,dy)/a fixed
+ *             at set_state; domain lx x ly (default 1 x 1). Stage 0 writes
+ *             (U, U + dt/2 L(U)); stage 1 writes (U + dt L(U*), U*).
+ *  INCREMENT  nvars 1, nstages 1, dtype F64: u' = u + 1 (Section 3.1 example).
+ *  HASH       nvars 1, nstages 1, dtype U64: 64-bit mix of the sub-step index
+ *             and the 9 neighbour words in row order (a test update).
+ *  LEVELTAG   nvars 1, nstages 1, dtype F64: u' = u + 1 if all 9 neighbours
+ *             equal u, else NaN (a test update: wrong-level inputs show up).
+ *  WIDE2      nvars 5, nstages 2, dtype U64: eq. (complex_step) run as its
+ *             two radius-1 sub-steps, eqs. (substep1)-(substep2), modulo 2^64;
+ *             plane 0 holds u after each whole step.
+ */
+#define SWEPT2D_OP_HEAT       0
+#define SWEPT2D_OP_EULER_RK2  1
+#define SWEPT2D_OP_INCREMENT  2
+#define SWEPT2D_OP_HASH       3
+#define SWEPT2D_OP_LEVELTAG   4
+#define SWEPT2D_OP_WIDE2      5
+
+/* Element types of the state. */
+#define SWEPT2D_F64  0
+#define SWEPT2D_U64  3
+
+/* Advance modes. */
+#define SWEPT2D_SWEPT 0   /* swept rule: Up, then per half cycle Bridge + Octahedron, final Down */
+#define SWEPT2D_NAIVE 1   /* one kernel launch per sub-step over the whole grid */
+
+/*
+ * Create a handle for an nx x ny grid.
+ *   tile   side n of the square tiles for the swept mode: even, >= 4, dividing
+ *          nx and ny, and small enough that two (n+2)^2 x nvars level buffers
+ *          fit in shared memory; 0 = naive mode only.
+ *   params op parameters (see above); nparams their count.
+ *   stream a cudaStream_t (NULL = legacy default stream).
+ * Allocates the device state and, if tile > 0, two panel buffers of
+ * 4 (n^2/2 + n) nvars elements per tile each. Errors: EINVAL (bad sizes, op
+ * mismatch), ENOMEM, ECUDA. On error *out is NULL.
+ */
+int swept2d_create(swept2d_t **out, int nx, int ny, int nvars, int nstages, int tile,
+                   int op, const double *params, int nparams, int dtype, void *stream);
+
+/* Copy nvars*ny*nx elements from src (device memory if src_is_device, else host
+ * memory) into the state, and reset the sub-step counter to 0. For EULER_RK2 it
+ * also computes the wave speed a and the fixed dt (Section 7's CFL number read
+ * as a fixed step from the initial state). Errors: EINVAL (NULL), ECUDA. */
+int swept2d_set_state(swept2d_t *h, const void *src, int src_is_device);
+
+/* Advance nsteps whole time steps (nsteps*nstages sub-steps) with mode
+ * SWEPT2D_SWEPT or SWEPT2D_NAIVE. The swept mode runs
+ * H = floor(nsteps*nstages / (n/2)) half cycles and the remaining sub-steps
+ * with the naive kernel. Asynchronous on the handle's stream; the state is in
+ * natural storage when the work completes. Errors: EINVAL (nsteps < 0, swept
+ * mode on a naive-only handle), ESTATE (no set_state yet), ECUDA. */
+int swept2d_advance(swept2d_t *h, long long nsteps, int mode);
+
+/* Copy the state to dst (device memory if dst_is_device, else host memory),
+ * after all work queued on the handle's stream; synchronises the stream.
+ * Errors: EINVAL (NULL), ESTATE, ECUDA. */
+int swept2d_get_state(swept2d_t *h, void *dst, int dst_is_device);
+
+/* Free all device memory of the handle and the handle itself (NULL is a no-op).
+ * Synchronises the handle's stream first. */
+int swept2d_destroy(swept2d_t *h);
+
+/* Last error message of the handle ("" if none). With h NULL: the message of
+ * the last failed swept2d_create on the calling thread. */
+const char *swept2d_last_error(const swept2d_t *h);
+
+/* Read-only queries, written to *out as a double. */
+#define SWEPT2D_Q_DT            0   /* EULER_RK2: fixed time step */
+#define SWEPT2D_Q_WAVESPEED     1   /* EULER_RK2: max wave speed a of the initial state */
+#define SWEPT2D_Q_SUBSTEPS      2   /* sub-steps advanced since set_state */
+#define SWEPT2D_Q_LAUNCHES      3   /* kernels launched by this handle since create */
+#define SWEPT2D_Q_STATE_BYTES   4   /* bytes of one state copy */
+#define SWEPT2D_Q_PANEL_BYTES   5   /* bytes of one panel buffer (0 if naive-only) */
+#define SWEPT2D_Q_SMEM_BYTES    6   /* dynamic shared memory per swept block */
+int swept2d_query(const swept2d_t *h, int what, double *out);
+
+/* Kernel timing: when on, every launch of the handle is bracketed by CUDA
+ * events on the handle's stream. swept2d_kernel_stats synchronises the stream
+ * and returns, for one kernel kind, the number of timed launches and their
+ * summed duration in milliseconds since timing was switched on. */
+#define SWEPT2D_K_NAIVE       0
+#define SWEPT2D_K_UP          1
+#define SWEPT2D_K_BRIDGE      2
+#define SWEPT2D_K_OCTAHEDRON  3
+#define SWEPT2D_K_DOWN        4
+#define SWEPT2D_K_REDUCE      5
+#define SWEPT2D_K_COUNT       6
+int swept2d_set_timing(swept2d_t *h, int on);
+int swept2d_kernel_stats(swept2d_t *h, int kind, long long *launches, double *total_ms);
+
+/* Measured FP64 issue rate of this GPU: a kernel of independent fused
+ * multiply-add chains on `stream`; writes lane-operations per second (one FMA
+ * = one operation) to *ops_per_s. Used to state the FP64-pipe roofline. */
+int swept2d_measure_fp64_rate(void *stream, double *ops_per_s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SWEPT2D_H */

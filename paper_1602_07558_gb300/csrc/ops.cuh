@@ -1,0 +1,184 @@
+// Point updates St_k (Section 2; the paper's timestep(i, p), Section 5).
+//
+// Each update is a functor with
+//   S        storage element type of one state value
+//   NV       values per point (the vector point state of Section 2, item 2)
+//   NST      sub-steps (stages) per time step
+//   operator()(stage, g, a, out): a(dx, dy, v) reads value v of the neighbour at
+//            offset (dx, dy) in {-1,0,1}^2 at the level below; out[0..NV) is the
+//            new point state; g is the global sub-step index.
+// The same functor runs in the naive kernel (neighbours from global memory) and
+// in every swept component (neighbours from shared memory), so the two paths
+// produce identical bits. All floating-point operations are written with
+// explicit round-to-nearest intrinsics, so no contraction can change them.
+#pragma once
+#include <cstdint>
+
+typedef unsigned long long u64;
+
+namespace swept {
+
+// Forward-Euler 5-point heat update, u' = u + r ((u_E + u_S) + (u_W + u_N) - 4u)
+// with the last multiply-add fused. s - 4u is formed as fma(-4, u, s), which is
+// the same rounding of the same exact value (4u is exact for |u| < 2^1021).
+struct HeatOp {
+    typedef double S;
+    static constexpr int NV = 1, NST = 1;
+    double r;
+    __host__ __device__ explicit HeatOp(const double *c) : r(c[0]) {}
+    template <class A>
+    __device__ __forceinline__ void operator()(int, u64, const A &a, S *out) const {
+        const double c = a(0, 0, 0);
+        const double pe = __dadd_rn(a(1, 0, 0), a(0, 1, 0));    // east + south
+        const double pw = __dadd_rn(a(-1, 0, 0), a(0, -1, 0));  // west + north
+        const double d = __fma_rn(-4.0, c, __dadd_rn(pe, pw));
+        out[0] = __fma_rn(r, d, c);
+    }
+};
+
+// Section 3.1 worked example: u' = u + 1.
+struct IncrementOp {
+    typedef double S;
+    static constexpr int NV = 1, NST = 1;
+    __host__ __device__ explicit IncrementOp(const double *) {}
+    template <class A>
+    __device__ __forceinline__ void operator()(int, u64, const A &a, S *out) const {
+        out[0] = __dadd_rn(a(0, 0, 0), 1.0);
+    }
+};
+
+// Test update: u' = u + 1 if all 9 neighbours hold the centre's level, else NaN.
+struct LevelTagOp {
+    typedef double S;
+    static constexpr int NV = 1, NST = 1;
+    __host__ __device__ explicit LevelTagOp(const double *) {}
+    template <class A>
+    __device__ __forceinline__ void operator()(int, u64, const A &a, S *out) const {
+        const double c = a(0, 0, 0);
+        bool same = true;
+#pragma unroll
+        for (int dj = -1; dj <= 1; ++dj)
+#pragma unroll
+            for (int di = -1; di <= 1; ++di) same = same && (a(di, dj, 0) == c);
+        out[0] = same ? __dadd_rn(c, 1.0) : __longlong_as_double(0x7ff8000000000000LL);
+    }
+};
+
+// SplitMix64 output function (Steele, Lea & Flood, OOPSLA 2014).
+__device__ __forceinline__ u64 mix64(u64 z) {
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+
+// Test update on 64-bit words: h = mix(g + golden); h = mix(h + w) over the 9
+// neighbours in row order (north row west..east, own row, south row).
+struct HashOp {
+    typedef u64 S;
+    static constexpr int NV = 1, NST = 1;
+    __host__ __device__ explicit HashOp(const double *) {}
+    template <class A>
+    __device__ __forceinline__ void operator()(int, u64 g, const A &a, S *out) const {
+        u64 h = mix64(g + 0x9e3779b97f4a7c15ULL);
+#pragma unroll
+        for (int dj = -1; dj <= 1; ++dj)
+#pragma unroll
+            for (int di = -1; di <= 1; ++di) h = mix64(h + a(di, dj, 0));
+        out[0] = h;
+    }
+};
+
+// Eq. (complex_step) as its two radius-1 sub-steps on 64-bit words (mod 2^64):
+// eq. (substep1) pushes (u, u_W, u_E, u_N, u_S); eq. (substep2) forms
+// u' = (west's 2nd + east's 3rd + north's 4th + south's 5th) - 4 (own 1st).
+struct Wide2Op {
+    typedef u64 S;
+    static constexpr int NV = 5, NST = 2;
+    __host__ __device__ explicit Wide2Op(const double *) {}
+    template <class A>
+    __device__ __forceinline__ void operator()(int stage, u64, const A &a, S *out) const {
+        if (stage == 0) {
+            out[0] = a(0, 0, 0);
+            out[1] = a(-1, 0, 0);
+            out[2] = a(1, 0, 0);
+            out[3] = a(0, -1, 0);
+            out[4] = a(0, 1, 0);
+        } else {
+            out[0] = a(-1, 0, 1) + a(1, 0, 2) + a(0, -1, 3) + a(0, 1, 4) - 4ULL * a(0, 0, 0);
+            out[1] = out[2] = out[3] = out[4] = 0ULL;
+        }
+    }
+};
+
+// 2D compressible Euler, midpoint RK2, central flux + scalar dissipation.
+// Point state: planes 0-3 U = (rho, m, q, E); planes 4-7 U*.
+//   stage 0: (U, U*) <- (U, U + tau0 L(U))
+//   stage 1: (U, U*) <- (U + tau1 L(U*), U*)
+// L(W) = (kax ((W_E + W_W) - 2W) + kay ((W_S + W_N) - 2W)) - (cx (F_E - F_W) + cy (G_S - G_N))
+// with F = (m, m u + p, q u, (E+p) u), G = (q, m v, q v + p, (E+p) v),
+// u = m/rho, v = q/rho, p = (gamma-1)(E - 0.5 (m u + q v)). Products followed
+// by a sum are fused exactly where the formula is written "a b + c".
+// Host-precomputed constants c[] = {gamma-1, cx, cy, kax, kay, tau0, tau1}.
+struct EulerOp {
+    typedef double S;
+    static constexpr int NV = 8, NST = 2;
+    double gm1, cx, cy, kax, kay, tau0, tau1;
+    __host__ __device__ explicit EulerOp(const double *c)
+        : gm1(c[0]), cx(c[1]), cy(c[2]), kax(c[3]), kay(c[4]), tau0(c[5]), tau1(c[6]) {}
+
+    __device__ __forceinline__ void prims(double r, double m, double q, double E, double &u,
+                                          double &v, double &pr, double &Ep) const {
+        const double iv = __ddiv_rn(1.0, r);
+        u = __dmul_rn(m, iv);
+        v = __dmul_rn(q, iv);
+        const double ke = __dmul_rn(0.5, __fma_rn(m, u, __dmul_rn(q, v)));
+        pr = __dmul_rn(gm1, __dsub_rn(E, ke));
+        Ep = __dadd_rn(E, pr);
+    }
+    __device__ __forceinline__ void xflux(double r, double m, double q, double E, double *F) const {
+        double u, v, pr, Ep;
+        prims(r, m, q, E, u, v, pr, Ep);
+        F[0] = m;
+        F[1] = __fma_rn(m, u, pr);
+        F[2] = __dmul_rn(q, u);
+        F[3] = __dmul_rn(Ep, u);
+    }
+    __device__ __forceinline__ void yflux(double r, double m, double q, double E, double *G) const {
+        double u, v, pr, Ep;
+        prims(r, m, q, E, u, v, pr, Ep);
+        G[0] = q;
+        G[1] = __dmul_rn(m, v);
+        G[2] = __fma_rn(q, v, pr);
+        G[3] = __dmul_rn(Ep, v);
+    }
+    template <class A>
+    __device__ __forceinline__ void operator()(int stage, u64, const A &a, S *out) const {
+        const int w0 = stage == 0 ? 0 : 4;
+        const double tau = stage == 0 ? tau0 : tau1;
+        double FW[4], FE[4], GN[4], GS[4];
+        xflux(a(-1, 0, w0), a(-1, 0, w0 + 1), a(-1, 0, w0 + 2), a(-1, 0, w0 + 3), FW);
+        xflux(a(1, 0, w0), a(1, 0, w0 + 1), a(1, 0, w0 + 2), a(1, 0, w0 + 3), FE);
+        yflux(a(0, -1, w0), a(0, -1, w0 + 1), a(0, -1, w0 + 2), a(0, -1, w0 + 3), GN);
+        yflux(a(0, 1, w0), a(0, 1, w0 + 1), a(0, 1, w0 + 2), a(0, 1, w0 + 3), GS);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const double wc = a(0, 0, w0 + c);
+            const double lx = __fma_rn(-2.0, wc, __dadd_rn(a(1, 0, w0 + c), a(-1, 0, w0 + c)));
+            const double ly = __fma_rn(-2.0, wc, __dadd_rn(a(0, 1, w0 + c), a(0, -1, w0 + c)));
+            const double diss = __fma_rn(kax, lx, __dmul_rn(kay, ly));
+            const double flux = __fma_rn(cx, __dsub_rn(FE[c], FW[c]),
+                                         __dmul_rn(cy, __dsub_rn(GS[c], GN[c])));
+            const double L = __dsub_rn(diss, flux);
+            const double res = __fma_rn(tau, L, a(0, 0, c));
+            if (stage == 0) {
+                out[c] = a(0, 0, c);
+                out[4 + c] = res;
+            } else {
+                out[c] = res;
+                out[4 + c] = a(0, 0, 4 + c);
+            }
+        }
+    }
+};
+
+}  // namespace swept

@@ -1,0 +1,190 @@
+"""Python binding of libswept2d.so (argument marshalling only).
+
+Every step of the time advance runs in the library's CUDA kernels; this module
+only loads the library, converts arguments and raises on error status. If the
+library cannot be built or loaded it raises -- there is no CPU fallback.
+
+The names follow the C ABI in ``include/swept2d.h``::
+
+    s = Swept2D(nx, ny, op="heat", tile=32, params=(0.2,), stream=torch_stream)
+    s.set_state(u0)               # numpy array or torch tensor, (nvars, ny, nx)
+    s.advance(10_000)             # mode="swept" (default) or "naive"
+    u = s.get_state()             # numpy array (or fills a given tensor/array)
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+OK, EINVAL, ECUDA, ENOMEM, ETIMEOUT, ESTATE = 0, -1, -2, -3, -4, -5
+OPS = {"heat": 0, "euler_rk2": 1, "increment": 2, "hash": 3, "leveltag": 4, "wide2": 5}
+# (nvars, nstages, dtype code, numpy dtype) of each point update
+OP_SHAPE = {
+    "heat": (1, 1, 0, np.float64),
+    "euler_rk2": (8, 2, 0, np.float64),
+    "increment": (1, 1, 0, np.float64),
+    "hash": (1, 1, 3, np.uint64),
+    "leveltag": (1, 1, 0, np.float64),
+    "wide2": (5, 2, 3, np.uint64),
+}
+MODES = {"swept": 0, "naive": 1}
+Q = {"dt": 0, "wavespeed": 1, "substeps": 2, "launches": 3, "state_bytes": 4,
+     "panel_bytes": 5, "smem_bytes": 6}
+KERNELS = {"naive": 0, "up": 1, "bridge": 2, "octahedron": 3, "down": 4, "reduce": 5}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class SweptError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"swept2d error {code}: {msg}")
+        self.code = code
+
+
+def lib():
+    """Load (building first if sources changed) libswept2d.so."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        vp, i, ll, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong, ctypes.c_double
+        L.swept2d_create.argtypes = [ctypes.POINTER(vp), i, i, i, i, i, i,
+                                     ctypes.POINTER(d), i, i, vp]
+        L.swept2d_set_state.argtypes = [vp, vp, i]
+        L.swept2d_advance.argtypes = [vp, ll, i]
+        L.swept2d_get_state.argtypes = [vp, vp, i]
+        L.swept2d_destroy.argtypes = [vp]
+        L.swept2d_last_error.argtypes = [vp]
+        L.swept2d_last_error.restype = ctypes.c_char_p
+        L.swept2d_query.argtypes = [vp, i, ctypes.POINTER(d)]
+        L.swept2d_set_timing.argtypes = [vp, i]
+        L.swept2d_kernel_stats.argtypes = [vp, i, ctypes.POINTER(ll), ctypes.POINTER(d)]
+        L.swept2d_measure_fp64_rate.argtypes = [vp, ctypes.POINTER(d)]
+        for name in ("swept2d_create", "swept2d_set_state", "swept2d_advance",
+                     "swept2d_get_state", "swept2d_destroy", "swept2d_query",
+                     "swept2d_set_timing", "swept2d_kernel_stats", "swept2d_measure_fp64_rate"):
+            getattr(L, name).restype = i
+        _lib = L
+        return L
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)          # torch.cuda.Stream / ExternalStream
+
+
+def _buffer(x, dtype, nbytes):
+    """(pointer, is_device, keepalive) of a numpy array or torch tensor."""
+    if isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous or x.dtype.itemsize != np.dtype(dtype).itemsize:
+            raise ValueError("array must be C-contiguous with the op's element size")
+        if x.nbytes != nbytes:
+            raise ValueError(f"array has {x.nbytes} bytes, the state has {nbytes}")
+        return x.ctypes.data, 0, x
+    try:
+        import torch
+    except ImportError as e:  # pragma: no cover
+        raise TypeError("expected a numpy array") from e
+    if not isinstance(x, torch.Tensor):
+        raise TypeError("expected a numpy array or a torch tensor")
+    if not x.is_contiguous() or x.element_size() != np.dtype(dtype).itemsize:
+        raise ValueError("tensor must be contiguous with the op's element size")
+    if x.numel() * x.element_size() != nbytes:
+        raise ValueError("tensor size does not match the state")
+    return x.data_ptr(), 1 if x.is_cuda else 0, x
+
+
+def measure_fp64_rate(stream=None) -> float:
+    """FP64 fused multiply-adds per second measured on the current device."""
+    out = ctypes.c_double()
+    rc = lib().swept2d_measure_fp64_rate(_stream_handle(stream), ctypes.byref(out))
+    if rc != OK:
+        raise SweptError(rc, "measure_fp64_rate failed")
+    return out.value
+
+
+class Swept2D:
+    """One periodic nx x ny grid advanced by the swept rule (or the naive path)."""
+
+    def __init__(self, nx, ny, op="heat", tile=0, params=(), stream=None):
+        if op not in OPS:
+            raise ValueError(f"unknown op {op!r}; one of {sorted(OPS)}")
+        self.nx, self.ny, self.op, self.tile = int(nx), int(ny), op, int(tile)
+        self.nvars, self.nstages, self._dtype_code, self.np_dtype = OP_SHAPE[op]
+        self.params = tuple(float(p) for p in params)
+        self._stream = _stream_handle(stream)
+        self._h = ctypes.c_void_p()
+        arr = (ctypes.c_double * max(1, len(self.params)))(*self.params)
+        L = lib()
+        rc = L.swept2d_create(ctypes.byref(self._h), self.nx, self.ny, self.nvars, self.nstages,
+                              self.tile, OPS[op], arr, len(self.params), self._dtype_code,
+                              self._stream)
+        if rc != OK:
+            raise SweptError(rc, L.swept2d_last_error(None).decode())
+        self.state_bytes = int(self.query("state_bytes"))
+
+    # -- helpers
+    def _check(self, rc):
+        if rc != OK:
+            raise SweptError(rc, lib().swept2d_last_error(self._h).decode())
+
+    @property
+    def shape(self):
+        return (self.nvars, self.ny, self.nx)
+
+    # -- the C ABI, one method per entry point
+    def set_state(self, state):
+        ptr, dev, keep = _buffer(state, self.np_dtype, self.state_bytes)
+        self._check(lib().swept2d_set_state(self._h, ptr, dev))
+        del keep
+
+    def advance(self, nsteps, mode="swept"):
+        self._check(lib().swept2d_advance(self._h, int(nsteps), MODES[mode]))
+
+    def get_state(self, out=None):
+        if out is None:
+            out = np.empty(self.shape, dtype=self.np_dtype)
+        ptr, dev, keep = _buffer(out, self.np_dtype, self.state_bytes)
+        self._check(lib().swept2d_get_state(self._h, ptr, dev))
+        return out
+
+    def query(self, what):
+        v = ctypes.c_double()
+        self._check(lib().swept2d_query(self._h, Q[what], ctypes.byref(v)))
+        return v.value
+
+    def set_timing(self, on=True):
+        self._check(lib().swept2d_set_timing(self._h, 1 if on else 0))
+
+    def kernel_stats(self, kind):
+        n, ms = ctypes.c_longlong(), ctypes.c_double()
+        self._check(lib().swept2d_kernel_stats(self._h, KERNELS[kind], ctypes.byref(n),
+                                               ctypes.byref(ms)))
+        return n.value, ms.value
+
+    def close(self):
+        if self._h:
+            lib().swept2d_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,168 @@
+"""GPU parity: the CUDA paths (through the C ABI) against the CPU oracle.
+
+Bar (stated per test): bitwise for the integer/word updates and for heat (the
+GPU and the oracle evaluate the same IEEE operations in the same order);
+swept == naive bitwise for every update (the same point-update code); Euler
+within 1e-12 of the oracle in the max-norm relative to max(|oracle|, |u0|)
+(the test also reports whether it is bitwise).
+"""
+import numpy as np
+import pytest
+
+from paper_1602_07558_gb300 import inputs
+from paper_1602_07558_gb300.swept2d import Swept2D
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+GAMMA, CFL, KAPPA = 1.4, 0.3, 0.5
+
+
+def run(op, u0, nsteps, tile, mode, params=(), chunks=None):
+    ny, nx = u0.shape[-2:]
+    with Swept2D(nx, ny, op=op, tile=tile, params=params) as s:
+        s.set_state(np.ascontiguousarray(u0.reshape(s.shape)))
+        for c in (chunks or [nsteps]):
+            s.advance(c, mode=mode)
+        return s.get_state()
+
+
+# ------------------------------------------------------------------ heat, 64^2
+
+def test_heat_64_uniform_512_steps_matches_oracle_bitwise(oracle_lib):
+    """Heat, periodic 64 x 64, r = 0.2, 512 steps, U[0,1) from seed 0, tile 16."""
+    u0 = inputs.uniform(64, 64, seed=0)
+    ref = oracle_lib.heat(u0, 0.2, 512)
+    naive = run("heat", u0, 512, 16, "naive", (0.2,))[0]
+    swept = run("heat", u0, 512, 16, "swept", (0.2,))[0]
+    assert np.array_equal(naive, ref)
+    assert np.array_equal(swept, naive)
+
+
+def test_heat_64_fourier_mode_matches_oracle_and_decays(oracle_lib):
+    u0 = inputs.fourier_mode(64, 64, 3, 5)
+    ref = oracle_lib.heat(u0, 0.2, 512)
+    swept = run("heat", u0, 512, 16, "swept", (0.2,))[0]
+    assert np.array_equal(swept, ref)
+    g = 1.0 - 0.8 * (np.sin(np.pi * 3 / 64) ** 2 + np.sin(np.pi * 5 / 64) ** 2)
+    assert np.max(np.abs(swept - g ** 512 * u0)) <= 4 * 512 * np.finfo(float).eps
+
+
+@pytest.mark.parametrize("nx,ny,tile,nsteps", [
+    (96, 64, 32, 77),      # several tiles, ragged tail (77 = 4*16 + 13)
+    (64, 96, 16, 41),      # nx != ny the other way, odd number of half cycles + tail
+    (40, 24, 8, 35),
+    (32, 32, 4, 30),       # smallest tile
+    (128, 64, 64, 100),    # largest FP64 heat tile that fits two level buffers
+    (16, 48, 16, 21),      # one tile across x: a tile borders itself
+    (64, 64, 16, 7),       # fewer steps than a half cycle: naive tail only
+    (64, 64, 16, 0),
+])
+def test_heat_swept_equals_naive_and_oracle(oracle_lib, nx, ny, tile, nsteps):
+    u0 = inputs.uniform(nx, ny, seed=nx + ny + tile)
+    ref = oracle_lib.heat(u0, 0.2, nsteps)
+    swept = run("heat", u0, nsteps, tile, "swept", (0.2,))[0]
+    naive = run("heat", u0, nsteps, tile, "naive", (0.2,))[0]
+    assert np.array_equal(naive, ref)
+    assert np.array_equal(swept, ref)
+
+
+# ---------------------------------------------------- test updates (bitwise)
+
+@pytest.mark.parametrize("nx,ny,tile,nsub", [
+    (64, 48, 16, 40), (48, 64, 8, 29), (24, 24, 4, 13), (32, 16, 16, 24), (16, 16, 16, 16),
+])
+def test_hash_swept_is_bitwise_the_oracle(oracle_lib, nx, ny, tile, nsub):
+    """Any wrong, missing or stale neighbour in any swept component changes the
+    64-bit mix; every level of every component is exercised."""
+    u0 = inputs.random_words(nx, ny, seed=tile * 7 + nsub)[0]
+    ref = oracle_lib.hash_op(u0, nsub)
+    assert np.array_equal(run("hash", u0, nsub, tile, "swept")[0], ref)
+    assert np.array_equal(run("hash", u0, nsub, tile, "naive")[0], ref)
+
+
+def test_hash_sub_step_counter_runs_across_advance_calls(oracle_lib):
+    u0 = inputs.random_words(32, 32, seed=1)[0]
+    ref = oracle_lib.hash_op(u0, 3 + 16 + 5)
+    got = run("hash", u0, None, 8, "swept", chunks=[3, 16, 5])[0]
+    assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("tile,nsub", [(8, 24), (16, 40), (32, 48)])
+def test_leveltag_every_point_sees_nine_neighbours_of_its_level(tile, nsub):
+    u0 = np.zeros((64, 64))
+    got = run("leveltag", u0, nsub, tile, "swept")[0]
+    assert not np.isnan(got).any()
+    assert np.all(got == nsub)
+
+
+def test_increment_worked_example():
+    """Section 3.1 example, 8 x 8 tiles on 4 subdomains, one full cycle."""
+    got = run("increment", np.ones((16, 16)), 8, 8, "swept")[0]
+    assert np.all(got == 9.0)
+
+
+@pytest.mark.parametrize("tile,nsteps", [(8, 12), (16, 9), (4, 7)])
+def test_wide2_two_substep_scheme_matches_direct_radius2(oracle_lib, tile, nsteps):
+    """nstages = 2 with a 5-component point state through every component."""
+    words = inputs.random_words(48, 32, seed=tile)[0]
+    u0 = np.zeros((5, 32, 48), dtype=np.uint64)
+    u0[0] = words
+    ref = oracle_lib.wide2(words, nsteps)
+    swept = run("wide2", u0, nsteps, tile, "swept")
+    naive = run("wide2", u0, nsteps, tile, "naive")
+    assert np.array_equal(swept, naive)
+    assert np.array_equal(swept[0], ref)
+
+
+# ---------------------------------------------------------------------- Euler
+
+def _euler_u0(nx, ny, seed, literal=False):
+    U = inputs.euler_pulse(nx, ny, seed, gamma=GAMMA, literal=literal)
+    return np.concatenate([U, U]), U
+
+
+@pytest.mark.parametrize("nx,ny,tile,nsteps", [(64, 48, 16, 40), (32, 32, 8, 13), (64, 64, 32, 20)])
+def test_euler_swept_equals_naive_and_oracle(oracle_lib, nx, ny, tile, nsteps):
+    u0, U = _euler_u0(nx, ny, seed=2)
+    a, dt = oracle_lib.euler_setup(U, GAMMA, CFL)
+    ref = oracle_lib.euler_rk2(U, GAMMA, dt, KAPPA, a, nsteps)
+    with Swept2D(nx, ny, op="euler_rk2", tile=tile, params=(GAMMA, CFL, KAPPA)) as s:
+        s.set_state(u0)
+        assert s.query("wavespeed") == a and s.query("dt") == dt
+        s.advance(nsteps, mode="swept")
+        swept = s.get_state()
+    naive = run("euler_rk2", u0, nsteps, tile, "naive", (GAMMA, CFL, KAPPA))
+    assert np.array_equal(swept, naive)
+    denom = max(np.max(np.abs(ref)), np.max(np.abs(U)))
+    assert np.max(np.abs(swept[:4] - ref)) / denom <= 1e-12
+    assert np.array_equal(swept[:4], ref)      # same operations in the same order
+
+
+# ------------------------------------------------------ full-size sampled check
+
+def test_heat_4096_tile_32_full_grid_matches_oracle(oracle_lib):
+    """The benchmark's grid and tile (4096 x 4096, n = 32): three half cycles
+    plus a tail, compared with the oracle on every point."""
+    u0 = inputs.smooth_field(4096, 4096, seed=1)
+    ref = oracle_lib.heat(u0, 0.2, 53)
+    got = run("heat", u0, 53, 32, "swept", (0.2,))[0]
+    assert np.array_equal(got, ref)
+    # conservation over a longer swept run of the same grid
+    long = run("heat", u0, 640, 32, "swept", (0.2,))[0]
+    assert abs(long.sum() - u0.sum()) <= 640 * u0.size * 4 * np.finfo(float).eps * np.abs(u0).max()
+
+
+def test_device_tensors_in_and_out():
+    u0 = torch.rand(1, 64, 64, dtype=torch.float64, device="cuda")
+    with Swept2D(64, 64, op="heat", tile=16, params=(0.2,),
+                 stream=torch.cuda.current_stream()) as s:
+        s.set_state(u0)
+        s.advance(16)
+        out = torch.empty_like(u0)
+        s.get_state(out)
+        host = s.get_state()
+    assert np.array_equal(out.cpu().numpy(), host)
