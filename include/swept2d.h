@@ -35,6 +35,8 @@
 #ifndef SWEPT2D_H
 #define SWEPT2D_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -152,6 +154,46 @@ int swept2d_kernel_stats(swept2d_t *h, int kind, long long *launches, double *to
  * multiply-add chains on `stream`; writes lane-operations per second (one FMA
  * = one operation) to *ops_per_s. Used to state the FP64-pipe roofline. */
 int swept2d_measure_fp64_rate(void *stream, double *ops_per_s);
+
+/*
+ * Allocation-free swept advance of the heat equation (FP64). The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate device
+ * memory where they advance a grid -- e.g. an application that owns all device
+ * memory through its own fixed pool and forbids cudaMalloc outside it (or a
+ * plugin running inside one), or a latency-critical loop that cannot afford the
+ * implicit device-wide synchronisation of cudaMalloc/cudaFree.
+ *
+ * It advances the nx x ny grid u_in (device memory, one FP64 plane, row-major)
+ * by nsteps steps of HEAT with diffusion number r and tile n = `tile`, writing
+ * u_out (device memory; must not overlap u_in; u_in is not modified). The result
+ * is bit for bit that of a handle (op HEAT, same tile) advanced in mode
+ * SWEPT2D_SWEPT, sub-step indices counted from 0. Work is queued on `stream`
+ * (a cudaStream_t; NULL = legacy default stream) and the call returns without
+ * synchronising.
+ *
+ * Memory. It calls no cudaMalloc, cudaFree or other allocating routine. Its only
+ * scratch is a static device array of SWEPT2D_STATIC_SCRATCH_BYTES in this
+ * library, which every GPU that loads the library holds until the process
+ * exits. It needs 2 * 4 * (n*n/2 + n) * 8 bytes per tile (the two panel
+ * buffers) plus nx*ny*8 bytes when nsteps is not a multiple of n/2, each part
+ * rounded up to 256 bytes; larger grids are rejected with SWEPT2D_EINVAL and a
+ * message. Nothing in the scratch needs to start at zero.
+ *
+ * Set-up. The first call on each device looks up the device address of the
+ * scratch array (cudaGetSymbolAddress, with that device current) and caches it;
+ * make that first call before any stream capture begins.
+ *
+ * Concurrency. All calls on a device share the one scratch array, and it keeps
+ * the contents of the last call: calls whose work overlaps on the GPU (other
+ * streams, other host threads) race on it and corrupt each other's results.
+ * Order them on one stream or synchronise between them.
+ *
+ * Errors: SWEPT2D_EINVAL (bad sizes or pointers, grid too large for the
+ * scratch), SWEPT2D_ECUDA; a message goes to err (errlen bytes, may be NULL).
+ */
+#define SWEPT2D_STATIC_SCRATCH_BYTES ((size_t)32 << 20)
+int swept2d_heat_advance_static(const double *u_in, double *u_out, int nx, int ny, int tile,
+                                double r, long long nsteps, void *stream, char *err, int errlen);
 
 #ifdef __cplusplus
 }

@@ -188,3 +188,28 @@ class Swept2D:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def heat_advance_static(u_in, u_out, nx, ny, tile, r, nsteps, stream=None):
+    """swept2d_heat_advance_static: the allocation-free swept heat advance.
+
+    For callers that may not allocate device memory while they advance (their
+    host application owns all device memory through a fixed pool, or they
+    cannot afford cudaMalloc's implicit synchronisation). ``u_in`` and
+    ``u_out`` are device buffers (torch CUDA tensors or raw pointers) of
+    nx*ny FP64 values; the only scratch is the library's static device array
+    (``SWEPT2D_STATIC_SCRATCH_BYTES``), shared by every call on a device, so
+    calls must not overlap on the GPU. Returns nothing; raises SweptError.
+    """
+    L = lib()
+    fn = L.swept2d_heat_advance_static
+    fn.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                   ctypes.c_double, ctypes.c_longlong, ctypes.c_void_p, ctypes.c_char_p,
+                   ctypes.c_int]
+    fn.restype = ctypes.c_int
+    ptr = lambda x: x if isinstance(x, int) else x.data_ptr()
+    err = ctypes.create_string_buffer(256)
+    rc = fn(ptr(u_in), ptr(u_out), int(nx), int(ny), int(tile), float(r), int(nsteps),
+            _stream_handle(stream), err, 256)
+    if rc != OK:
+        raise SweptError(rc, err.value.decode())
