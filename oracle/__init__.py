@@ -68,8 +68,15 @@ def _load():
         lib.oracle_euler_setup.argtypes = [i, i, d, d, d, d, p,
                                            ctypes.POINTER(d), ctypes.POINTER(d)]
         lib.oracle_euler_rk2.argtypes = [i, i, d, d, d, d, d, d, ll, p]
+        lib.oracle_heat_kahan_f32.argtypes = [i, i, d, ll, p, p]
+        lib.oracle_heat_kahan_bf16.argtypes = [i, i, d, ll, p, p]
+        lib.oracle_f32_to_bf16.argtypes = [ctypes.c_float]
+        lib.oracle_f32_to_bf16.restype = ctypes.c_uint16
+        lib.oracle_bf16_to_f32.argtypes = [ctypes.c_uint16]
+        lib.oracle_bf16_to_f32.restype = ctypes.c_float
         for name in ("oracle_heat", "oracle_increment", "oracle_hash", "oracle_leveltag",
-                     "oracle_wide2", "oracle_euler_setup", "oracle_euler_rk2"):
+                     "oracle_wide2", "oracle_euler_setup", "oracle_euler_rk2",
+                     "oracle_heat_kahan_f32", "oracle_heat_kahan_bf16"):
             getattr(lib, name).restype = i
         _lib = lib
         return lib
@@ -159,3 +166,27 @@ def euler_rk2(U0, gamma: float, dt: float, kappa: float, a: float, nsteps: int,
                                     float(kappa), float(a), int(nsteps), U.ctypes.data),
            "euler_rk2")
     return U
+
+
+def f32_to_bf16(x: float) -> int:
+    """binary32 -> bfloat16 bits, round to nearest even."""
+    return int(_load().oracle_f32_to_bf16(ctypes.c_float(x)))
+
+
+def bf16_to_f32(h: int) -> float:
+    return float(_load().oracle_bf16_to_f32(ctypes.c_uint16(h)))
+
+
+def heat_kahan(u0, c0, r: float, nsteps: int, storage: str = "f32"):
+    """Heat in binary32 arithmetic with Kahan-compensated time accumulation.
+    ``storage`` "f32": u0, c0 float32 arrays; "bf16": uint16 arrays of bfloat16
+    bits. Returns new (u, c) arrays of the same type."""
+    dt = np.float32 if storage == "f32" else np.uint16
+    u = _grid(u0, dt)
+    c = _grid(c0, dt)
+    if u.shape != c.shape:
+        raise ValueError("u and c differ in shape")
+    ny, nx = u.shape
+    fn = _load().oracle_heat_kahan_f32 if storage == "f32" else _load().oracle_heat_kahan_bf16
+    _check(fn(nx, ny, float(r), int(nsteps), u.ctypes.data, c.ctypes.data), "heat_kahan")
+    return u, c

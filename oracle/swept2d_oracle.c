@@ -36,6 +36,9 @@
  *             (substep2), is what the swept path runs)
  *   euler     2D compressible Euler, central flux plus scalar dissipation,
  *             midpoint (2-stage) Runge-Kutta, dt fixed from the initial state
+ *   heat_kahan the heat update in binary32 arithmetic with the time update
+ *             accumulated by Kahan's compensated summation, state (u, c) stored
+ *             in binary32 or in bfloat16 (reduced-precision storage forms)
  */
 #include <math.h>
 #include <stdint.h>
@@ -310,5 +313,109 @@ int oracle_euler_rk2(int nx, int ny, double gamma, double dt, double lx, double 
         memcpy(U, Un, 4 * np * sizeof(double));
     }
     free(Us); free(Un);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ heat_kahan
+ * Reduced-precision storage of the heat state with binary32 arithmetic. Each
+ * point stores u and a compensation c (Kahan, "Further remarks on reducing
+ * truncation errors", CACM 8(1), 1965): the increment of one step is
+ *     delta = r * ((u_E + u_S) + (u_W + u_N) - 4u)        (last difference fused)
+ * and it is added to u by compensated summation, the storage rounding playing
+ * the role of the rounded sum:
+ *     y = delta - c;  t = u + y;  u' = store(t);  c' = store((u' - u) - y)
+ * store() is exact for binary32 and round-to-nearest-even to bfloat16 (the top
+ * 16 bits of a binary32) for the bfloat16 form. Neighbours read the stored u. */
+
+/* binary32 -> bfloat16, round to nearest, ties to even (NaN stays NaN). */
+uint16_t oracle_f32_to_bf16(float f) {
+    uint32_t x;
+    memcpy(&x, &f, sizeof x);
+    if ((x & 0x7fffffffu) > 0x7f800000u) return (uint16_t)((x >> 16) | 0x0040u);
+    uint32_t lsb = (x >> 16) & 1u;
+    x += 0x7fffu + lsb;
+    return (uint16_t)(x >> 16);
+}
+
+float oracle_bf16_to_f32(uint16_t h) {
+    uint32_t x = (uint32_t)h << 16;
+    float f;
+    memcpy(&f, &x, sizeof f);
+    return f;
+}
+
+static void kahan_point(float r, float uc, float cc, float e, float s, float w, float n,
+                        float *t_out, float *y_out) {
+    float pe = e + s;
+    float pw = w + n;
+    float d = fmaf(-4.0f, uc, pe + pw);
+    float delta = r * d;
+    float y = delta - cc;
+    *t_out = uc + y;
+    *y_out = y;
+}
+
+int oracle_heat_kahan_f32(int nx, int ny, double r64, long long nsteps, float *u, float *c) {
+    if (nx < 1 || ny < 1 || nsteps < 0 || !u || !c) return -1;
+    size_t npts = (size_t)nx * ny;
+    float r = (float)r64;
+    float *u2 = (float *)malloc(npts * sizeof(float));
+    float *c2 = (float *)malloc(npts * sizeof(float));
+    if (!u2 || !c2) { free(u2); free(c2); return -3; }
+    float *ua = u, *ca = c, *ub = u2, *cb = c2;
+    for (long long s = 0; s < nsteps; ++s) {
+#pragma omp parallel for schedule(static)
+        for (int j = 0; j < ny; ++j) {
+            int jn = wrapi(j - 1, ny), js = wrapi(j + 1, ny);
+            for (int i = 0; i < nx; ++i) {
+                int iw = wrapi(i - 1, nx), ie = wrapi(i + 1, nx);
+                size_t p = (size_t)j * nx + i;
+                float t, y;
+                kahan_point(r, ua[p], ca[p], ua[(size_t)j * nx + ie], ua[(size_t)js * nx + i],
+                            ua[(size_t)j * nx + iw], ua[(size_t)jn * nx + i], &t, &y);
+                ub[p] = t;
+                cb[p] = (t - ua[p]) - y;
+            }
+        }
+        float *tu = ua; ua = ub; ub = tu;
+        float *tc = ca; ca = cb; cb = tc;
+    }
+    if (ua != u) { memcpy(u, ua, npts * sizeof(float)); memcpy(c, ca, npts * sizeof(float)); }
+    free(u2); free(c2);
+    return 0;
+}
+
+int oracle_heat_kahan_bf16(int nx, int ny, double r64, long long nsteps, uint16_t *u, uint16_t *c) {
+    if (nx < 1 || ny < 1 || nsteps < 0 || !u || !c) return -1;
+    size_t npts = (size_t)nx * ny;
+    float r = (float)r64;
+    uint16_t *u2 = (uint16_t *)malloc(npts * sizeof(uint16_t));
+    uint16_t *c2 = (uint16_t *)malloc(npts * sizeof(uint16_t));
+    if (!u2 || !c2) { free(u2); free(c2); return -3; }
+    uint16_t *ua = u, *ca = c, *ub = u2, *cb = c2;
+    for (long long s = 0; s < nsteps; ++s) {
+#pragma omp parallel for schedule(static)
+        for (int j = 0; j < ny; ++j) {
+            int jn = wrapi(j - 1, ny), js = wrapi(j + 1, ny);
+            for (int i = 0; i < nx; ++i) {
+                int iw = wrapi(i - 1, nx), ie = wrapi(i + 1, nx);
+                size_t p = (size_t)j * nx + i;
+                float uc = oracle_bf16_to_f32(ua[p]);
+                float t, y;
+                kahan_point(r, uc, oracle_bf16_to_f32(ca[p]),
+                            oracle_bf16_to_f32(ua[(size_t)j * nx + ie]),
+                            oracle_bf16_to_f32(ua[(size_t)js * nx + i]),
+                            oracle_bf16_to_f32(ua[(size_t)j * nx + iw]),
+                            oracle_bf16_to_f32(ua[(size_t)jn * nx + i]), &t, &y);
+                uint16_t un = oracle_f32_to_bf16(t);
+                ub[p] = un;
+                cb[p] = oracle_f32_to_bf16((oracle_bf16_to_f32(un) - uc) - y);
+            }
+        }
+        uint16_t *tu = ua; ua = ub; ub = tu;
+        uint16_t *tc = ca; ca = cb; cb = tc;
+    }
+    if (ua != u) { memcpy(u, ua, npts * sizeof(uint16_t)); memcpy(c, ca, npts * sizeof(uint16_t)); }
+    free(u2); free(c2);
     return 0;
 }

@@ -282,3 +282,95 @@ def test_euler_transpose_symmetry_on_square_grids(oracle_lib):
     mirror = np.stack([UT[0].T, UT[2].T, UT[1].T, UT[3].T])
     assert np.max(np.abs(UtT - mirror)) <= 1e-13
     assert np.max(np.abs(UT - U0)) > 1e-4
+
+
+# ------------------------------------------------------- reduced-precision heat
+
+def test_bf16_rounding_is_round_to_nearest_even(oracle_lib):
+    """Hand-checked ties and a library conversion (torch's float32 -> bfloat16,
+    round to nearest even) on random values across many binades."""
+    assert oracle_lib.f32_to_bf16(1.0) == 0x3F80
+    assert oracle_lib.f32_to_bf16(1.0 + 2 ** -8) == 0x3F80          # tie -> even
+    assert oracle_lib.f32_to_bf16(1.0 + 3 * 2 ** -8) == 0x3F82      # tie -> even
+    assert oracle_lib.f32_to_bf16(1.0 + 2 ** -8 + 2 ** -20) == 0x3F81
+    assert oracle_lib.f32_to_bf16(-2.0) == 0xC000
+    assert oracle_lib.bf16_to_f32(0x3F81) == 1.0078125
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(21)
+    x = (rng.standard_normal(2000) * 10.0 ** rng.uniform(-20, 20, 2000)).astype(np.float32)
+    ref = torch.from_numpy(x).to(torch.bfloat16).view(torch.int16).numpy().astype(np.uint16)
+    got = np.array([oracle_lib.f32_to_bf16(float(v)) for v in x], dtype=np.uint16)
+    assert np.array_equal(got, ref)
+
+
+def _plain_f32_heat(u0, r, T):
+    """Uncompensated binary32 forward Euler (numpy), the baseline Kahan improves on."""
+    u = u0.astype(np.float32)
+    r = np.float32(r)
+    for _ in range(T):
+        s = (np.roll(u, -1, 1) + np.roll(u, -1, 0)) + (np.roll(u, 1, 1) + np.roll(u, 1, 0))
+        u = u + r * (s - np.float32(4) * u)
+    return u
+
+
+def test_heat_kahan_f32_tracks_fp64_better_than_plain_f32(oracle_lib):
+    """A slowly decaying mode (per-step increments ~1e-3 of u): the compensated
+    accumulation keeps the binary32 result closer to the FP64 one than
+    uncompensated binary32 arithmetic (the stencil still reads the rounded
+    stored values, which bounds the gain to a few times), and it still follows
+    the exact decay."""
+    n, T = 64, 2000
+    u64 = 1.0 + 0.5 * inputs.fourier_mode(n, n, 1, 1)
+    ref = oracle_lib.heat(u64, 0.2, T)
+    u, c = oracle_lib.heat_kahan(u64.astype(np.float32), np.zeros((n, n), np.float32), 0.2, T)
+    err_kahan = np.max(np.abs(u.astype(np.float64) - ref))
+    err_plain = np.max(np.abs(_plain_f32_heat(u64, 0.2, T).astype(np.float64) - ref))
+    assert err_kahan < err_plain / 2.5
+    assert err_kahan < 1e-6
+    g = 1.0 - 0.8 * (2 * np.sin(np.pi / n) ** 2)
+    assert np.max(np.abs(u - (1.0 + 0.5 * g ** T * inputs.fourier_mode(n, n, 1, 1)))) < 2e-6
+
+
+def test_heat_kahan_zero_rate_and_compensation_identity(oracle_lib):
+    """r = 0 with no pending compensation leaves u and c unchanged; with r > 0
+    the stored pair satisfies the compensated-sum identities u' = u + y and
+    c' = (u' - u) - y at every point, y = delta - c, with the increment
+    recomputed in float32 by numpy."""
+    rng = np.random.default_rng(4)
+    u0 = rng.random((12, 10)).astype(np.float32)
+    c0 = (rng.standard_normal((12, 10)) * 1e-8).astype(np.float32)
+    u, c = oracle_lib.heat_kahan(u0, np.zeros_like(u0), 0.0, 5)
+    assert np.array_equal(u, u0) and np.all(c == 0)
+    u1, c1 = oracle_lib.heat_kahan(u0, c0, 0.2, 1)
+    f = np.float32
+    s = (np.roll(u0, -1, 1) + np.roll(u0, -1, 0)) + (np.roll(u0, 1, 1) + np.roll(u0, 1, 0))
+    d = (s.astype(np.float64) - 4.0 * u0.astype(np.float64)).astype(np.float32)   # fused: one rounding
+    y = f(0.2) * d - c0
+    assert np.array_equal(u1, u0 + y)
+    assert np.array_equal(c1, (u1 - u0) - y)
+
+
+def test_heat_kahan_bf16_storage_keeps_small_increments(oracle_lib):
+    """With bfloat16 storage (8-bit significand) the per-step increments of a
+    slow mode fall below half an ulp of u: uncompensated (numpy float32 update,
+    rounded to bfloat16 by the oracle's rounding) the field stagnates; with the
+    compensation it keeps following the FP64 solution to within a few times the
+    error of representing the initial field in bfloat16."""
+    n, T = 32, 300
+    x = np.arange(n)
+    u64 = np.tile(1.0 + 0.25 * np.cos(2 * np.pi * x / n), (n, 1))
+    ref = oracle_lib.heat(u64, 0.2, T)
+    bits = np.vectorize(lambda v: oracle_lib.f32_to_bf16(float(v)), otypes=[np.uint16])
+    tofl = np.vectorize(oracle_lib.bf16_to_f32, otypes=[np.float64])
+    u0 = bits(u64.astype(np.float32))
+    rep_err = np.max(np.abs(tofl(u0) - u64))
+    u, c = oracle_lib.heat_kahan(u0, np.zeros_like(u0), 0.2, T, storage="bf16")
+    err_kahan = np.max(np.abs(tofl(u) - ref))
+    plain = tofl(u0)
+    for _ in range(T):
+        s = (np.roll(plain, -1, 1) + np.roll(plain, -1, 0)) + (np.roll(plain, 1, 1) + np.roll(plain, 1, 0))
+        plain = tofl(bits((plain + 0.2 * (s - 4 * plain)).astype(np.float32)))
+    err_plain = np.max(np.abs(plain - ref))
+    assert np.max(np.abs(ref - 1.0)) < 0.25 * 0.2          # the mode really decayed
+    assert err_kahan < 3 * rep_err
+    assert err_plain > 10 * err_kahan
