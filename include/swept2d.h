@@ -89,7 +89,8 @@ typedef struct swept2d swept2d_t;
  * Create a handle for an nx x ny grid.
  *   tile   side n of the square tiles for the swept mode: even, >= 4, dividing
  *          nx and ny, and small enough that two (n+2)^2 x nvars level buffers
- *          fit in shared memory; 0 = naive mode only.
+ *          (plus one (n+2)^2 plane of pair sums for HEAT) fit in shared memory;
+ *          0 = naive mode only.
  *   params op parameters (see above); nparams their count.
  *   stream a cudaStream_t (NULL = legacy default stream).
  * Allocates the device state and, if tile > 0, two panel buffers of

@@ -230,7 +230,7 @@ int swept2d_create(swept2d_t **out, int nx, int ny, int nvars, int nstages, int 
             fail(h, 0, "tile must be even, >= 4 and divide nx and ny");
             return bail(SWEPT2D_EINVAL);
         }
-        const size_t sm = (size_t)2 * t->nv * (tile + 2) * (tile + 2) * t->esize;
+        const size_t sm = t->smem_bytes(tile);
         int dev = 0, optin = 0;
         cudaGetDevice(&dev);
         if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)

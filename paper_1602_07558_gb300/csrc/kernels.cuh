@@ -26,7 +26,8 @@
 // north <- S of x-bridge(I,J), south <- N of x-bridge(I,J+1).
 //
 // Shared memory per block: two level buffers (Algorithm 1's U and D), each NV
-// planes of (n+2) x (n+2) with the tile at offset (1, 1).
+// planes of (n+2) x (n+2) with the tile at offset (1, 1), plus Op::AUX planes of
+// the same shape for point updates that stage partial results (heat: pair sums).
 #pragma once
 #include <cuda_runtime.h>
 
@@ -44,6 +45,22 @@ struct Geom {
 __device__ __forceinline__ int wrap_add(int a, int d, int m) {
     int r = a + d;
     return r >= m ? r - m : (r < 0 ? r + m : r);
+}
+
+// Asynchronous global -> shared copy of one element (cp.async, no register
+// staging) so that the next level's panel loads overlap the current level's
+// arithmetic; async_wait() waits for this thread's copies (a __syncthreads()
+// afterwards publishes them to the block).
+template <class S>
+__device__ __forceinline__ void async_copy(S *smem_dst, const S *gmem_src) {
+    static_assert(sizeof(S) == 4 || sizeof(S) == 8 || sizeof(S) == 16, "cp.async size");
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gmem_src),
+                 "n"((int)sizeof(S)));
+}
+__device__ __forceinline__ void async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void async_wait() {
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
 // Neighbourhood accessor into a shared-memory level buffer; p points at the
@@ -75,7 +92,8 @@ struct GlobalAcc {
 template <class Op>
 __device__ __forceinline__ void compute_rect(const Op &op, int stage, u64 g,
                                              const typename Op::S *src, typename Op::S *dst,
-                                             int P, int x0, int y0, int W, int H) {
+                                             typename Op::S * /*aux*/, int P, int x0, int y0,
+                                             int W, int H) {
     typedef typename Op::S S;
     const int plane = P * P, cnt = W * H;
     for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
@@ -86,6 +104,32 @@ __device__ __forceinline__ void compute_rect(const Op &op, int stage, u64 g,
         op(stage, g, acc, out);
 #pragma unroll
         for (int v = 0; v < Op::NV; ++v) dst[v * plane + off] = out[v];
+    }
+}
+
+// Heat: the east+south pair sum Pr(x, y) = u(x+1, y) + u(x, y+1) of a point is
+// the west+north pair sum of its south-east neighbour (x+1, y+1), so it is
+// formed once for [x0-1, x0+W) x [y0-1, y0+H) into the aux buffer (pass 1),
+// and each point then needs s = Pr(x, y) + Pr(x-1, y-1) and two fused
+// multiply-adds (pass 2): about 4.1 FP64 operations per point instead of 5,
+// with the same roundings as HeatOp::operator() (the pair sums commute).
+__device__ __forceinline__ void compute_rect(const HeatOp &op, int, u64, const double *src,
+                                             double *dst, double *aux, int P, int x0, int y0,
+                                             int W, int H) {
+    const int W1 = W + 1, cnt1 = W1 * (H + 1);
+    for (int e = threadIdx.x; e < cnt1; e += blockDim.x) {
+        const int yy = e / W1, xx = e - yy * W1;
+        const int off = (y0 + yy) * P + (x0 + xx);      // point (x0-1+xx, y0-1+yy)
+        aux[off] = __dadd_rn(src[off + 1], src[off + P]);
+    }
+    __syncthreads();
+    const int cnt = W * H;
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+        const int yy = e / W, xx = e - yy * W;
+        const int off = (y0 + yy + 1) * P + (x0 + xx + 1);
+        const double c = src[off];
+        const double sum = __dadd_rn(aux[off], aux[off - P - 1]);
+        dst[off] = __fma_rn(op.r, __fma_rn(-4.0, c, sum), c);
     }
 }
 
@@ -133,13 +177,48 @@ __global__ void __launch_bounds__(256) naive_kernel(Op op, Geom G, const typenam
     for (int v = 0; v < Op::NV; ++v) out[v * plane + p] = res[v];
 }
 
+// Heat, naive path: each warp walks down a chunk of 31 columns over ROWS rows
+// (32 on large grids, fewer on small ones so that enough warps run); lane l
+// holds column x = 31 c + l - 1 (lane 0 only supplies the pair sum
+// of the column to the left). The east+south pair sum of row y-1 moves one lane
+// to the right with a shuffle and is the west+north pair sum at row y, so a
+// point costs about 4.1 FP64 operations, with the roundings of HeatOp.
+template <int ROWS>
+__global__ void __launch_bounds__(256) naive_heat_kernel(HeatOp op, Geom G, const double *in,
+                                                         double *out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int x = blockIdx.x * 31 + lane - 1;
+    if (x < 0) x += G.nx;
+    const bool active = lane > 0 && x < G.nx;
+    if (x >= G.nx) x %= G.nx;            // idle lanes read valid memory, store nothing
+    const int xe = x + 1 == G.nx ? 0 : x + 1;
+    const int y0 = (blockIdx.y * 8 + warp) * ROWS;
+    if (y0 >= G.ny) return;               // whole warp leaves together
+    const int y1 = min(y0 + ROWS, G.ny);
+    const size_t nx = G.nx;
+    int ym = y0 - 1;
+    if (ym < 0) ym += G.ny;
+    double c = in[(size_t)y0 * nx + x];
+    double pp = __dadd_rn(in[(size_t)ym * nx + xe], c);   // Pr(x, y0-1)
+    for (int y = y0; y < y1; ++y) {
+        const int ys = y + 1 == G.ny ? 0 : y + 1;
+        const double sd = in[(size_t)ys * nx + x];
+        const double pc = __dadd_rn(in[(size_t)y * nx + xe], sd);   // Pr(x, y)
+        const double q = __shfl_up_sync(0xffffffffu, pp, 1);         // Pr(x-1, y-1)
+        const double res = __fma_rn(op.r, __fma_rn(-4.0, c, __dadd_rn(pc, q)), c);
+        if (active) out[(size_t)y * nx + x] = res;
+        pp = pc;
+        c = sd;
+    }
+}
+
 // ------------------------------------------------------- UpwardPyramid (Alg. 1)
 // Shared body: tile at level 0 of half cycle g0 is in buffer 0; builds levels
 // 1..h-1 and writes the up panels of levels 0..h-1 to slot `slot`.
 template <class Op>
 __device__ __forceinline__ void up_body(const Op &op, const Geom &G, typename Op::S *buf0,
-                                        typename Op::S *buf1, int P, u64 g0, typename Op::S *up,
-                                        int slot, int first_parity) {
+                                        typename Op::S *buf1, typename Op::S *aux, int P, u64 g0,
+                                        typename Op::S *up, int slot, int first_parity) {
     typedef typename Op::S S;
     const int n = G.n, h = n / 2;
     for (int k = 0; k < h; ++k) {
@@ -149,8 +228,8 @@ __device__ __forceinline__ void up_body(const Op &op, const Geom &G, typename Op
         write_up_panels<S, Op::NV>(cur, P, G, k, up, slot);
         if (k + 1 < h) {
             const u64 g = g0 + k;
-            compute_rect(op, (int)(g % Op::NST), g, cur, nxt, P, k + 1, k + 1, n - 2 * k - 2,
-                         n - 2 * k - 2);
+            compute_rect(op, (int)(g % Op::NST), g, cur, nxt, aux, P, k + 1, k + 1,
+                         n - 2 * k - 2, n - 2 * k - 2);
         }
         __syncthreads();
     }
@@ -165,6 +244,7 @@ __global__ void __launch_bounds__(256) up_kernel(Op op, Geom G, const typename O
     const int n = G.n, P = n + 2, plane = P * P;
     S *buf0 = reinterpret_cast<S *>(smem_raw);
     S *buf1 = buf0 + Op::NV * plane;
+    S *aux = buf1 + Op::NV * plane;
     const int I = blockIdx.x, J = blockIdx.y;
     const size_t gplane = (size_t)G.nx * G.ny;
     const int x0 = o + I * n, y0 = o + J * n;
@@ -177,7 +257,7 @@ __global__ void __launch_bounds__(256) up_kernel(Op op, Geom G, const typename O
             buf0[v * plane + (b + 1) * P + (a + 1)] = state[v * gplane + (size_t)y * G.nx + x];
     }
     __syncthreads();
-    up_body(op, G, buf0, buf1, P, g0, up, J * G.T + I, 0);
+    up_body(op, G, buf0, buf1, aux, P, g0, up, J * G.T + I, 0);
 }
 
 // ------------------------------------------- Bridges (Algorithms 2 and 3)
@@ -196,6 +276,7 @@ __global__ void __launch_bounds__(256) bridge_kernel(Op op, Geom G, const typena
     S *bufs[2];
     bufs[0] = reinterpret_cast<S *>(smem_raw);
     bufs[1] = bufs[0] + NV * plane;
+    S *aux = bufs[1] + NV * plane;
     const int I = blockIdx.x, J = blockIdx.y;
     const bool xb = blockIdx.z == 1;
     const int slot = J * G.T + I;
@@ -222,10 +303,13 @@ __global__ void __launch_bounds__(256) bridge_kernel(Op op, Geom G, const typena
             const S *src = up + ((size_t)(which ? hi_slot : slot) * 4 + (which ? hi_side : lo_side)) * NV * G.PS +
                            off + d * L + p;
 #pragma unroll
-            for (int v = 0; v < NV; ++v) dst[v * plane + (y + 1) * P + (x + 1)] = src[(size_t)v * G.PS];
+            for (int v = 0; v < NV; ++v)
+                async_copy(dst + v * plane + (y + 1) * P + (x + 1), src + (size_t)v * G.PS);
         }
+        async_commit();
     };
     load_strips(0, bufs[0]);
+    async_wait();
     __syncthreads();
     for (int k = 0; k < h; ++k) {
         S *cur = bufs[k & 1];
@@ -249,9 +333,10 @@ __global__ void __launch_bounds__(256) bridge_kernel(Op op, Geom G, const typena
             const u64 g = g0 + k;
             const int u0 = k + 1, uw = n - 2 * k - 2, w0 = h - k - 1, ww = 2 * k + 2;
             if (xb)
-                compute_rect(op, (int)(g % Op::NST), g, cur, nxt, P, w0, u0, ww, uw);
+                compute_rect(op, (int)(g % Op::NST), g, cur, nxt, aux, P, w0, u0, ww, uw);
             else
-                compute_rect(op, (int)(g % Op::NST), g, cur, nxt, P, u0, w0, uw, ww);
+                compute_rect(op, (int)(g % Op::NST), g, cur, nxt, aux, P, u0, w0, uw, ww);
+            async_wait();
         }
         __syncthreads();
     }
@@ -262,8 +347,8 @@ __global__ void __launch_bounds__(256) bridge_kernel(Op op, Geom G, const typena
 // panels. Ends with the full tile at level h in buffer (h & 1).
 template <class Op>
 __device__ __forceinline__ void down_body(const Op &op, const Geom &G, typename Op::S *buf0,
-                                          typename Op::S *buf1, int P, const typename Op::S *br,
-                                          u64 g0) {
+                                          typename Op::S *buf1, typename Op::S *aux, int P,
+                                          const typename Op::S *br, u64 g0) {
     typedef typename Op::S S;
     constexpr int NV = Op::NV;
     const int n = G.n, h = n / 2, plane = P * P;
@@ -289,18 +374,22 @@ __device__ __forceinline__ void down_body(const Op &op, const Geom &G, typename 
             }
             const S *src = br + ((size_t)src_slot * 4 + src_side) * NV * G.PS + off + d * L + p;
 #pragma unroll
-            for (int v = 0; v < NV; ++v) dst[v * plane + (y + 1) * P + (x + 1)] = src[(size_t)v * G.PS];
+            for (int v = 0; v < NV; ++v)
+                async_copy(dst + v * plane + (y + 1) * P + (x + 1), src + (size_t)v * G.PS);
         }
+        async_commit();
     };
     load_ring(0, buf0);
+    async_wait();
     __syncthreads();
     for (int k = 0; k < h; ++k) {
         S *cur = (k & 1) ? buf1 : buf0;
         S *nxt = (k & 1) ? buf0 : buf1;
         if (k + 1 < h) load_ring(k + 1, nxt);   // disjoint from the square computed below
         const u64 g = g0 + k;
-        compute_rect(op, (int)(g % Op::NST), g, cur, nxt, P, h - k - 1, h - k - 1, 2 * k + 2,
-                     2 * k + 2);
+        compute_rect(op, (int)(g % Op::NST), g, cur, nxt, aux, P, h - k - 1, h - k - 1,
+                     2 * k + 2, 2 * k + 2);
+        async_wait();
         __syncthreads();
     }
 }
@@ -315,7 +404,8 @@ __global__ void __launch_bounds__(256) octahedron_kernel(Op op, Geom G, const ty
     const int n = G.n, h = n / 2, P = n + 2, plane = P * P;
     S *buf0 = reinterpret_cast<S *>(smem_raw);
     S *buf1 = buf0 + Op::NV * plane;
-    down_body(op, G, buf0, buf1, P, br, g0);
+    S *aux = buf1 + Op::NV * plane;
+    down_body(op, G, buf0, buf1, aux, P, br, g0);
     // Down(I,J) in frame o+h is Up(I,J) of frame h when o = 0, and Up(I+1,J+1)
     // of frame 0 when o = h.
     int I = blockIdx.x, J = blockIdx.y;
@@ -323,7 +413,7 @@ __global__ void __launch_bounds__(256) octahedron_kernel(Op op, Geom G, const ty
         I = I + 1 == G.T ? 0 : I + 1;
         J = J + 1 == G.Q ? 0 : J + 1;
     }
-    up_body(op, G, buf0, buf1, P, g0 + h, up, J * G.T + I, h & 1);
+    up_body(op, G, buf0, buf1, aux, P, g0 + h, up, J * G.T + I, h & 1);
 }
 
 // K4: final Down of an advance; writes the tile at level h to the state.
@@ -335,7 +425,8 @@ __global__ void __launch_bounds__(256) down_kernel(Op op, Geom G, const typename
     const int n = G.n, h = n / 2, P = n + 2, plane = P * P;
     S *buf0 = reinterpret_cast<S *>(smem_raw);
     S *buf1 = buf0 + Op::NV * plane;
-    down_body(op, G, buf0, buf1, P, br, g0);
+    S *aux = buf1 + Op::NV * plane;
+    down_body(op, G, buf0, buf1, aux, P, br, g0);
     const S *fin = (h & 1) ? buf1 : buf0;
     const size_t gplane = (size_t)G.nx * G.ny;
     const int x0 = o + h + blockIdx.x * n, y0 = o + h + blockIdx.y * n;

@@ -2,6 +2,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "kernels.cuh"
 
 namespace swept {
@@ -9,6 +11,7 @@ namespace swept {
 // Function table of one point update (filled in by an instantiation unit).
 struct OpTable {
     int nv, nst, esize;
+    size_t (*smem_bytes)(int n);   // dynamic shared memory of a swept block with tile n
     cudaError_t (*naive)(const Geom &, const double *c, const void *in, void *out, u64 g,
                          cudaStream_t);
     cudaError_t (*up)(const Geom &, const double *c, const void *state, void *up, int o, u64 g0,
@@ -25,7 +28,7 @@ constexpr int kBlock = 256;
 
 template <class Op>
 inline size_t swept_smem_bytes(int n) {
-    return (size_t)2 * Op::NV * (n + 2) * (n + 2) * sizeof(typename Op::S);
+    return (size_t)(2 * Op::NV + Op::AUX) * (n + 2) * (n + 2) * sizeof(typename Op::S);
 }
 
 // Raise the dynamic shared-memory limit of a kernel when it needs more than
@@ -41,8 +44,26 @@ struct Launch {
     typedef typename Op::S S;
     static cudaError_t naive(const Geom &G, const double *c, const void *in, void *out, u64 g,
                              cudaStream_t st) {
-        dim3 grid((G.nx + 31) / 32, (G.ny + 7) / 8);
-        naive_kernel<Op><<<grid, kBlock, 0, st>>>(Op(c), G, (const S *)in, (S *)out, g);
+        if constexpr (std::is_same<Op, HeatOp>::value) {
+            // rows per warp: as many as keep about 32 warps per SM in flight
+            const long long chunks = (G.nx + 30) / 31;
+            int rows = 32;
+            while (rows > 1 && chunks * ((G.ny + rows - 1) / rows) < 152LL * 32) rows >>= 1;
+            const int warps = (G.ny + rows - 1) / rows;
+            dim3 grid((unsigned)chunks, (warps + 7) / 8);
+            const Op op(c);
+            switch (rows) {
+                case 32: naive_heat_kernel<32><<<grid, kBlock, 0, st>>>(op, G, (const S *)in, (S *)out); break;
+                case 16: naive_heat_kernel<16><<<grid, kBlock, 0, st>>>(op, G, (const S *)in, (S *)out); break;
+                case 8: naive_heat_kernel<8><<<grid, kBlock, 0, st>>>(op, G, (const S *)in, (S *)out); break;
+                case 4: naive_heat_kernel<4><<<grid, kBlock, 0, st>>>(op, G, (const S *)in, (S *)out); break;
+                case 2: naive_heat_kernel<2><<<grid, kBlock, 0, st>>>(op, G, (const S *)in, (S *)out); break;
+                default: naive_heat_kernel<1><<<grid, kBlock, 0, st>>>(op, G, (const S *)in, (S *)out); break;
+            }
+        } else {
+            dim3 grid((G.nx + 31) / 32, (G.ny + 7) / 8);
+            naive_kernel<Op><<<grid, kBlock, 0, st>>>(Op(c), G, (const S *)in, (S *)out, g);
+        }
         return cudaGetLastError();
     }
     static cudaError_t up(const Geom &G, const double *c, const void *state, void *up, int o,
@@ -82,8 +103,8 @@ struct Launch {
         return cudaGetLastError();
     }
     static const OpTable *table() {
-        static const OpTable t = {Op::NV, Op::NST, (int)sizeof(S), &naive, &up, &bridge,
-                                  &octahedron, &down};
+        static const OpTable t = {Op::NV, Op::NST, (int)sizeof(S), &swept_smem_bytes<Op>,
+                                  &naive, &up, &bridge, &octahedron, &down};
         return &t;
     }
 };

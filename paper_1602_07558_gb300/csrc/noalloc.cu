@@ -99,7 +99,7 @@ extern "C" int swept2d_heat_advance_static(const double *u_in, double *u_out, in
         set_err(err, errlen, "u_in and u_out must not overlap");
         return SWEPT2D_EINVAL;
     }
-    const size_t smem = (size_t)2 * (tile + 2) * (tile + 2) * sizeof(double);
+    const size_t smem = swept::optable_heat()->smem_bytes(tile);
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)

@@ -23,7 +23,7 @@ namespace swept {
 // the same rounding of the same exact value (4u is exact for |u| < 2^1021).
 struct HeatOp {
     typedef double S;
-    static constexpr int NV = 1, NST = 1;
+    static constexpr int NV = 1, NST = 1, AUX = 1;
     double r;
     __host__ __device__ explicit HeatOp(const double *c) : r(c[0]) {}
     template <class A>
@@ -39,7 +39,7 @@ struct HeatOp {
 // Section 3.1 worked example: u' = u + 1.
 struct IncrementOp {
     typedef double S;
-    static constexpr int NV = 1, NST = 1;
+    static constexpr int NV = 1, NST = 1, AUX = 0;
     __host__ __device__ explicit IncrementOp(const double *) {}
     template <class A>
     __device__ __forceinline__ void operator()(int, u64, const A &a, S *out) const {
@@ -50,7 +50,7 @@ struct IncrementOp {
 // Test update: u' = u + 1 if all 9 neighbours hold the centre's level, else NaN.
 struct LevelTagOp {
     typedef double S;
-    static constexpr int NV = 1, NST = 1;
+    static constexpr int NV = 1, NST = 1, AUX = 0;
     __host__ __device__ explicit LevelTagOp(const double *) {}
     template <class A>
     __device__ __forceinline__ void operator()(int, u64, const A &a, S *out) const {
@@ -75,7 +75,7 @@ __device__ __forceinline__ u64 mix64(u64 z) {
 // neighbours in row order (north row west..east, own row, south row).
 struct HashOp {
     typedef u64 S;
-    static constexpr int NV = 1, NST = 1;
+    static constexpr int NV = 1, NST = 1, AUX = 0;
     __host__ __device__ explicit HashOp(const double *) {}
     template <class A>
     __device__ __forceinline__ void operator()(int, u64 g, const A &a, S *out) const {
@@ -93,7 +93,7 @@ struct HashOp {
 // u' = (west's 2nd + east's 3rd + north's 4th + south's 5th) - 4 (own 1st).
 struct Wide2Op {
     typedef u64 S;
-    static constexpr int NV = 5, NST = 2;
+    static constexpr int NV = 5, NST = 2, AUX = 0;
     __host__ __device__ explicit Wide2Op(const double *) {}
     template <class A>
     __device__ __forceinline__ void operator()(int stage, u64, const A &a, S *out) const {
@@ -121,7 +121,7 @@ struct Wide2Op {
 // Host-precomputed constants c[] = {gamma-1, cx, cy, kax, kay, tau0, tau1}.
 struct EulerOp {
     typedef double S;
-    static constexpr int NV = 8, NST = 2;
+    static constexpr int NV = 8, NST = 2, AUX = 0;
     double gm1, cx, cy, kax, kay, tau0, tau1;
     __host__ __device__ explicit EulerOp(const double *c)
         : gm1(c[0]), cx(c[1]), cy(c[2]), kax(c[3]), kay(c[4]), tau0(c[5]), tau1(c[6]) {}
