@@ -69,6 +69,13 @@ typedef struct swept2d swept2d_t;
  *  WIDE2      nvars 5, nstages 2, dtype U64: eq. (complex_step) run as its
  *             two radius-1 sub-steps, eqs. (substep1)-(substep2), modulo 2^64;
  *             plane 0 holds u after each whole step.
+ *  HEAT_KAHAN nvars 2, nstages 1, dtype F32 or BF16, params {r}: the heat
+ *             update in binary32 arithmetic with the time update accumulated
+ *             by Kahan's compensated summation; plane 0 = u, plane 1 = the
+ *             compensation c (start it at 0): delta = r ((u_E + u_S) + (u_W +
+ *             u_N) - 4u), y = delta - c, u' = store(u + y), c' = store((u' - u)
+ *             - y), store() = rounding to the storage type (none for F32).
+ *             r is rounded to binary32. u' - c' is the compensated value.
  */
 #define SWEPT2D_OP_HEAT       0
 #define SWEPT2D_OP_EULER_RK2  1
@@ -76,9 +83,12 @@ typedef struct swept2d swept2d_t;
 #define SWEPT2D_OP_HASH       3
 #define SWEPT2D_OP_LEVELTAG   4
 #define SWEPT2D_OP_WIDE2      5
+#define SWEPT2D_OP_HEAT_KAHAN 6
 
 /* Element types of the state. */
 #define SWEPT2D_F64  0
+#define SWEPT2D_F32  1
+#define SWEPT2D_BF16 2   /* bfloat16: the upper 16 bits of a binary32 */
 #define SWEPT2D_U64  3
 
 /* Advance modes. */
@@ -116,7 +126,9 @@ int swept2d_advance(swept2d_t *h, long long nsteps, int mode);
 
 /* Copy the state to dst (device memory if dst_is_device, else host memory),
  * after all work queued on the handle's stream; synchronises the stream.
- * Errors: EINVAL (NULL), ESTATE, ECUDA. */
+ * Errors: EINVAL (NULL), ESTATE, ECUDA, ETIMEOUT (a kernel's bounded wait for
+ * its panel copies gave up since the last set_state; the state is then
+ * unspecified). */
 int swept2d_get_state(swept2d_t *h, void *dst, int dst_is_device);
 
 /* Free all device memory of the handle and the handle itself (NULL is a no-op).
@@ -136,6 +148,15 @@ const char *swept2d_last_error(const swept2d_t *h);
 #define SWEPT2D_Q_PANEL_BYTES   5   /* bytes of one panel buffer (0 if naive-only) */
 #define SWEPT2D_Q_SMEM_BYTES    6   /* dynamic shared memory per swept block */
 int swept2d_query(const swept2d_t *h, int what, double *out);
+
+/* Launch shape of the swept kernels of a handle (a tuning knob, not a change
+ * of results: every setting gives the same bits). threads: 64, 128 or 256 per
+ * block (default 256). stage: 1 = the bridge and downward-pyramid blocks bring
+ * their whole input panel set into shared memory with TMA bulk copies at block
+ * start; 0 = they prefetch each level's strip with cp.async (default: 1 for
+ * HEAT_KAHAN, 0 otherwise, and 0 wherever the staged panels do not fit).
+ * Errors: EINVAL (bad value, naive-only handle, does not fit). */
+int swept2d_set_tuning(swept2d_t *h, int threads, int stage);
 
 /* Kernel timing: when on, every launch of the handle is bracketed by CUDA
  * events on the handle's stream. swept2d_kernel_stats synchronises the stream
@@ -176,7 +197,8 @@ int swept2d_measure_fp64_rate(void *stream, double *ops_per_s);
  * scratch is a static device array of SWEPT2D_STATIC_SCRATCH_BYTES in this
  * library, which every GPU that loads the library holds until the process
  * exits. It needs 2 * 4 * (n*n/2 + n) * 8 bytes per tile (the two panel
- * buffers) plus nx*ny*8 bytes when nsteps is not a multiple of n/2, each part
+ * buffers; n*n/2 + n rounded up to a multiple of 8) plus nx*ny*8 bytes when
+ * nsteps is not a multiple of n/2, each part
  * rounded up to 256 bytes; larger grids are rejected with SWEPT2D_EINVAL and a
  * message. Nothing in the scratch needs to start at zero.
  *

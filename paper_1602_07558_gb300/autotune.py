@@ -1,0 +1,81 @@
+"""Autotuner for the swept path's launch shape.
+
+For one grid and point update it times a short swept advance for every
+candidate tile side n (even, dividing nx and ny, fitting shared memory),
+threads per block and panel staging, and returns the fastest. All candidates
+give bitwise the same result, so the choice is purely about speed. The probe
+runs whole half cycles of every candidate tile (4 of the largest), timed with
+CUDA events on the given stream after one warm-up pass.
+
+The cost model of the paper (Section 4, eq. (cost): n^2 s + 4 tau / n per
+sub-step) predicts an optimum n* = (2 tau / s)^(1/3); here tau is a kernel
+boundary and s the time of one point update, and the measured table stands in
+for the model.
+"""
+from __future__ import annotations
+
+from .swept2d import Swept2D, SweptError
+
+
+def candidates(nx, ny, tiles=(16, 32, 64), threads=(64, 128, 256), stages=(False, True)):
+    for n in tiles:
+        if nx % n == 0 and ny % n == 0:
+            for t in threads:
+                for st in stages:
+                    yield n, t, st
+
+
+def autotune(nx, ny, op, params, dtype=None, state=None, stream=None, probe_steps=None,
+             tiles=(16, 32, 64), threads=(64, 128, 256), stages=(False, True)):
+    """Returns ((tile, threads, stage), table) with table a list of
+    {"tile", "threads", "stage", "ms", "gcell_per_s"} for every candidate that ran."""
+    import torch
+    table = []
+    valid = [n for n in tiles if nx % n == 0 and ny % n == 0]
+    if not valid:
+        raise ValueError("no candidate tile divides the grid")
+    nst = {"euler_rk2": 2, "wide2": 2}.get(op, 1)
+    if probe_steps is None:
+        probe_steps = max(4 * (max(valid) // 2) // nst, 8)
+    stream = stream or torch.cuda.current_stream()
+    for n in valid:
+        try:
+            s = Swept2D(nx, ny, op=op, tile=n, params=params, stream=stream, dtype=dtype)
+        except SweptError:
+            continue
+        with s:
+            for t in threads:
+                for st in stages:
+                    try:
+                        s.set_tuning(t, st)
+                    except SweptError:
+                        continue
+                    ev0 = torch.cuda.Event(enable_timing=True)
+                    ev1 = torch.cuda.Event(enable_timing=True)
+                    times = []
+                    for rep in range(2):
+                        with torch.cuda.stream(stream):
+                            if state is not None:
+                                s.set_state(state)
+                            else:
+                                s.set_state(torch.zeros(s.shape, device="cuda",
+                                                        dtype=_torch_dtype(s.np_dtype)))
+                            ev0.record(stream)
+                            s.advance(probe_steps)
+                            ev1.record(stream)
+                        ev1.synchronize()
+                        times.append(ev0.elapsed_time(ev1))
+                    ms = times[-1]
+                    table.append({"tile": n, "threads": t, "stage": bool(st), "ms": ms,
+                                  "gcell_per_s": nx * ny * probe_steps / (ms * 1e-3) / 1e9})
+    if not table:
+        raise RuntimeError("no candidate could run")
+    best = min(table, key=lambda r: r["ms"])
+    return (best["tile"], best["threads"], best["stage"]), table
+
+
+def _torch_dtype(np_dtype):
+    import numpy as np
+    import torch
+    return {np.dtype(np.float64): torch.float64, np.dtype(np.float32): torch.float32,
+            np.dtype(np.uint16): torch.int16, np.dtype(np.uint64): torch.int64}[np.dtype(np_dtype)]

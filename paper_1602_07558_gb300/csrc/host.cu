@@ -36,6 +36,8 @@ struct swept2d {
     cudaStream_t stream = nullptr;
     void *state = nullptr, *state2 = nullptr, *up = nullptr, *br = nullptr;
     unsigned long long *scratch8 = nullptr;
+    int *errword = nullptr;   // set by a kernel whose bounded wait gave up
+    swept::Tuning tune;
     size_t state_bytes = 0, panel_bytes = 0, smem_bytes = 0;
     double consts[8] = {0};
     double params[8] = {0};
@@ -120,8 +122,11 @@ int launch(swept2d *h, int kind, const char *what, F &&f) {
     return SWEPT2D_OK;
 }
 
-const OpTable *table_for(int op) {
+const OpTable *table_for(int op, int dtype) {
     switch (op) {
+        case SWEPT2D_OP_HEAT_KAHAN:
+            return dtype == SWEPT2D_F32 ? swept::optable_heat_kahan_f32()
+                 : dtype == SWEPT2D_BF16 ? swept::optable_heat_kahan_bf16() : nullptr;
         case SWEPT2D_OP_HEAT: return swept::optable_heat();
         case SWEPT2D_OP_EULER_RK2: return swept::optable_euler();
         case SWEPT2D_OP_INCREMENT: return swept::optable_increment();
@@ -132,8 +137,10 @@ const OpTable *table_for(int op) {
     }
 }
 
-int expected_dtype(int op) {
-    return (op == SWEPT2D_OP_HASH || op == SWEPT2D_OP_WIDE2) ? SWEPT2D_U64 : SWEPT2D_F64;
+bool dtype_ok(int op, int dtype) {
+    if (op == SWEPT2D_OP_HASH || op == SWEPT2D_OP_WIDE2) return dtype == SWEPT2D_U64;
+    if (op == SWEPT2D_OP_HEAT_KAHAN) return dtype == SWEPT2D_F32 || dtype == SWEPT2D_BF16;
+    return dtype == SWEPT2D_F64;
 }
 
 void free_all(swept2d *h) {
@@ -142,6 +149,7 @@ void free_all(swept2d *h) {
     if (h->up) cudaFree(h->up);
     if (h->br) cudaFree(h->br);
     if (h->scratch8) cudaFree(h->scratch8);
+    if (h->errword) cudaFree(h->errword);
     for (auto &t : h->timed) {
         cudaEventDestroy(t.start);
         cudaEventDestroy(t.stop);
@@ -149,6 +157,7 @@ void free_all(swept2d *h) {
     for (auto e : h->event_pool) cudaEventDestroy(e);
     h->state = h->state2 = h->up = h->br = nullptr;
     h->scratch8 = nullptr;
+    h->errword = nullptr;
 }
 
 int naive_substeps(swept2d *h, long long count) {
@@ -178,16 +187,19 @@ int swept_substeps(swept2d *h, long long total) {
             const u64 g0 = g_start + (u64)j * half;
             const int o = (j & 1) ? half : 0;
             rc = launch(h, SWEPT2D_K_BRIDGE, "bridge kernel", [&] {
-                return h->ops->bridge(h->G, h->consts, h->up, h->br, g0, h->stream);
+                return h->ops->bridge(h->G, h->consts, h->up, h->br, g0, h->errword, h->tune,
+                                      h->stream);
             });
             if (rc) return rc;
             if (j + 1 < H) {
                 rc = launch(h, SWEPT2D_K_OCTAHEDRON, "octahedron kernel", [&] {
-                    return h->ops->octahedron(h->G, h->consts, h->br, h->up, o, g0, h->stream);
+                    return h->ops->octahedron(h->G, h->consts, h->br, h->up, o, g0, h->errword,
+                                              h->tune, h->stream);
                 });
             } else {
                 rc = launch(h, SWEPT2D_K_DOWN, "down kernel", [&] {
-                    return h->ops->down(h->G, h->consts, h->br, h->state, o, g0, h->stream);
+                    return h->ops->down(h->G, h->consts, h->br, h->state, o, g0, h->errword,
+                                        h->tune, h->stream);
                 });
             }
             if (rc) return rc;
@@ -213,14 +225,15 @@ int swept2d_create(swept2d_t **out, int nx, int ny, int nvars, int nstages, int 
         delete h;
         return code;
     };
-    const OpTable *t = table_for(op);
-    if (!t) { fail(h, SWEPT2D_EINVAL, "unknown op"); return bail(SWEPT2D_EINVAL); }
+    if (op < 0 || op > SWEPT2D_OP_HEAT_KAHAN) { fail(h, 0, "unknown op"); return bail(SWEPT2D_EINVAL); }
+    if (!dtype_ok(op, dtype)) { fail(h, 0, "dtype does not match the op"); return bail(SWEPT2D_EINVAL); }
+    const OpTable *t = table_for(op, dtype);
+    if (!t) { fail(h, 0, "unknown op"); return bail(SWEPT2D_EINVAL); }
     if (nx < 1 || ny < 1) { fail(h, 0, "nx and ny must be >= 1"); return bail(SWEPT2D_EINVAL); }
     if (nvars != t->nv || nstages != t->nst) {
         fail(h, 0, "nvars/nstages do not match the op");
         return bail(SWEPT2D_EINVAL);
     }
-    if (dtype != expected_dtype(op)) { fail(h, 0, "dtype does not match the op"); return bail(SWEPT2D_EINVAL); }
     if (nparams < 0 || nparams > 8 || (nparams > 0 && !params)) {
         fail(h, 0, "bad params");
         return bail(SWEPT2D_EINVAL);
@@ -230,7 +243,7 @@ int swept2d_create(swept2d_t **out, int nx, int ny, int nvars, int nstages, int 
             fail(h, 0, "tile must be even, >= 4 and divide nx and ny");
             return bail(SWEPT2D_EINVAL);
         }
-        const size_t sm = t->smem_bytes(tile);
+        const size_t sm = t->smem_for(tile, false);
         int dev = 0, optin = 0;
         cudaGetDevice(&dev);
         if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
@@ -239,16 +252,23 @@ int swept2d_create(swept2d_t **out, int nx, int ny, int nvars, int nstages, int 
             fail(h, 0, "tile too large for shared memory");
             return bail(SWEPT2D_EINVAL);
         }
-        h->smem_bytes = sm;
+        h->smem_bytes = t->smem_for(tile, t->default_stage);
+        if (h->smem_bytes > (size_t)optin) {   // staging does not fit: prefetch per level
+            h->tune.stage = false;
+            h->smem_bytes = sm;
+        }
     }
     h->nx = nx; h->ny = ny; h->nv = nvars; h->nst = nstages; h->n = tile; h->op = op;
     h->dtype = dtype; h->esize = t->esize; h->ops = t;
+    h->tune.threads = 256;
+    h->tune.stage = t->default_stage;
     h->stream = (cudaStream_t)stream;
     h->nparams = nparams;
     for (int i = 0; i < nparams; ++i) h->params[i] = params[i];
     // op constants
     switch (op) {
         case SWEPT2D_OP_HEAT:
+        case SWEPT2D_OP_HEAT_KAHAN:
             if (nparams < 1) { fail(h, 0, "heat needs params {r}"); return bail(SWEPT2D_EINVAL); }
             h->consts[0] = params[0];
             break;
@@ -263,7 +283,7 @@ int swept2d_create(swept2d_t **out, int nx, int ny, int nvars, int nstages, int 
     }
     h->G.nx = nx; h->G.ny = ny; h->G.n = tile;
     h->G.T = tile ? nx / tile : 0; h->G.Q = tile ? ny / tile : 0;
-    h->G.PS = tile ? tile * tile / 2 + tile : 0;
+    h->G.PS = tile ? swept::panel_stride(tile) : 0;
     h->state_bytes = (size_t)nvars * nx * ny * t->esize;
     cudaError_t e;
     if ((e = cudaMalloc(&h->state, h->state_bytes)) != cudaSuccess ||
@@ -279,7 +299,9 @@ int swept2d_create(swept2d_t **out, int nx, int ny, int nvars, int nstages, int 
             return bail(e == cudaErrorMemoryAllocation ? SWEPT2D_ENOMEM : SWEPT2D_ECUDA);
         }
     }
-    if ((e = cudaMalloc(&h->scratch8, sizeof(unsigned long long))) != cudaSuccess) {
+    if ((e = cudaMalloc(&h->scratch8, sizeof(unsigned long long))) != cudaSuccess ||
+        (e = cudaMalloc(&h->errword, sizeof(int))) != cudaSuccess ||
+        (e = cudaMemset(h->errword, 0, sizeof(int))) != cudaSuccess) {
         cuda_fail(h, e, "scratch allocation");
         return bail(SWEPT2D_ECUDA);
     }
@@ -298,6 +320,8 @@ int swept2d_set_state(swept2d_t *h, const void *src, int src_is_device) {
     if (!src_is_device && (e = cudaStreamSynchronize(h->stream)) != cudaSuccess)
         return cuda_fail(h, e, "set_state sync");
     h->substeps = 0;
+    if ((e = cudaMemsetAsync(h->errword, 0, sizeof(int), h->stream)) != cudaSuccess)
+        return cuda_fail(h, e, "set_state error word");
     if (h->op == SWEPT2D_OP_EULER_RK2) {
         const double gamma = h->params[0], cfl = h->params[1], kappa = h->params[2];
         const double lx = h->nparams >= 5 ? h->params[3] : 1.0;
@@ -344,6 +368,10 @@ int swept2d_get_state(swept2d_t *h, void *dst, int dst_is_device) {
                                     h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "get_state copy");
     if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return cuda_fail(h, e, "get_state sync");
+    int flag = 0;
+    if ((e = cudaMemcpy(&flag, h->errword, sizeof flag, cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(h, e, "get_state error word");
+    if (flag) return fail(h, SWEPT2D_ETIMEOUT, "a kernel's bounded wait for its panel copies gave up; the state is unspecified");
     return SWEPT2D_OK;
 }
 
@@ -372,6 +400,23 @@ int swept2d_query(const swept2d_t *h, int what, double *out) {
         case SWEPT2D_Q_SMEM_BYTES: *out = (double)h->smem_bytes; break;
         default: return SWEPT2D_EINVAL;
     }
+    return SWEPT2D_OK;
+}
+
+int swept2d_set_tuning(swept2d_t *h, int threads, int stage) {
+    if (!h) return SWEPT2D_EINVAL;
+    if (threads != 64 && threads != 128 && threads != 256)
+        return fail(h, SWEPT2D_EINVAL, "set_tuning: threads must be 64, 128 or 256");
+    if (h->n == 0) return fail(h, SWEPT2D_EINVAL, "set_tuning: naive-only handle");
+    const size_t sm = h->ops->smem_for(h->n, stage != 0);
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        optin = 227 * 1024;
+    if (sm > (size_t)optin) return fail(h, SWEPT2D_EINVAL, "set_tuning: staged panels do not fit");
+    h->tune.threads = threads;
+    h->tune.stage = stage != 0;
+    h->smem_bytes = sm;
     return SWEPT2D_OK;
 }
 

@@ -10,7 +10,8 @@
 // The four counts (n-2t)^2 + 2 * 2t(n-2t) + (2t)^2 = n^2 partition each level.
 //
 // Panels (Section 3, "triangular sides"): per tile slot, side (N=0, S=1, W=2,
-// E=3) and value plane, a packed array of PS = n^2/2 + n elements holding the
+// E=3) and value plane, a packed array of n^2/2 + n elements (stride PS, padded
+// to 16 bytes) holding the
 // 2-wide edge strip of each level k = 0..h-1 as two lines (d = 0 outermost,
 // d = 1 inner) of L elements, line d at offset off(k) + d L:
 //   up panels     L = n - 2k,  off(k) = 2k(n-k+1)   (16, 12, 8, 4 for n = 8)
@@ -28,6 +29,10 @@
 // Shared memory per block: two level buffers (Algorithm 1's U and D), each NV
 // planes of (n+2) x (n+2) with the tile at offset (1, 1), plus Op::AUX planes of
 // the same shape for point updates that stage partial results (heat: pair sums).
+// With staging (template flag STG) a block also gets its whole input panel set
+// (every level) in shared memory, brought in by TMA bulk copies at block start
+// on one mbarrier, so the level loop touches no global memory for its inputs;
+// without it, the next level's panel strip is prefetched with cp.async.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -39,8 +44,29 @@ struct Geom {
     int nx, ny;   // grid
     int n;        // tile side
     int T, Q;     // tiles along x and y
-    int PS;       // panel elements per (slot, side, plane) = n*n/2 + n
+    int PS;       // panel stride per (slot, side, plane): n*n/2 + n rounded up to a
+                  // multiple of 8 elements, so every panel starts on 16 bytes
 };
+
+__host__ __device__ inline int panel_stride(int n) { return ((n * n / 2 + n) + 7) & ~7; }
+
+// Dynamic shared memory of a swept block: level buffers (+ aux planes), then
+// (when staged) the block's input panels, then an mbarrier.
+struct SmemPlan {
+    size_t stage_off, bar_off, total;
+};
+template <class Op>
+__host__ __device__ inline SmemPlan smem_plan(int n, int stage_segments, bool staged) {
+    typedef typename Op::S S;
+    const size_t P = (size_t)n + 2;
+    const size_t levels = (size_t)(2 * Op::NV + Op::AUX) * P * P * sizeof(S);
+    SmemPlan pl;
+    pl.stage_off = (levels + 15) & ~(size_t)15;
+    const size_t stage = staged ? (size_t)stage_segments * Op::NV * panel_stride(n) * sizeof(S) : 0;
+    pl.bar_off = (pl.stage_off + stage + 7) & ~(size_t)7;
+    pl.total = pl.bar_off + (staged && stage_segments ? 8 : 0);
+    return pl;
+}
 
 __device__ __forceinline__ int wrap_add(int a, int d, int m) {
     int r = a + d;
@@ -53,14 +79,79 @@ __device__ __forceinline__ int wrap_add(int a, int d, int m) {
 // afterwards publishes them to the block).
 template <class S>
 __device__ __forceinline__ void async_copy(S *smem_dst, const S *gmem_src) {
-    static_assert(sizeof(S) == 4 || sizeof(S) == 8 || sizeof(S) == 16, "cp.async size");
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gmem_src),
-                 "n"((int)sizeof(S)));
+    if constexpr (sizeof(S) == 4 || sizeof(S) == 8 || sizeof(S) == 16) {
+        const unsigned sa = (unsigned)__cvta_generic_to_shared(smem_dst);
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gmem_src),
+                     "n"((int)sizeof(S)));
+    } else {
+        *smem_dst = *gmem_src;       // 2-byte elements: cp.async has no 2-byte form
+    }
 }
 __device__ __forceinline__ void async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ __forceinline__ void async_wait() {
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+// ---- TMA bulk copies (global -> shared) completed on an mbarrier.
+// All waits are bounded: after kSpinLimit polls the block records a timeout in
+// the error word (if any) and gives up instead of hanging.
+constexpr long long kSpinLimit = 1LL << 22;
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes,
+                                         unsigned long long *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Every thread waits for phase 0 of `bar`; returns false (the same for the
+// whole block) if the wait gave up, after recording it in *err.
+__device__ __forceinline__ bool block_wait_bulk(unsigned long long *bar, int *err) {
+    bool ok = false;
+    for (long long it = 0; it < kSpinLimit && !ok; ++it) ok = mbar_try_wait(bar, 0);
+    const int bad = __syncthreads_or(!ok);
+    if (bad) {
+        if (threadIdx.x == 0) {
+            if (err) atomicExch(err, 1);
+            for (long long it = 0; it < kSpinLimit; ++it)   // let copies in flight land
+                if (mbar_try_wait(bar, 0)) break;
+        }
+        __syncthreads();
+        return false;
+    }
+    return true;
+}
+
+// q = floor(e / d) for 0 <= e < 2^20 and 1 <= d <= 2^10 via a binary32
+// reciprocal: (e + 1/2) / d is at least 1/(2d) away from an integer, far more
+// than the two roundings' error, so the truncation is exact. Saves the integer
+// division sequence in the per-point index arithmetic.
+__device__ __forceinline__ int div_small(int e, float rd) {
+    return (int)(((float)e + 0.5f) * rd);
 }
 
 // Neighbourhood accessor into a shared-memory level buffer; p points at the
@@ -74,15 +165,25 @@ struct SmemAcc {
     }
 };
 
-// Neighbourhood accessor into the global state with periodic wrap.
+// Neighbourhood accessor into the global state with periodic wrap; the three
+// wrapped rows and columns are formed once per point.
 template <class S>
 struct GlobalAcc {
     const S *base;
     size_t plane;
-    int nx, ny, x, y;
+    size_t row[3];
+    int col[3];
+    __device__ __forceinline__ GlobalAcc(const S *b, size_t pl, int nx, int ny, int x, int y)
+        : base(b), plane(pl) {
+        row[0] = (size_t)wrap_add(y, -1, ny) * nx;
+        row[1] = (size_t)y * nx;
+        row[2] = (size_t)wrap_add(y, 1, ny) * nx;
+        col[0] = wrap_add(x, -1, nx);
+        col[1] = x;
+        col[2] = wrap_add(x, 1, nx);
+    }
     __device__ __forceinline__ S operator()(int dx, int dy, int v) const {
-        const int xx = wrap_add(x, dx, nx), yy = wrap_add(y, dy, ny);
-        return base[v * plane + (size_t)yy * nx + xx];
+        return base[v * plane + row[dy + 1] + col[dx + 1]];
     }
 };
 
@@ -96,8 +197,9 @@ __device__ __forceinline__ void compute_rect(const Op &op, int stage, u64 g,
                                              int W, int H) {
     typedef typename Op::S S;
     const int plane = P * P, cnt = W * H;
+    const float rw = 1.0f / (float)W;
     for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
-        const int yy = e / W, xx = e - yy * W;
+        const int yy = div_small(e, rw), xx = e - yy * W;
         const int off = (y0 + yy + 1) * P + (x0 + xx + 1);
         SmemAcc<S> acc{src + off, P, plane};
         S out[Op::NV];
@@ -117,15 +219,16 @@ __device__ __forceinline__ void compute_rect(const HeatOp &op, int, u64, const d
                                              double *dst, double *aux, int P, int x0, int y0,
                                              int W, int H) {
     const int W1 = W + 1, cnt1 = W1 * (H + 1);
+    const float rw1 = 1.0f / (float)W1, rw = 1.0f / (float)W;
     for (int e = threadIdx.x; e < cnt1; e += blockDim.x) {
-        const int yy = e / W1, xx = e - yy * W1;
+        const int yy = div_small(e, rw1), xx = e - yy * W1;
         const int off = (y0 + yy) * P + (x0 + xx);      // point (x0-1+xx, y0-1+yy)
         aux[off] = __dadd_rn(src[off + 1], src[off + P]);
     }
     __syncthreads();
     const int cnt = W * H;
     for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
-        const int yy = e / W, xx = e - yy * W;
+        const int yy = div_small(e, rw), xx = e - yy * W;
         const int off = (y0 + yy + 1) * P + (x0 + xx + 1);
         const double c = src[off];
         const double sum = __dadd_rn(aux[off], aux[off - P - 1]);
@@ -149,8 +252,9 @@ __device__ __forceinline__ void write_up_panels(const S *cur, int P, const Geom 
                                                 S *up, int slot) {
     const int n = G.n, L = n - 2 * k, L2 = 2 * L, plane = P * P;
     const size_t off = (size_t)2 * k * (n - k + 1);
+    const float rl2 = 1.0f / (float)L2;
     for (int e = threadIdx.x; e < 4 * L2; e += blockDim.x) {
-        const int side = e / L2, r = e - side * L2, d = r >= L, p = r - d * L;
+        const int side = div_small(e, rl2), r = e - side * L2, d = r >= L, p = r - d * L;
         int a, b;
         up_panel_xy(side, n, k, d, p, a, b);
         S *dst = up + ((size_t)slot * 4 + side) * NV * G.PS + off + d * L + p;
@@ -169,7 +273,7 @@ __global__ void __launch_bounds__(256) naive_kernel(Op op, Geom G, const typenam
     const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
     if (x >= G.nx || y >= G.ny) return;
     const size_t plane = (size_t)G.nx * G.ny;
-    GlobalAcc<S> acc{in, plane, G.nx, G.ny, x, y};
+    GlobalAcc<S> acc(in, plane, G.nx, G.ny, x, y);
     S res[Op::NV];
     op((int)(g % Op::NST), g, acc, res);
     const size_t p = (size_t)y * G.nx + x;
@@ -266,9 +370,9 @@ __global__ void __launch_bounds__(256) up_kernel(Op op, Geom G, const typename O
 // and Up(I+1,J), frame (o+h, o). Both run levels 1..h-1 of half cycle g0.
 // In "along/across" coordinates (u along the bridge, w across it) the two are
 // the same; (x, y) = (u, w) for the y-bridge and (w, u) for the x-bridge.
-template <class Op>
+template <class Op, bool STG>
 __global__ void __launch_bounds__(256) bridge_kernel(Op op, Geom G, const typename Op::S *up,
-                                                     typename Op::S *br, u64 g0) {
+                                                     typename Op::S *br, u64 g0, int *err) {
     typedef typename Op::S S;
     constexpr int NV = Op::NV;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -290,26 +394,50 @@ __global__ void __launch_bounds__(256) bridge_kernel(Op op, Geom G, const typena
     // across-offset of each output line start: y-bridge W starts at h-k (south
     // corner), E at h-k-2 (north corner); x-bridge N at h-k-2 (west), S at h-k (east)
     const int lo_w_shift = xb ? -2 : 0, hi_w_shift = xb ? 0 : -2;
+    const S *seg[2] = {up + ((size_t)slot * 4 + lo_side) * NV * G.PS,
+                       up + ((size_t)hi_slot * 4 + hi_side) * NV * G.PS};
 
-    // prefetch the input strips of level 0 into buffer 0
+    const S *stg = nullptr;
+    if constexpr (STG) {
+        // the two input panels (every level) arrive in shared memory by TMA
+        const SmemPlan pl = smem_plan<Op>(n, 2, true);
+        S *st = reinterpret_cast<S *>(smem_raw + pl.stage_off);
+        unsigned long long *bar = reinterpret_cast<unsigned long long *>(smem_raw + pl.bar_off);
+        if (threadIdx.x == 0) mbar_init(bar, 1);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const unsigned bytes = (unsigned)(G.PS * sizeof(S));
+            mbar_expect_tx(bar, 2 * NV * bytes);
+            for (int w = 0; w < 2; ++w)
+                for (int v = 0; v < NV; ++v)
+                    bulk_g2s(st + (w * NV + v) * G.PS, seg[w] + (size_t)v * G.PS, bytes, bar);
+        }
+        if (!block_wait_bulk(bar, err)) return;
+        stg = st;
+    }
     auto load_strips = [&](int k, S *dst) {
         const int L = n - 2 * k, L2 = 2 * L;
-        const size_t off = (size_t)2 * k * (n - k + 1);
+        const int off = 2 * k * (n - k + 1);
         for (int e = threadIdx.x; e < 2 * L2; e += blockDim.x) {
             const int which = e >= L2, r = e - which * L2, d = r >= L, p = r - d * L;
             const int uu = k + p;
             const int ww = which ? h + k + d : h - 1 - k - d;
             const int x = xb ? ww : uu, y = xb ? uu : ww;
-            const S *src = up + ((size_t)(which ? hi_slot : slot) * 4 + (which ? hi_side : lo_side)) * NV * G.PS +
-                           off + d * L + p;
+            S *dd = dst + (y + 1) * P + (x + 1);
+            if constexpr (STG) {
+                const S *src = stg + which * NV * G.PS + off + d * L + p;
 #pragma unroll
-            for (int v = 0; v < NV; ++v)
-                async_copy(dst + v * plane + (y + 1) * P + (x + 1), src + (size_t)v * G.PS);
+                for (int v = 0; v < NV; ++v) dd[v * plane] = src[v * G.PS];
+            } else {
+                const S *src = seg[which] + off + d * L + p;
+#pragma unroll
+                for (int v = 0; v < NV; ++v) async_copy(dd + v * plane, src + (size_t)v * G.PS);
+            }
         }
-        async_commit();
+        if constexpr (!STG) async_commit();
     };
     load_strips(0, bufs[0]);
-    async_wait();
+    if constexpr (!STG) async_wait();
     __syncthreads();
     for (int k = 0; k < h; ++k) {
         S *cur = bufs[k & 1];
@@ -336,7 +464,7 @@ __global__ void __launch_bounds__(256) bridge_kernel(Op op, Geom G, const typena
                 compute_rect(op, (int)(g % Op::NST), g, cur, nxt, aux, P, w0, u0, ww, uw);
             else
                 compute_rect(op, (int)(g % Op::NST), g, cur, nxt, aux, P, u0, w0, uw, ww);
-            async_wait();
+            if constexpr (!STG) async_wait();
         }
         __syncthreads();
     }
@@ -345,10 +473,11 @@ __global__ void __launch_bounds__(256) bridge_kernel(Op op, Geom G, const typena
 // --------------------------------------------- DownwardPyramid (Algorithm 5)
 // Down(I,J) in frame (o+h, o+h): levels 1..h of half cycle g0 from the bridge
 // panels. Ends with the full tile at level h in buffer (h & 1).
-template <class Op>
-__device__ __forceinline__ void down_body(const Op &op, const Geom &G, typename Op::S *buf0,
-                                          typename Op::S *buf1, typename Op::S *aux, int P,
-                                          const typename Op::S *br, u64 g0) {
+template <class Op, bool STG>
+__device__ __forceinline__ bool down_body(const Op &op, const Geom &G, unsigned char *smem_raw,
+                                          typename Op::S *buf0, typename Op::S *buf1,
+                                          typename Op::S *aux, int P, const typename Op::S *br,
+                                          u64 g0, int *err) {
     typedef typename Op::S S;
     constexpr int NV = Op::NV;
     const int n = G.n, h = n / 2, plane = P * P;
@@ -356,31 +485,55 @@ __device__ __forceinline__ void down_body(const Op &op, const Geom &G, typename 
     const int slot = J * G.T + I;
     const int east = J * G.T + (I + 1 == G.T ? 0 : I + 1);
     const int south = (J + 1 == G.Q ? 0 : J + 1) * G.T + I;
+    // ring side -> (source slot, source panel side): west <- E of y-bridge(I,J),
+    // east <- W of y-bridge(I+1,J), north <- S of x-bridge(I,J), south <- N of x-bridge(I,J+1)
+    const S *seg[4] = {br + ((size_t)slot * 4 + 3) * NV * G.PS, br + ((size_t)east * 4 + 2) * NV * G.PS,
+                       br + ((size_t)slot * 4 + 1) * NV * G.PS, br + ((size_t)south * 4 + 0) * NV * G.PS};
+    const S *stg = nullptr;
+    if constexpr (STG) {
+        const SmemPlan pl = smem_plan<Op>(n, 4, true);
+        S *st = reinterpret_cast<S *>(smem_raw + pl.stage_off);
+        unsigned long long *bar = reinterpret_cast<unsigned long long *>(smem_raw + pl.bar_off);
+        if (threadIdx.x == 0) mbar_init(bar, 1);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const unsigned bytes = (unsigned)(G.PS * sizeof(S));
+            mbar_expect_tx(bar, 4 * NV * bytes);
+            for (int side = 0; side < 4; ++side)
+                for (int v = 0; v < NV; ++v)
+                    bulk_g2s(st + (side * NV + v) * G.PS, seg[side] + (size_t)v * G.PS, bytes, bar);
+        }
+        if (!block_wait_bulk(bar, err)) return false;
+        stg = st;
+    }
     auto load_ring = [&](int k, S *dst) {
         const int L = 2 * k + 2, L2 = 2 * L;
-        const size_t off = (size_t)2 * k * (k + 1);
+        const int off = 2 * k * (k + 1);
+        const float rl2 = 1.0f / (float)L2;
         for (int e = threadIdx.x; e < 4 * L2; e += blockDim.x) {
-            const int side = e / L2, r = e - side * L2, d = r >= L, p = r - d * L;
-            int x, y, src_slot, src_side;
+            const int side = div_small(e, rl2), r = e - side * L2, d = r >= L, p = r - d * L;
+            int x, y;
             switch (side) {
-                case 0:  // west side <- E panel of y-bridge(I,J)
-                    x = h - 1 - k - d; y = h - k - 2 + p; src_slot = slot; src_side = 3; break;
-                case 1:  // east side <- W panel of y-bridge(I+1,J)
-                    x = h + k + d; y = h - k + p; src_slot = east; src_side = 2; break;
-                case 2:  // north side <- S panel of x-bridge(I,J)
-                    x = h - k + p; y = h - 1 - k - d; src_slot = slot; src_side = 1; break;
-                default:  // south side <- N panel of x-bridge(I,J+1)
-                    x = h - k - 2 + p; y = h + k + d; src_slot = south; src_side = 0; break;
+                case 0: x = h - 1 - k - d; y = h - k - 2 + p; break;   // west
+                case 1: x = h + k + d; y = h - k + p; break;           // east
+                case 2: x = h - k + p; y = h - 1 - k - d; break;       // north
+                default: x = h - k - 2 + p; y = h + k + d; break;      // south
             }
-            const S *src = br + ((size_t)src_slot * 4 + src_side) * NV * G.PS + off + d * L + p;
+            S *dd = dst + (y + 1) * P + (x + 1);
+            if constexpr (STG) {
+                const S *src = stg + side * NV * G.PS + off + d * L + p;
 #pragma unroll
-            for (int v = 0; v < NV; ++v)
-                async_copy(dst + v * plane + (y + 1) * P + (x + 1), src + (size_t)v * G.PS);
+                for (int v = 0; v < NV; ++v) dd[v * plane] = src[v * G.PS];
+            } else {
+                const S *src = seg[side] + off + d * L + p;
+#pragma unroll
+                for (int v = 0; v < NV; ++v) async_copy(dd + v * plane, src + (size_t)v * G.PS);
+            }
         }
-        async_commit();
+        if constexpr (!STG) async_commit();
     };
     load_ring(0, buf0);
-    async_wait();
+    if constexpr (!STG) async_wait();
     __syncthreads();
     for (int k = 0; k < h; ++k) {
         S *cur = (k & 1) ? buf1 : buf0;
@@ -389,23 +542,25 @@ __device__ __forceinline__ void down_body(const Op &op, const Geom &G, typename 
         const u64 g = g0 + k;
         compute_rect(op, (int)(g % Op::NST), g, cur, nxt, aux, P, h - k - 1, h - k - 1,
                      2 * k + 2, 2 * k + 2);
-        async_wait();
+        if constexpr (!STG) async_wait();
         __syncthreads();
     }
+    return true;
 }
 
 // K3: octahedron = Down of half cycle g0 (frame o+h) fused with the Up of half
 // cycle g0+h in the same tile and frame; writes the next up panels.
-template <class Op>
+template <class Op, bool STG>
 __global__ void __launch_bounds__(256) octahedron_kernel(Op op, Geom G, const typename Op::S *br,
-                                                         typename Op::S *up, int o, u64 g0) {
+                                                         typename Op::S *up, int o, u64 g0,
+                                                         int *err) {
     typedef typename Op::S S;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = G.n, h = n / 2, P = n + 2, plane = P * P;
     S *buf0 = reinterpret_cast<S *>(smem_raw);
     S *buf1 = buf0 + Op::NV * plane;
     S *aux = buf1 + Op::NV * plane;
-    down_body(op, G, buf0, buf1, aux, P, br, g0);
+    if (!down_body<Op, STG>(op, G, smem_raw, buf0, buf1, aux, P, br, g0, err)) return;
     // Down(I,J) in frame o+h is Up(I,J) of frame h when o = 0, and Up(I+1,J+1)
     // of frame 0 when o = h.
     int I = blockIdx.x, J = blockIdx.y;
@@ -417,16 +572,16 @@ __global__ void __launch_bounds__(256) octahedron_kernel(Op op, Geom G, const ty
 }
 
 // K4: final Down of an advance; writes the tile at level h to the state.
-template <class Op>
+template <class Op, bool STG>
 __global__ void __launch_bounds__(256) down_kernel(Op op, Geom G, const typename Op::S *br,
-                                                   typename Op::S *state, int o, u64 g0) {
+                                                   typename Op::S *state, int o, u64 g0, int *err) {
     typedef typename Op::S S;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = G.n, h = n / 2, P = n + 2, plane = P * P;
     S *buf0 = reinterpret_cast<S *>(smem_raw);
     S *buf1 = buf0 + Op::NV * plane;
     S *aux = buf1 + Op::NV * plane;
-    down_body(op, G, buf0, buf1, aux, P, br, g0);
+    if (!down_body<Op, STG>(op, G, smem_raw, buf0, buf1, aux, P, br, g0, err)) return;
     const S *fin = (h & 1) ? buf1 : buf0;
     const size_t gplane = (size_t)G.nx * G.ny;
     const int x0 = o + h + blockIdx.x * n, y0 = o + h + blockIdx.y * n;

@@ -8,28 +8,48 @@
 
 namespace swept {
 
+// Launch shape of the swept kernels: threads per block (64, 128 or 256) and
+// whether the bridge and downward-pyramid blocks stage their input panels in
+// shared memory by TMA (else they prefetch each level with cp.async).
+struct Tuning {
+    int threads = 256;
+    bool stage = false;
+};
+
 // Function table of one point update (filled in by an instantiation unit).
 struct OpTable {
     int nv, nst, esize;
-    size_t (*smem_bytes)(int n);   // dynamic shared memory of a swept block with tile n
+    size_t (*smem_bytes)(int n);   // largest dynamic shared memory of a swept block, tile n
     cudaError_t (*naive)(const Geom &, const double *c, const void *in, void *out, u64 g,
                          cudaStream_t);
     cudaError_t (*up)(const Geom &, const double *c, const void *state, void *up, int o, u64 g0,
                       cudaStream_t);
+    // err: device word set to nonzero if a bounded wait gave up (may be NULL);
+    // tn: launch shape (threads per block, panel staging)
     cudaError_t (*bridge)(const Geom &, const double *c, const void *up, void *br, u64 g0,
-                          cudaStream_t);
+                          int *err, const Tuning &tn, cudaStream_t);
     cudaError_t (*octahedron)(const Geom &, const double *c, const void *br, void *up, int o,
-                              u64 g0, cudaStream_t);
+                              u64 g0, int *err, const Tuning &tn, cudaStream_t);
     cudaError_t (*down)(const Geom &, const double *c, const void *br, void *state, int o, u64 g0,
-                        cudaStream_t);
+                        int *err, const Tuning &tn, cudaStream_t);
+    bool default_stage;
+    size_t (*smem_for)(int n, bool stage);   // largest swept block's shared memory
 };
 
 constexpr int kBlock = 256;
 
+// Dynamic shared memory of each swept kernel: the up kernel stages nothing,
+// the bridge stages 2 input panels, the octahedron and the final down 4.
 template <class Op>
-inline size_t swept_smem_bytes(int n) {
-    return (size_t)(2 * Op::NV + Op::AUX) * (n + 2) * (n + 2) * sizeof(typename Op::S);
-}
+inline size_t up_smem(int n) { return smem_plan<Op>(n, 0, false).total; }
+template <class Op>
+inline size_t bridge_smem(int n, bool stage) { return smem_plan<Op>(n, 2, stage).total; }
+template <class Op>
+inline size_t down_smem(int n, bool stage) { return smem_plan<Op>(n, 4, stage).total; }
+template <class Op>
+inline size_t swept_smem_bytes(int n) { return down_smem<Op>(n, Op::STAGE); }
+template <class Op>
+inline size_t swept_smem_for(int n, bool stage) { return down_smem<Op>(n, stage); }
 
 // Raise the dynamic shared-memory limit of a kernel when it needs more than
 // the default 48 KB (the attribute is per kernel and per device).
@@ -68,43 +88,62 @@ struct Launch {
     }
     static cudaError_t up(const Geom &G, const double *c, const void *state, void *up, int o,
                           u64 g0, cudaStream_t st) {
-        const size_t sm = swept_smem_bytes<Op>(G.n);
+        const size_t sm = up_smem<Op>(G.n);
         cudaError_t e = allow_smem(up_kernel<Op>, sm);
         if (e != cudaSuccess) return e;
         up_kernel<Op><<<dim3(G.T, G.Q), kBlock, sm, st>>>(Op(c), G, (const S *)state, (S *)up, o,
                                                           g0);
         return cudaGetLastError();
     }
-    static cudaError_t bridge(const Geom &G, const double *c, const void *up, void *br, u64 g0,
-                              cudaStream_t st) {
-        const size_t sm = swept_smem_bytes<Op>(G.n);
-        cudaError_t e = allow_smem(bridge_kernel<Op>, sm);
+    template <bool STG>
+    static cudaError_t bridge_t(const Geom &G, const double *c, const void *up, void *br, u64 g0,
+                                int *err, int threads, cudaStream_t st) {
+        const size_t sm = bridge_smem<Op>(G.n, STG);
+        cudaError_t e = allow_smem(bridge_kernel<Op, STG>, sm);
         if (e != cudaSuccess) return e;
-        bridge_kernel<Op><<<dim3(G.T, G.Q, 2), kBlock, sm, st>>>(Op(c), G, (const S *)up, (S *)br,
-                                                                 g0);
+        bridge_kernel<Op, STG><<<dim3(G.T, G.Q, 2), threads, sm, st>>>(Op(c), G, (const S *)up,
+                                                                       (S *)br, g0, err);
+        return cudaGetLastError();
+    }
+    static cudaError_t bridge(const Geom &G, const double *c, const void *up, void *br, u64 g0,
+                              int *err, const Tuning &tn, cudaStream_t st) {
+        return tn.stage ? bridge_t<true>(G, c, up, br, g0, err, tn.threads, st)
+                        : bridge_t<false>(G, c, up, br, g0, err, tn.threads, st);
+    }
+    template <bool STG>
+    static cudaError_t octahedron_t(const Geom &G, const double *c, const void *br, void *up,
+                                    int o, u64 g0, int *err, int threads, cudaStream_t st) {
+        const size_t sm = down_smem<Op>(G.n, STG);
+        cudaError_t e = allow_smem(octahedron_kernel<Op, STG>, sm);
+        if (e != cudaSuccess) return e;
+        octahedron_kernel<Op, STG><<<dim3(G.T, G.Q), threads, sm, st>>>(Op(c), G, (const S *)br,
+                                                                        (S *)up, o, g0, err);
         return cudaGetLastError();
     }
     static cudaError_t octahedron(const Geom &G, const double *c, const void *br, void *up, int o,
-                                  u64 g0, cudaStream_t st) {
-        const size_t sm = swept_smem_bytes<Op>(G.n);
-        cudaError_t e = allow_smem(octahedron_kernel<Op>, sm);
+                                  u64 g0, int *err, const Tuning &tn, cudaStream_t st) {
+        return tn.stage ? octahedron_t<true>(G, c, br, up, o, g0, err, tn.threads, st)
+                        : octahedron_t<false>(G, c, br, up, o, g0, err, tn.threads, st);
+    }
+    template <bool STG>
+    static cudaError_t down_t(const Geom &G, const double *c, const void *br, void *state, int o,
+                              u64 g0, int *err, int threads, cudaStream_t st) {
+        const size_t sm = down_smem<Op>(G.n, STG);
+        cudaError_t e = allow_smem(down_kernel<Op, STG>, sm);
         if (e != cudaSuccess) return e;
-        octahedron_kernel<Op><<<dim3(G.T, G.Q), kBlock, sm, st>>>(Op(c), G, (const S *)br,
-                                                                  (S *)up, o, g0);
+        down_kernel<Op, STG><<<dim3(G.T, G.Q), threads, sm, st>>>(Op(c), G, (const S *)br,
+                                                                  (S *)state, o, g0, err);
         return cudaGetLastError();
     }
     static cudaError_t down(const Geom &G, const double *c, const void *br, void *state, int o,
-                            u64 g0, cudaStream_t st) {
-        const size_t sm = swept_smem_bytes<Op>(G.n);
-        cudaError_t e = allow_smem(down_kernel<Op>, sm);
-        if (e != cudaSuccess) return e;
-        down_kernel<Op><<<dim3(G.T, G.Q), kBlock, sm, st>>>(Op(c), G, (const S *)br, (S *)state,
-                                                            o, g0);
-        return cudaGetLastError();
+                            u64 g0, int *err, const Tuning &tn, cudaStream_t st) {
+        return tn.stage ? down_t<true>(G, c, br, state, o, g0, err, tn.threads, st)
+                        : down_t<false>(G, c, br, state, o, g0, err, tn.threads, st);
     }
     static const OpTable *table() {
-        static const OpTable t = {Op::NV, Op::NST, (int)sizeof(S), &swept_smem_bytes<Op>,
-                                  &naive, &up, &bridge, &octahedron, &down};
+        static const OpTable t = {Op::NV,      Op::NST,     (int)sizeof(S), &swept_smem_bytes<Op>,
+                                  &naive,      &up,         &bridge,        &octahedron,
+                                  &down,       Op::STAGE,   &swept_smem_for<Op>};
         return &t;
     }
 };
@@ -116,6 +155,8 @@ const OpTable *optable_increment();
 const OpTable *optable_hash();
 const OpTable *optable_leveltag();
 const OpTable *optable_wide2();
+const OpTable *optable_heat_kahan_f32();
+const OpTable *optable_heat_kahan_bf16();
 
 // Euler helpers (euler.cu): the max wave speed of planes 0-3 of a state.
 cudaError_t euler_wavespeed(const double *state, int nx, int ny, double gamma,

@@ -99,7 +99,7 @@ extern "C" int swept2d_heat_advance_static(const double *u_in, double *u_out, in
         set_err(err, errlen, "u_in and u_out must not overlap");
         return SWEPT2D_EINVAL;
     }
-    const size_t smem = swept::optable_heat()->smem_bytes(tile);
+    const size_t smem = swept::optable_heat()->smem_for(tile, false);
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
@@ -111,7 +111,7 @@ extern "C" int swept2d_heat_advance_static(const double *u_in, double *u_out, in
     swept::Geom G;
     G.nx = nx; G.ny = ny; G.n = tile;
     G.T = nx / tile; G.Q = ny / tile;
-    G.PS = tile * tile / 2 + tile;
+    G.PS = swept::panel_stride(tile);
     const size_t panel_bytes = (size_t)G.T * G.Q * 4 * G.PS * sizeof(double);
     const int half = tile / 2;
     const long long H = nsteps / half, rem = nsteps - H * half;
@@ -134,6 +134,7 @@ extern "C" int swept2d_heat_advance_static(const double *u_in, double *u_out, in
 
     const swept::OpTable *t = swept::optable_heat();
     const double consts[8] = {r, 0, 0, 0, 0, 0, 0, 0};
+    const swept::Tuning tn;   // 256 threads, per-level prefetch (the handle path's heat default)
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = cudaSuccess;
     auto check = [&](cudaError_t ce, const char *what) {
@@ -164,12 +165,12 @@ extern "C" int swept2d_heat_advance_static(const double *u_in, double *u_out, in
     for (long long j = 0; j < H; ++j) {
         const u64 g0 = (u64)j * half;
         const int o = (j & 1) ? half : 0;
-        if (!check(t->bridge(G, consts, up, br, g0, st), "bridge kernel")) return SWEPT2D_ECUDA;
+        if (!check(t->bridge(G, consts, up, br, g0, nullptr, tn, st), "bridge kernel")) return SWEPT2D_ECUDA;
         if (j + 1 < H) {
-            if (!check(t->octahedron(G, consts, br, up, o, g0, st), "octahedron kernel"))
+            if (!check(t->octahedron(G, consts, br, up, o, g0, nullptr, tn, st), "octahedron kernel"))
                 return SWEPT2D_ECUDA;
         } else {
-            if (!check(t->down(G, consts, br, swept_dst, o, g0, st), "down kernel"))
+            if (!check(t->down(G, consts, br, swept_dst, o, g0, nullptr, tn, st), "down kernel"))
                 return SWEPT2D_ECUDA;
         }
     }

@@ -1,0 +1,8 @@
+// Instantiation unit: heat with binary32 arithmetic and Kahan-compensated time
+// accumulation, state stored in binary32 or in bfloat16.
+#include "launch.cuh"
+
+namespace swept {
+const OpTable *optable_heat_kahan_f32() { return Launch<HeatKahanOp<float>>::table(); }
+const OpTable *optable_heat_kahan_bf16() { return Launch<HeatKahanOp<__nv_bfloat16>>::table(); }
+}  // namespace swept

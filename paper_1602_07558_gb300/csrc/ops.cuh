@@ -4,6 +4,8 @@
 //   S        storage element type of one state value
 //   NV       values per point (the vector point state of Section 2, item 2)
 //   NST      sub-steps (stages) per time step
+//   AUX      extra shared-memory planes the update's level computation uses
+//   STAGE    stage the block's input panels in shared memory by TMA
 //   operator()(stage, g, a, out): a(dx, dy, v) reads value v of the neighbour at
 //            offset (dx, dy) in {-1,0,1}^2 at the level below; out[0..NV) is the
 //            new point state; g is the global sub-step index.
@@ -12,6 +14,8 @@
 // produce identical bits. All floating-point operations are written with
 // explicit round-to-nearest intrinsics, so no contraction can change them.
 #pragma once
+#include <cuda_bf16.h>
+
 #include <cstdint>
 
 typedef unsigned long long u64;
@@ -24,6 +28,7 @@ namespace swept {
 struct HeatOp {
     typedef double S;
     static constexpr int NV = 1, NST = 1, AUX = 1;
+    static constexpr bool STAGE = false;
     double r;
     __host__ __device__ explicit HeatOp(const double *c) : r(c[0]) {}
     template <class A>
@@ -36,10 +41,51 @@ struct HeatOp {
     }
 };
 
+// Storage <-> binary32 conversions of the reduced-precision forms.
+template <class S>
+struct Store;
+template <>
+struct Store<float> {
+    __device__ static __forceinline__ float ld(float v) { return v; }
+    __device__ static __forceinline__ float st(float v) { return v; }
+};
+template <>
+struct Store<__nv_bfloat16> {
+    __device__ static __forceinline__ float ld(__nv_bfloat16 v) { return __bfloat162float(v); }
+    __device__ static __forceinline__ __nv_bfloat16 st(float v) { return __float2bfloat16_rn(v); }
+};
+
+// Heat in binary32 arithmetic with the time update accumulated by Kahan's
+// compensated summation; point state (u, c) stored as SS (float or bfloat16):
+//   delta = r ((u_E + u_S) + (u_W + u_N) - 4u)   (the difference fused)
+//   y = delta - c;  t = u + y;  u' = store(t);  c' = store((u' - u) - y)
+// Neighbours read the stored u. r is rounded to binary32 on the host.
+template <class SS>
+struct HeatKahanOp {
+    typedef SS S;
+    static constexpr int NV = 2, NST = 1, AUX = 0;
+    static constexpr bool STAGE = true;
+    float r;
+    __host__ __device__ explicit HeatKahanOp(const double *c) : r((float)c[0]) {}
+    template <class A>
+    __device__ __forceinline__ void operator()(int, u64, const A &a, S *out) const {
+        typedef Store<S> St;
+        const float uc = St::ld(a(0, 0, 0)), cc = St::ld(a(0, 0, 1));
+        const float pe = __fadd_rn(St::ld(a(1, 0, 0)), St::ld(a(0, 1, 0)));
+        const float pw = __fadd_rn(St::ld(a(-1, 0, 0)), St::ld(a(0, -1, 0)));
+        const float d = __fmaf_rn(-4.0f, uc, __fadd_rn(pe, pw));
+        const float y = __fsub_rn(__fmul_rn(r, d), cc);
+        const S un = St::st(__fadd_rn(uc, y));
+        out[0] = un;
+        out[1] = St::st(__fsub_rn(__fsub_rn(St::ld(un), uc), y));
+    }
+};
+
 // Section 3.1 worked example: u' = u + 1.
 struct IncrementOp {
     typedef double S;
     static constexpr int NV = 1, NST = 1, AUX = 0;
+    static constexpr bool STAGE = false;
     __host__ __device__ explicit IncrementOp(const double *) {}
     template <class A>
     __device__ __forceinline__ void operator()(int, u64, const A &a, S *out) const {
@@ -51,6 +97,7 @@ struct IncrementOp {
 struct LevelTagOp {
     typedef double S;
     static constexpr int NV = 1, NST = 1, AUX = 0;
+    static constexpr bool STAGE = false;
     __host__ __device__ explicit LevelTagOp(const double *) {}
     template <class A>
     __device__ __forceinline__ void operator()(int, u64, const A &a, S *out) const {
@@ -76,6 +123,7 @@ __device__ __forceinline__ u64 mix64(u64 z) {
 struct HashOp {
     typedef u64 S;
     static constexpr int NV = 1, NST = 1, AUX = 0;
+    static constexpr bool STAGE = false;
     __host__ __device__ explicit HashOp(const double *) {}
     template <class A>
     __device__ __forceinline__ void operator()(int, u64 g, const A &a, S *out) const {
@@ -94,6 +142,7 @@ struct HashOp {
 struct Wide2Op {
     typedef u64 S;
     static constexpr int NV = 5, NST = 2, AUX = 0;
+    static constexpr bool STAGE = false;
     __host__ __device__ explicit Wide2Op(const double *) {}
     template <class A>
     __device__ __forceinline__ void operator()(int stage, u64, const A &a, S *out) const {
@@ -122,6 +171,7 @@ struct Wide2Op {
 struct EulerOp {
     typedef double S;
     static constexpr int NV = 8, NST = 2, AUX = 0;
+    static constexpr bool STAGE = false;
     double gm1, cx, cy, kax, kay, tau0, tau1;
     __host__ __device__ explicit EulerOp(const double *c)
         : gm1(c[0]), cx(c[1]), cy(c[2]), kax(c[3]), kay(c[4]), tau0(c[5]), tau1(c[6]) {}

@@ -21,15 +21,20 @@ import numpy as np
 from . import build as _build
 
 OK, EINVAL, ECUDA, ENOMEM, ETIMEOUT, ESTATE = 0, -1, -2, -3, -4, -5
-OPS = {"heat": 0, "euler_rk2": 1, "increment": 2, "hash": 3, "leveltag": 4, "wide2": 5}
-# (nvars, nstages, dtype code, numpy dtype) of each point update
+OPS = {"heat": 0, "euler_rk2": 1, "increment": 2, "hash": 3, "leveltag": 4, "wide2": 5,
+       "heat_kahan": 6}
+DTYPES = {"f64": (0, np.float64), "f32": (1, np.float32), "bf16": (2, np.uint16),
+          "u64": (3, np.uint64)}
+# (nvars, nstages, default dtype) of each point update; bf16 states are passed
+# as uint16 arrays of bfloat16 bits (or torch.bfloat16 tensors)
 OP_SHAPE = {
-    "heat": (1, 1, 0, np.float64),
-    "euler_rk2": (8, 2, 0, np.float64),
-    "increment": (1, 1, 0, np.float64),
-    "hash": (1, 1, 3, np.uint64),
-    "leveltag": (1, 1, 0, np.float64),
-    "wide2": (5, 2, 3, np.uint64),
+    "heat": (1, 1, "f64"),
+    "euler_rk2": (8, 2, "f64"),
+    "increment": (1, 1, "f64"),
+    "hash": (1, 1, "u64"),
+    "leveltag": (1, 1, "f64"),
+    "wide2": (5, 2, "u64"),
+    "heat_kahan": (2, 1, "f32"),
 }
 MODES = {"swept": 0, "naive": 1}
 Q = {"dt": 0, "wavespeed": 1, "substeps": 2, "launches": 3, "state_bytes": 4,
@@ -65,11 +70,13 @@ def lib():
         L.swept2d_last_error.restype = ctypes.c_char_p
         L.swept2d_query.argtypes = [vp, i, ctypes.POINTER(d)]
         L.swept2d_set_timing.argtypes = [vp, i]
+        L.swept2d_set_tuning.argtypes = [vp, i, i]
         L.swept2d_kernel_stats.argtypes = [vp, i, ctypes.POINTER(ll), ctypes.POINTER(d)]
         L.swept2d_measure_fp64_rate.argtypes = [vp, ctypes.POINTER(d)]
         for name in ("swept2d_create", "swept2d_set_state", "swept2d_advance",
                      "swept2d_get_state", "swept2d_destroy", "swept2d_query",
-                     "swept2d_set_timing", "swept2d_kernel_stats", "swept2d_measure_fp64_rate"):
+                     "swept2d_set_timing", "swept2d_kernel_stats", "swept2d_measure_fp64_rate",
+                     "swept2d_set_tuning"):
             getattr(L, name).restype = i
         _lib = L
         return L
@@ -116,11 +123,15 @@ def measure_fp64_rate(stream=None) -> float:
 class Swept2D:
     """One periodic nx x ny grid advanced by the swept rule (or the naive path)."""
 
-    def __init__(self, nx, ny, op="heat", tile=0, params=(), stream=None):
+    def __init__(self, nx, ny, op="heat", tile=0, params=(), stream=None, dtype=None):
         if op not in OPS:
             raise ValueError(f"unknown op {op!r}; one of {sorted(OPS)}")
         self.nx, self.ny, self.op, self.tile = int(nx), int(ny), op, int(tile)
-        self.nvars, self.nstages, self._dtype_code, self.np_dtype = OP_SHAPE[op]
+        self.nvars, self.nstages, default = OP_SHAPE[op]
+        self.dtype = dtype or default
+        if self.dtype not in DTYPES:
+            raise ValueError(f"unknown dtype {dtype!r}; one of {sorted(DTYPES)}")
+        self._dtype_code, self.np_dtype = DTYPES[self.dtype]
         self.params = tuple(float(p) for p in params)
         self._stream = _stream_handle(stream)
         self._h = ctypes.c_void_p()
@@ -162,6 +173,10 @@ class Swept2D:
         v = ctypes.c_double()
         self._check(lib().swept2d_query(self._h, Q[what], ctypes.byref(v)))
         return v.value
+
+    def set_tuning(self, threads=256, stage=False):
+        """Launch shape of the swept kernels (same results for every setting)."""
+        self._check(lib().swept2d_set_tuning(self._h, int(threads), 1 if stage else 0))
 
     def set_timing(self, on=True):
         self._check(lib().swept2d_set_timing(self._h, 1 if on else 0))

@@ -21,9 +21,9 @@ if not torch.cuda.is_available():  # pragma: no cover
 GAMMA, CFL, KAPPA = 1.4, 0.3, 0.5
 
 
-def run(op, u0, nsteps, tile, mode, params=(), chunks=None):
+def run(op, u0, nsteps, tile, mode, params=(), chunks=None, dtype=None):
     ny, nx = u0.shape[-2:]
-    with Swept2D(nx, ny, op=op, tile=tile, params=params) as s:
+    with Swept2D(nx, ny, op=op, tile=tile, params=params, dtype=dtype) as s:
         s.set_state(np.ascontiguousarray(u0.reshape(s.shape)))
         for c in (chunks or [nsteps]):
             s.advance(c, mode=mode)
@@ -140,6 +140,75 @@ def test_euler_swept_equals_naive_and_oracle(oracle_lib, nx, ny, tile, nsteps):
     denom = max(np.max(np.abs(ref)), np.max(np.abs(U)))
     assert np.max(np.abs(swept[:4] - ref)) / denom <= 1e-12
     assert np.array_equal(swept[:4], ref)      # same operations in the same order
+
+
+# ------------------------------------------- reduced-precision forms (bitwise)
+
+def _to_bf16_bits(a):
+    """binary32 -> bfloat16 bits with torch's conversion (round to nearest even)."""
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(torch.bfloat16) \
+        .view(torch.int16).numpy().view(np.uint16)
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+@pytest.mark.parametrize("nx,ny,tile,nsteps", [
+    (96, 64, 32, 77), (64, 64, 16, 40), (32, 48, 8, 23), (128, 64, 64, 70),
+])
+def test_heat_kahan_swept_equals_naive_and_oracle(oracle_lib, storage, nx, ny, tile, nsteps):
+    """Binary32 arithmetic, Kahan-compensated update, binary32 or bfloat16
+    storage: u and c bit for bit the oracle's, swept == naive."""
+    u32 = inputs.uniform(nx, ny, seed=nx + tile).astype(np.float32)
+    u0 = u32 if storage == "f32" else _to_bf16_bits(u32)
+    c0 = np.zeros_like(u0)
+    ref_u, ref_c = oracle_lib.heat_kahan(u0, c0, 0.2, nsteps, storage=storage)
+    state = np.stack([u0, c0])
+    swept = run("heat_kahan", state, nsteps, tile, "swept", (0.2,), dtype=storage)
+    naive = run("heat_kahan", state, nsteps, tile, "naive", (0.2,), dtype=storage)
+    assert np.array_equal(swept, naive)
+    assert np.array_equal(swept[0], ref_u)
+    assert np.array_equal(swept[1], ref_c)
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_heat_kahan_2048_full_grid_matches_oracle(oracle_lib, storage):
+    """The precision workload's grid and tile (2048 x 2048, n = 32), 3 half
+    cycles and a tail, every point of u and c against the oracle."""
+    u32 = inputs.smooth_field(2048, 2048, seed=1).astype(np.float32)
+    u0 = u32 if storage == "f32" else _to_bf16_bits(u32)
+    c0 = np.zeros_like(u0)
+    ref_u, ref_c = oracle_lib.heat_kahan(u0, c0, 0.2, 53, storage=storage)
+    got = run("heat_kahan", np.stack([u0, c0]), 53, 32, "swept", (0.2,), dtype=storage)
+    assert np.array_equal(got[0], ref_u) and np.array_equal(got[1], ref_c)
+
+
+# ------------------------------------------------- launch shape never matters
+
+@pytest.mark.parametrize("op,dtype,params", [
+    ("heat", "f64", (0.2,)), ("heat_kahan", "f32", (0.2,)), ("heat_kahan", "bf16", (0.2,)),
+    ("hash", "u64", ()), ("wide2", "u64", ()),
+])
+@pytest.mark.parametrize("threads,stage", [(64, False), (128, True), (256, True), (256, False)])
+def test_tuning_gives_identical_bits(op, dtype, params, threads, stage):
+    """Threads per block and TMA panel staging change the schedule, never the
+    result: every setting equals the naive path bit for bit."""
+    nx, ny, tile, nsteps = 64, 48, 16, 37
+    rng = np.random.default_rng(threads + stage)
+    shape = {"heat": 1, "heat_kahan": 2, "hash": 1, "wide2": 5}[op]
+    if dtype == "f64":
+        u0 = rng.random((shape, ny, nx))
+    elif dtype == "f32":
+        u0 = np.stack([rng.random((ny, nx)), np.zeros((ny, nx))]).astype(np.float32)
+    elif dtype == "bf16":
+        u0 = np.stack([_to_bf16_bits(rng.random((ny, nx))), np.zeros((ny, nx), np.uint16)])
+    else:
+        u0 = rng.integers(0, 2**64, size=(shape, ny, nx), dtype=np.uint64)
+    naive = run(op, u0, nsteps, tile, "naive", params, dtype=dtype)
+    with Swept2D(nx, ny, op=op, tile=tile, params=params, dtype=dtype) as s:
+        s.set_tuning(threads, stage)
+        s.set_state(np.ascontiguousarray(u0))
+        s.advance(nsteps)
+        got = s.get_state()
+    assert np.array_equal(got, naive)
 
 
 # ------------------------------------------------------ full-size sampled check
