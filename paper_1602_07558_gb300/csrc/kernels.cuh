@@ -146,13 +146,28 @@ __device__ __forceinline__ bool block_wait_bulk(unsigned long long *bar, int *er
     return true;
 }
 
-// q = floor(e / d) for 0 <= e < 2^20 and 1 <= d <= 2^10 via a binary32
-// reciprocal: (e + 1/2) / d is at least 1/(2d) away from an integer, far more
-// than the two roundings' error, so the truncation is exact. Saves the integer
-// division sequence in the per-point index arithmetic.
-__device__ __forceinline__ int div_small(int e, float rd) {
-    return (int)(((float)e + 0.5f) * rd);
-}
+// Threads take consecutive points of a W-wide rectangle (point e = t, t + T,
+// t + 2T, ... in row order, T = blockDim), so warps stay full; the (column,
+// row) of the next point follows by adding (T mod W, T div W) with a carry,
+// so a level costs two integer divisions per thread, not one per point.
+struct LinearWalk {
+    int xx, yy, dq, dr;
+    __device__ __forceinline__ explicit LinearWalk(int W) {
+        const int T = blockDim.x;
+        yy = (int)threadIdx.x / W;
+        xx = (int)threadIdx.x - yy * W;
+        dq = T / W;
+        dr = T - dq * W;
+    }
+    __device__ __forceinline__ void next(int W) {
+        xx += dr;
+        yy += dq;
+        if (xx >= W) {
+            xx -= W;
+            ++yy;
+        }
+    }
+};
 
 // Neighbourhood accessor into a shared-memory level buffer; p points at the
 // centre point in plane 0.
@@ -196,11 +211,10 @@ __device__ __forceinline__ void compute_rect(const Op &op, int stage, u64 g,
                                              typename Op::S * /*aux*/, int P, int x0, int y0,
                                              int W, int H) {
     typedef typename Op::S S;
-    const int plane = P * P, cnt = W * H;
-    const float rw = 1.0f / (float)W;
-    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
-        const int yy = div_small(e, rw), xx = e - yy * W;
-        const int off = (y0 + yy + 1) * P + (x0 + xx + 1);
+    const int plane = P * P;
+    if (W <= 0) return;
+    for (LinearWalk w(W); w.yy < H; w.next(W)) {
+        const int off = (y0 + w.yy + 1) * P + (x0 + w.xx + 1);
         SmemAcc<S> acc{src + off, P, plane};
         S out[Op::NV];
         op(stage, g, acc, out);
@@ -218,18 +232,14 @@ __device__ __forceinline__ void compute_rect(const Op &op, int stage, u64 g,
 __device__ __forceinline__ void compute_rect(const HeatOp &op, int, u64, const double *src,
                                              double *dst, double *aux, int P, int x0, int y0,
                                              int W, int H) {
-    const int W1 = W + 1, cnt1 = W1 * (H + 1);
-    const float rw1 = 1.0f / (float)W1, rw = 1.0f / (float)W;
-    for (int e = threadIdx.x; e < cnt1; e += blockDim.x) {
-        const int yy = div_small(e, rw1), xx = e - yy * W1;
-        const int off = (y0 + yy) * P + (x0 + xx);      // point (x0-1+xx, y0-1+yy)
+    for (LinearWalk w(W + 1); w.yy <= H; w.next(W + 1)) {
+        const int off = (y0 + w.yy) * P + (x0 + w.xx);    // point (x0-1+xx, y0-1+yy)
         aux[off] = __dadd_rn(src[off + 1], src[off + P]);
     }
     __syncthreads();
-    const int cnt = W * H;
-    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
-        const int yy = div_small(e, rw), xx = e - yy * W;
-        const int off = (y0 + yy + 1) * P + (x0 + xx + 1);
+    if (W <= 0) return;
+    for (LinearWalk w(W); w.yy < H; w.next(W)) {
+        const int off = (y0 + w.yy + 1) * P + (x0 + w.xx + 1);
         const double c = src[off];
         const double sum = __dadd_rn(aux[off], aux[off - P - 1]);
         dst[off] = __fma_rn(op.r, __fma_rn(-4.0, c, sum), c);
@@ -250,16 +260,18 @@ __device__ __forceinline__ void up_panel_xy(int side, int n, int k, int d, int p
 template <class S, int NV>
 __device__ __forceinline__ void write_up_panels(const S *cur, int P, const Geom &G, int k,
                                                 S *up, int slot) {
-    const int n = G.n, L = n - 2 * k, L2 = 2 * L, plane = P * P;
-    const size_t off = (size_t)2 * k * (n - k + 1);
-    const float rl2 = 1.0f / (float)L2;
-    for (int e = threadIdx.x; e < 4 * L2; e += blockDim.x) {
-        const int side = div_small(e, rl2), r = e - side * L2, d = r >= L, p = r - d * L;
-        int a, b;
-        up_panel_xy(side, n, k, d, p, a, b);
-        S *dst = up + ((size_t)slot * 4 + side) * NV * G.PS + off + d * L + p;
+    const int n = G.n, L = n - 2 * k, plane = P * P;
+    const int off = 2 * k * (n - k + 1);
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int line = threadIdx.x >> 5; line < 8; line += nw) {   // 4 sides x 2 lines
+        const int side = line >> 1, d = line & 1;
+        S *dst = up + ((size_t)slot * 4 + side) * NV * G.PS + off + d * L;
+        for (int p = lane; p < L; p += 32) {
+            int a, b;
+            up_panel_xy(side, n, k, d, p, a, b);
 #pragma unroll
-        for (int v = 0; v < NV; ++v) dst[(size_t)v * G.PS] = cur[v * plane + (b + 1) * P + (a + 1)];
+            for (int v = 0; v < NV; ++v) dst[(size_t)v * G.PS + p] = cur[v * plane + (b + 1) * P + (a + 1)];
+        }
     }
 }
 
@@ -313,6 +325,32 @@ __global__ void __launch_bounds__(256) naive_heat_kernel(HeatOp op, Geom G, cons
         if (active) out[(size_t)y * nx + x] = res;
         pp = pc;
         c = sd;
+    }
+}
+
+// Reduced-precision heat, naive path: lane = column, each warp walks ROWS rows
+// keeping north and centre in registers (4 loads per point).
+template <class SS, int ROWS>
+__global__ void __launch_bounds__(256) naive_heat_kahan_kernel(HeatKahanOp<SS> op, Geom G,
+                                                               const SS *in, SS *out) {
+    typedef Store<SS> St;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int x = blockIdx.x * 32 + lane;
+    const int y0 = (blockIdx.y * 8 + warp) * ROWS;
+    if (x >= G.nx || y0 >= G.ny) return;
+    const int y1 = min(y0 + ROWS, G.ny);
+    const size_t nx = G.nx, plane = (size_t)G.nx * G.ny;
+    const int xw = x == 0 ? G.nx - 1 : x - 1, xe = x + 1 == G.nx ? 0 : x + 1;
+    const int ym = y0 == 0 ? G.ny - 1 : y0 - 1;
+    float un = St::ld(in[(size_t)ym * nx + x]), uc = St::ld(in[(size_t)y0 * nx + x]);
+    for (int y = y0; y < y1; ++y) {
+        const int ys = y + 1 == G.ny ? 0 : y + 1;
+        const size_t row = (size_t)y * nx;
+        const float us = St::ld(in[(size_t)ys * nx + x]);
+        op.update(uc, St::ld(in[plane + row + x]), St::ld(in[row + xe]), us, St::ld(in[row + xw]),
+                  un, out[row + x], out[plane + row + x]);
+        un = uc;
+        uc = us;
     }
 }
 
@@ -415,23 +453,26 @@ __global__ void __launch_bounds__(256) bridge_kernel(Op op, Geom G, const typena
         if (!block_wait_bulk(bar, err)) return;
         stg = st;
     }
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     auto load_strips = [&](int k, S *dst) {
-        const int L = n - 2 * k, L2 = 2 * L;
+        const int L = n - 2 * k;
         const int off = 2 * k * (n - k + 1);
-        for (int e = threadIdx.x; e < 2 * L2; e += blockDim.x) {
-            const int which = e >= L2, r = e - which * L2, d = r >= L, p = r - d * L;
-            const int uu = k + p;
+        for (int line = threadIdx.x >> 5; line < 4; line += nw) {   // 2 strips x 2 lines
+            const int which = line >> 1, d = line & 1;
             const int ww = which ? h + k + d : h - 1 - k - d;
-            const int x = xb ? ww : uu, y = xb ? uu : ww;
-            S *dd = dst + (y + 1) * P + (x + 1);
-            if constexpr (STG) {
-                const S *src = stg + which * NV * G.PS + off + d * L + p;
+            for (int p = lane; p < L; p += 32) {
+                const int uu = k + p;
+                const int x = xb ? ww : uu, y = xb ? uu : ww;
+                S *dd = dst + (y + 1) * P + (x + 1);
+                if constexpr (STG) {
+                    const S *src = stg + which * NV * G.PS + off + d * L + p;
 #pragma unroll
-                for (int v = 0; v < NV; ++v) dd[v * plane] = src[v * G.PS];
-            } else {
-                const S *src = seg[which] + off + d * L + p;
+                    for (int v = 0; v < NV; ++v) dd[v * plane] = src[v * G.PS];
+                } else {
+                    const S *src = seg[which] + off + d * L + p;
 #pragma unroll
-                for (int v = 0; v < NV; ++v) async_copy(dd + v * plane, src + (size_t)v * G.PS);
+                    for (int v = 0; v < NV; ++v) async_copy(dd + v * plane, src + (size_t)v * G.PS);
+                }
             }
         }
         if constexpr (!STG) async_commit();
@@ -444,16 +485,20 @@ __global__ void __launch_bounds__(256) bridge_kernel(Op op, Geom G, const typena
         S *nxt = bufs[(k + 1) & 1];
         // bridge panels of level k
         {
-            const int L = 2 * k + 2, L2 = 2 * L;
-            const size_t off = (size_t)2 * k * (k + 1);
-            for (int e = threadIdx.x; e < 2 * L2; e += blockDim.x) {
-                const int which = e >= L2, r = e - which * L2, d = r >= L, p = r - d * L;
+            const int L = 2 * k + 2;
+            const int off = 2 * k * (k + 1);
+            for (int line = threadIdx.x >> 5; line < 4; line += nw) {   // 2 sides x 2 lines
+                const int which = line >> 1, d = line & 1;
                 const int uu = which ? n - 1 - k - d : k + d;
-                const int ww = h - k + (which ? hi_w_shift : lo_w_shift) + p;
-                const int x = xb ? ww : uu, y = xb ? uu : ww;
-                S *dst = br + ((size_t)slot * 4 + (which ? out_hi : out_lo)) * NV * G.PS + off + d * L + p;
+                const int w0 = h - k + (which ? hi_w_shift : lo_w_shift);
+                S *dst = br + ((size_t)slot * 4 + (which ? out_hi : out_lo)) * NV * G.PS + off + d * L;
+                for (int p = lane; p < L; p += 32) {
+                    const int ww = w0 + p;
+                    const int x = xb ? ww : uu, y = xb ? uu : ww;
 #pragma unroll
-                for (int v = 0; v < NV; ++v) dst[(size_t)v * G.PS] = cur[v * plane + (y + 1) * P + (x + 1)];
+                    for (int v = 0; v < NV; ++v)
+                        dst[(size_t)v * G.PS + p] = cur[v * plane + (y + 1) * P + (x + 1)];
+                }
             }
         }
         if (k + 1 < h) {
@@ -506,28 +551,33 @@ __device__ __forceinline__ bool down_body(const Op &op, const Geom &G, unsigned 
         if (!block_wait_bulk(bar, err)) return false;
         stg = st;
     }
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     auto load_ring = [&](int k, S *dst) {
-        const int L = 2 * k + 2, L2 = 2 * L;
+        const int L = 2 * k + 2;
         const int off = 2 * k * (k + 1);
-        const float rl2 = 1.0f / (float)L2;
-        for (int e = threadIdx.x; e < 4 * L2; e += blockDim.x) {
-            const int side = div_small(e, rl2), r = e - side * L2, d = r >= L, p = r - d * L;
-            int x, y;
+        for (int line = threadIdx.x >> 5; line < 8; line += nw) {   // 4 sides x 2 lines
+            const int side = line >> 1, d = line & 1;
+            // (x, y) of element p: x = bx + p ax, y = by + p ay
+            int bx, by, ax, ay;
             switch (side) {
-                case 0: x = h - 1 - k - d; y = h - k - 2 + p; break;   // west
-                case 1: x = h + k + d; y = h - k + p; break;           // east
-                case 2: x = h - k + p; y = h - 1 - k - d; break;       // north
-                default: x = h - k - 2 + p; y = h + k + d; break;      // south
+                case 0: bx = h - 1 - k - d; by = h - k - 2; ax = 0; ay = 1; break;   // west
+                case 1: bx = h + k + d; by = h - k; ax = 0; ay = 1; break;           // east
+                case 2: bx = h - k; by = h - 1 - k - d; ax = 1; ay = 0; break;       // north
+                default: bx = h - k - 2; by = h + k + d; ax = 1; ay = 0; break;      // south
             }
-            S *dd = dst + (y + 1) * P + (x + 1);
-            if constexpr (STG) {
-                const S *src = stg + side * NV * G.PS + off + d * L + p;
+            S *dbase = dst + (by + 1) * P + (bx + 1);
+            const int step = ay * P + ax;
+            for (int p = lane; p < L; p += 32) {
+                S *dd = dbase + p * step;
+                if constexpr (STG) {
+                    const S *src = stg + side * NV * G.PS + off + d * L + p;
 #pragma unroll
-                for (int v = 0; v < NV; ++v) dd[v * plane] = src[v * G.PS];
-            } else {
-                const S *src = seg[side] + off + d * L + p;
+                    for (int v = 0; v < NV; ++v) dd[v * plane] = src[v * G.PS];
+                } else {
+                    const S *src = seg[side] + off + d * L + p;
 #pragma unroll
-                for (int v = 0; v < NV; ++v) async_copy(dd + v * plane, src + (size_t)v * G.PS);
+                    for (int v = 0; v < NV; ++v) async_copy(dd + v * plane, src + (size_t)v * G.PS);
+                }
             }
         }
         if constexpr (!STG) async_commit();

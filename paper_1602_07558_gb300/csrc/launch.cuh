@@ -80,6 +80,21 @@ struct Launch {
                 case 2: naive_heat_kernel<2><<<grid, kBlock, 0, st>>>(op, G, (const S *)in, (S *)out); break;
                 default: naive_heat_kernel<1><<<grid, kBlock, 0, st>>>(op, G, (const S *)in, (S *)out); break;
             }
+        } else if constexpr (std::is_same<Op, HeatKahanOp<float>>::value ||
+                             std::is_same<Op, HeatKahanOp<__nv_bfloat16>>::value) {
+            const long long chunks = (G.nx + 31) / 32;
+            int rows = 16;
+            while (rows > 1 && chunks * ((G.ny + rows - 1) / rows) < 152LL * 32) rows >>= 1;
+            const int warps = (G.ny + rows - 1) / rows;
+            dim3 grid((unsigned)chunks, (warps + 7) / 8);
+            const Op op(c);
+            switch (rows) {
+                case 16: naive_heat_kahan_kernel<S, 16><<<grid, kBlock, 0, st>>>(op, G, (const S *)in, (S *)out); break;
+                case 8: naive_heat_kahan_kernel<S, 8><<<grid, kBlock, 0, st>>>(op, G, (const S *)in, (S *)out); break;
+                case 4: naive_heat_kahan_kernel<S, 4><<<grid, kBlock, 0, st>>>(op, G, (const S *)in, (S *)out); break;
+                case 2: naive_heat_kahan_kernel<S, 2><<<grid, kBlock, 0, st>>>(op, G, (const S *)in, (S *)out); break;
+                default: naive_heat_kahan_kernel<S, 1><<<grid, kBlock, 0, st>>>(op, G, (const S *)in, (S *)out); break;
+            }
         } else {
             dim3 grid((G.nx + 31) / 32, (G.ny + 7) / 8);
             naive_kernel<Op><<<grid, kBlock, 0, st>>>(Op(c), G, (const S *)in, (S *)out, g);

@@ -67,17 +67,22 @@ struct HeatKahanOp {
     static constexpr bool STAGE = true;
     float r;
     __host__ __device__ explicit HeatKahanOp(const double *c) : r((float)c[0]) {}
+    // the update from the centre (u, c) and the four edge neighbours' u
+    __device__ __forceinline__ void update(float uc, float cc, float ue, float us, float uw,
+                                           float un, S &u_out, S &c_out) const {
+        typedef Store<S> St;
+        const float pe = __fadd_rn(ue, us);
+        const float pw = __fadd_rn(uw, un);
+        const float d = __fmaf_rn(-4.0f, uc, __fadd_rn(pe, pw));
+        const float y = __fsub_rn(__fmul_rn(r, d), cc);
+        u_out = St::st(__fadd_rn(uc, y));
+        c_out = St::st(__fsub_rn(__fsub_rn(St::ld(u_out), uc), y));
+    }
     template <class A>
     __device__ __forceinline__ void operator()(int, u64, const A &a, S *out) const {
         typedef Store<S> St;
-        const float uc = St::ld(a(0, 0, 0)), cc = St::ld(a(0, 0, 1));
-        const float pe = __fadd_rn(St::ld(a(1, 0, 0)), St::ld(a(0, 1, 0)));
-        const float pw = __fadd_rn(St::ld(a(-1, 0, 0)), St::ld(a(0, -1, 0)));
-        const float d = __fmaf_rn(-4.0f, uc, __fadd_rn(pe, pw));
-        const float y = __fsub_rn(__fmul_rn(r, d), cc);
-        const S un = St::st(__fadd_rn(uc, y));
-        out[0] = un;
-        out[1] = St::st(__fsub_rn(__fsub_rn(St::ld(un), uc), y));
+        update(St::ld(a(0, 0, 0)), St::ld(a(0, 0, 1)), St::ld(a(1, 0, 0)), St::ld(a(0, 1, 0)),
+               St::ld(a(-1, 0, 0)), St::ld(a(0, -1, 0)), out[0], out[1]);
     }
 };
 
