@@ -2,7 +2,8 @@
 path beside it), printing one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload heat4096|heat64|heat2048_f32|heat2048_bf16|euler2048]
+                  [--workload heat4096|heat64|heat2048_f32|heat2048_bf16|euler2048|wave1024|
+                              batch1024]
 
 The default workload is the headline one: 2D heat, periodic 4096 x 4096 FP64,
 r = 0.2, 10,000 steps, smooth 32-mode initial field, tile 32. One bench step =
@@ -13,7 +14,11 @@ Other workloads: heat64 (64 x 64 FP64, 512 steps, tile 16, U[0,1) field);
 heat2048_f32 / heat2048_bf16 (2048 x 2048, binary32 arithmetic with Kahan-
 compensated time update, binary32 / bfloat16 storage, 100,000 steps, error
 against the FP64 solution reported); euler2048 (2048 x 2048 compressible Euler,
-midpoint RK2, 5,000 steps, tile 16).
+midpoint RK2, 5,000 steps, tile 16); wave1024 (the paper's Section 6 wave
+equation, leapfrog, Courant number 0.3, source at the centre, 1024 x 1024);
+batch1024 (1,024 independent grids of uneven sizes, binary32 storage, one
+graph-captured swept launch sequence for all of them, tile autotuned per size
+class, against the batched naive path and against looping single-grid runs).
 
 With N > 1 (torchrun, one process per GPU) every rank advances its own
 independent grid ("replicas only"), the timed region is bracketed by a barrier,
@@ -76,6 +81,13 @@ WORKLOADS = {
                               "compensated update, r=0.2, 100000 steps"),
     "euler2048": Workload("euler_rk2", "f64", 2048, 5_000, 16, (GAMMA, CFL, KAPPA), "euler", 2,
                           "Euler 2048x2048 FP64, midpoint RK2, CFL 0.3, 5000 steps"),
+    "batch1024": Workload("heat_kahan", "f32", 0, 20_000, 0, (0.2,), "batch", 3,
+                          "1024 independent periodic grids, nx and ny uniform in {32,48,...,512} "
+                          "(seed 3), heat with binary32 storage and Kahan-compensated update, "
+                          "r=0.2, 20000 steps"),
+    "wave1024": Workload("wave", "f64", 1024, 10_000, 32, (0.3,), "source", 0,
+                         "wave 1024x1024 FP64 leapfrog, Courant 0.3, Gaussian source at the "
+                         "centre, 10000 steps"),
 }
 
 
@@ -98,6 +110,8 @@ def parse():
     p.add_argument("--stage", type=int, default=None, help="1: stage panels by TMA")
     p.add_argument("--autotune", action="store_true",
                    help="pick tile, threads and staging by timing short runs first")
+    p.add_argument("--graph", action="store_true",
+                   help="run each advance (swept and naive) as a captured CUDA graph")
     a = p.parse_args()
     w = WORKLOADS[a.workload]
     for k in ("grid", "nsteps", "tile"):
@@ -115,6 +129,8 @@ def initial_state(w: Workload, rank: int = 0) -> np.ndarray:
     if w.op == "euler_rk2":
         U = inputs.euler_pulse(N, N, seed, gamma=GAMMA)
         return np.concatenate([U, U])
+    if w.op == "wave":
+        return inputs.wave_source(N, N)
     f = inputs.smooth_field(N, N, seed) if w.init == "smooth" else inputs.uniform(N, N, seed)
     if w.op == "heat":
         return f[None]
@@ -202,6 +218,9 @@ def oracle_advance(w: Workload, state: np.ndarray, nsteps: int) -> np.ndarray:
         a, dt = oracle.euler_setup(state[:4], GAMMA, CFL)
         U = oracle.euler_rk2(state[:4], GAMMA, dt, KAPPA, a, nsteps)
         return U
+    if w.op == "wave":
+        u, uo = oracle.wave(state[0], state[1], w.params[0] * w.params[0], nsteps)
+        return np.stack([u, uo])
     raise ValueError(w.op)
 
 
@@ -296,6 +315,9 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    if w.init == "batch":
+        run_batch(args, w, world, rank, local)
+        return
     if args.impl == "reference":
         run_reference(args, w, rank)
         return
@@ -364,7 +386,7 @@ def main():
                 flush.zero_()                       # L2 flush, outside the timed events
                 start.record(stream)
                 s.set_state(state_dev)
-                s.advance(w.nsteps, mode=mode)
+                s.advance(w.nsteps, mode=mode, graph=args.graph)
                 stop.record(stream)
             stop.synchronize()
             if i >= wu:
@@ -445,6 +467,7 @@ def main():
                        "nsteps": w.nsteps, "tile": w.tile, "threads": args.threads or 256,
                        "stage": args.stage, "autotune": tune_table,
                        "parallelism": "replicas" if world > 1 else "single",
+                       "cuda_graph": bool(args.graph),
                        "l2": "flushed (256 MB write) between timed steps"},
             "naive": {"value": naive_value, "unit": UNIT, "ms_per_step": ms_nv,
                       "roofline": naive_rf} if ms_nv else None,
@@ -515,6 +538,185 @@ def naive_kernel_ms(nv, state_dev, stream, w):
     n, ms = nv.kernel_stats("naive")
     nv.set_timing(False)
     return ms / max(1, n)
+
+
+# ------------------------------------------------------------ batched form
+
+def batch_sizes(seed, count=1024):
+    rng = np.random.default_rng(seed)
+    vals = np.arange(32, 513, 16)                 # {32, 48, ..., 512}
+    return [int(v) for v in rng.choice(vals, size=count)], \
+        [int(v) for v in rng.choice(vals, size=count)]
+
+
+def batch_states(nx, ny, seed, dtype):
+    from paper_1602_07558_gb300 import inputs
+    parts = []
+    for i, (a, b) in enumerate(zip(nx, ny)):
+        u = inputs.uniform(a, b, seed * 100_000 + i).astype(np.float32)
+        if dtype == "bf16":
+            import torch
+            u = torch.from_numpy(u).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
+        parts.append(np.stack([u, np.zeros_like(u)]).reshape(-1))
+    return parts
+
+
+def run_batch(args, w, world, rank, local):
+    nx, ny = batch_sizes(w.seed + rank)
+    count = len(nx)
+    cells = sum(a * b for a, b in zip(nx, ny))
+    parts = batch_states(nx, ny, w.seed + rank, w.dtype)
+    flat = np.concatenate(parts)
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        import oracle
+        oracle.build()
+        rng = np.random.default_rng(7)
+        sample = sorted(rng.choice(count, size=16, replace=False).tolist())
+        nsteps = max(1, args.nsteps or 200) if args.nsteps else 200
+        t0 = time.perf_counter()
+        done = 0
+        for i in sample:
+            st = parts[i].reshape(2, ny[i], nx[i])
+            oracle.heat_kahan(st[0], st[1], w.params[0], nsteps, storage=w.dtype)
+            done += nx[i] * ny[i] * nsteps
+        dt = time.perf_counter() - t0
+        value = done / dt / 1e9
+        print(json.dumps({
+            "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": 1, "warmup": 0, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": w.dtype, "data": "synthetic",
+            "config": {"workload": w.describe + " (CPU oracle)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
+                             "kind": "oracle",
+                             "sample": f"16 of the {count} grids, {nsteps} steps each"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }), flush=True)
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    from paper_1602_07558_gb300.autotune import autotune_batch
+    from paper_1602_07558_gb300.swept2d import Swept2D, SweptBatch
+    stream = torch.cuda.Stream()
+    dev = torch.from_numpy(flat).to("cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    nsteps = w.nsteps
+    tiles, stage, tune_table = autotune_batch(nx, ny, w.op, w.params, dtype=w.dtype,
+                                              stream=stream)
+
+    def timed(b, mode, k, wu):
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        times, l0 = [], 0
+        for i in range(wu + k):
+            if i == wu:
+                torch.cuda.synchronize()
+                l0 = b.query("launches")
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                ev0.record(stream)
+                b.set_state(dev)
+                b.advance(nsteps, mode=mode, graph=True)
+                ev1.record(stream)
+            ev1.synchronize()
+            if i >= wu:
+                times.append(ev0.elapsed_time(ev1))
+        return statistics.mean(times), int(b.query("launches") - l0)
+
+    with ClockSampler(local) as clocks:
+        with SweptBatch(nx, ny, tiles, op=w.op, params=w.params, stream=stream,
+                        dtype=w.dtype) as sb:
+            sb.set_tuning(256, stage)
+            ms_sw, launches = timed(sb, "swept", args.steps, max(1, args.warmup // 3))
+            out_sw = sb.get_state()
+            h_in = torch.from_numpy(flat.copy()).pin_memory()
+            h_out = torch.empty_like(h_in).pin_memory()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sb.set_state(h_in)
+            sb.advance(nsteps, graph=True)
+            sb.get_state(h_out)
+            e2e_s = time.perf_counter() - t0
+        naive_ms = None
+        if not args.no_naive:
+            with SweptBatch(nx, ny, [0] * count, op=w.op, params=w.params, stream=stream,
+                            dtype=w.dtype) as nb:
+                naive_ms, _ = timed(nb, "naive", 1, 1)
+                same = bool(np.array_equal(out_sw, nb.get_state()))
+        # looping single-grid swept runs, one handle per grid, on a random sample
+        rng = np.random.default_rng(11)
+        sample = sorted(rng.choice(count, size=16, replace=False).tolist())
+        loop_ms, loop_cells = 0.0, 0
+        for i in sample:
+            with Swept2D(nx[i], ny[i], op=w.op, tile=tiles[i], params=w.params, stream=stream,
+                         dtype=w.dtype) as h:
+                st = torch.from_numpy(parts[i]).to("cuda")
+                ev0 = torch.cuda.Event(enable_timing=True)
+                ev1 = torch.cuda.Event(enable_timing=True)
+                for rep in range(2):
+                    with torch.cuda.stream(stream):
+                        h.set_state(st)
+                        ev0.record(stream)
+                        h.advance(nsteps, graph=True)
+                        ev1.record(stream)
+                    ev1.synchronize()
+                loop_ms += ev0.elapsed_time(ev1)
+                loop_cells += nx[i] * ny[i]
+    value = world * cells * nsteps / (ms_sw * 1e-3) / 1e9
+    naive_value = world * cells * nsteps / (naive_ms * 1e-3) / 1e9 if naive_ms else None
+    loop_value = loop_cells * nsteps / (loop_ms * 1e-3) / 1e9
+    # error against FP64 on four sample grids (GPU FP64 heat, bitwise the oracle)
+    split, off = [], 0
+    for a, b in zip(nx, ny):
+        split.append(out_sw[off:off + 2 * a * b].reshape(2, b, a))
+        off += 2 * a * b
+    errs = []
+    for i in sample[:4]:
+        u0 = storage_to_f64(parts[i].reshape(2, ny[i], nx[i])[0], w.dtype)
+        with Swept2D(nx[i], ny[i], op="heat", tile=16, params=w.params, stream=stream) as f64:
+            f64.set_state(np.ascontiguousarray(u0[None]))
+            f64.advance(nsteps)
+            ref = f64.get_state()[0]
+        u = storage_to_f64(split[i][0], w.dtype)
+        errs.append(float(np.max(np.abs(u - ref)) / max(np.max(np.abs(ref)), np.max(np.abs(u0)))))
+    # parity of the two smallest grids against the oracle (every point)
+    import oracle
+    oracle.build()
+    smallest = sorted(range(count), key=lambda i: nx[i] * ny[i])[:2]
+    par = []
+    for i in smallest:
+        st = parts[i].reshape(2, ny[i], nx[i])
+        ru, rc = oracle.heat_kahan(st[0], st[1], w.params[0], nsteps, storage=w.dtype)
+        par.append(bool(np.array_equal(split[i][0], ru) and np.array_equal(split[i][1], rc)))
+    class_counts = {}
+    for t in tiles:
+        class_counts[str(t)] = class_counts.get(str(t), 0) + 1
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(1, args.warmup // 3), "ms_per_step": ms_sw, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": w.dtype, "data": "synthetic",
+            "config": {"workload": w.describe, "grids": count, "cells": cells,
+                       "tiles_chosen": class_counts, "stage": stage, "autotune": tune_table,
+                       "cuda_graph": True, "l2": "flushed (256 MB write) between timed steps"},
+            "naive_batched": {"value": naive_value, "unit": UNIT, "ms_per_step": naive_ms,
+                              "note": "one naive launch per sub-step covering all grids, graph"},
+            "looped_single_grid": {"value": loop_value, "unit": UNIT,
+                                   "sample": "16 random grids, one swept handle each, graph",
+                                   "estimated_ms_all_grids": loop_ms * cells / loop_cells},
+            "speedup_vs_naive": value / naive_value if naive_value else None,
+            "speedup_vs_looped": value / loop_value,
+            "swept_equals_naive_bitwise": same if not args.no_naive else None,
+            "oracle_parity_two_smallest_grids": par,
+            "error_vs_fp64": {"u_max_rel_4_sample_grids": errs,
+                              "fp64_reference": "GPU FP64 heat path from the same initial field"},
+            "e2e": {"value": cells * nsteps / e2e_s / 1e9, "unit": UNIT,
+                    "h2d_bytes_per_step": int(flat.nbytes), "d2h_bytes_per_step": int(flat.nbytes)},
+            "gpu_launches": launches, "clocks": clocks.summary(),
+        }), flush=True)
 
 
 if __name__ == "__main__":

@@ -76,6 +76,11 @@ typedef struct swept2d swept2d_t;
  *             u_N) - 4u), y = delta - c, u' = store(u + y), c' = store((u' - u)
  *             - y), store() = rounding to the storage type (none for F32).
  *             r is rounded to binary32. u' - c' is the compensated value.
+ *  WAVE       nvars 2, nstages 1, dtype F64, params {C}: the 2D wave equation
+ *             u_tt = c^2 laplace(u) by leapfrog (Section 6), C = c dt/dx the
+ *             Courant number; plane 0 = u^n, plane 1 = u^{n-1}:
+ *             d = ((u_E + u_S) + (u_W + u_N)) - 4u, u' = (2u - u_old) + C^2 d
+ *             (fused), and the new u_old is u. C^2 is formed as C*C.
  */
 #define SWEPT2D_OP_HEAT       0
 #define SWEPT2D_OP_EULER_RK2  1
@@ -84,6 +89,7 @@ typedef struct swept2d swept2d_t;
 #define SWEPT2D_OP_LEVELTAG   4
 #define SWEPT2D_OP_WIDE2      5
 #define SWEPT2D_OP_HEAT_KAHAN 6
+#define SWEPT2D_OP_WAVE       7
 
 /* Element types of the state. */
 #define SWEPT2D_F64  0
@@ -94,6 +100,12 @@ typedef struct swept2d swept2d_t;
 /* Advance modes. */
 #define SWEPT2D_SWEPT 0   /* swept rule: Up, then per half cycle Bridge + Octahedron, final Down */
 #define SWEPT2D_NAIVE 1   /* one kernel launch per sub-step over the whole grid */
+/* Flag OR-ed into the mode: run the advance's launch sequence as a CUDA graph.
+ * The first advance with a given (nsteps, mode) and state buffer is captured
+ * (stream capture on the handle's stream, which must not be the legacy default
+ * stream) and cached (up to 8 per handle); later ones replay it with one graph
+ * launch. Results are the same bits as without the flag. */
+#define SWEPT2D_GRAPH 0x100
 
 /*
  * Create a handle for an nx x ny grid.
@@ -147,6 +159,7 @@ const char *swept2d_last_error(const swept2d_t *h);
 #define SWEPT2D_Q_STATE_BYTES   4   /* bytes of one state copy */
 #define SWEPT2D_Q_PANEL_BYTES   5   /* bytes of one panel buffer (0 if naive-only) */
 #define SWEPT2D_Q_SMEM_BYTES    6   /* dynamic shared memory per swept block */
+#define SWEPT2D_Q_CELLS         7   /* points of the grid (of all grids, for a batch) */
 int swept2d_query(const swept2d_t *h, int what, double *out);
 
 /* Launch shape of the swept kernels of a handle (a tuning knob, not a change
@@ -176,6 +189,35 @@ int swept2d_kernel_stats(swept2d_t *h, int kind, long long *launches, double *to
  * multiply-add chains on `stream`; writes lane-operations per second (one FMA
  * = one operation) to *ops_per_s. Used to state the FP64-pipe roofline. */
 int swept2d_measure_fp64_rate(void *stream, double *ops_per_s);
+
+/*
+ * Batched form: many independent periodic grids of uneven sizes, advanced
+ * together by the same number of steps (the paper's method applied to each grid
+ * separately; no grid exchanges data with another). Grids with the same tile
+ * side form a class, and one launch per swept phase (or per naive sub-step)
+ * covers every tile of every grid of the class, so a batch of small grids costs
+ * the launches of one grid.
+ *   count       number of grids; nx[i], ny[i] their sizes
+ *   tile[i]     tile side of grid i (even, >= 4, dividing nx[i] and ny[i]), or 0
+ *               for a grid that only takes naive steps
+ *   op, params, dtype, stream   as for swept2d_create; supported: HEAT (F64),
+ *               HEAT_KAHAN (F32, BF16), HASH (U64)
+ * State layout: the grids' states concatenated in grid order, each nvars planes
+ * of ny[i] x nx[i]. Modes: SWEPT2D_SWEPT or SWEPT2D_NAIVE, optionally OR-ed with
+ * SWEPT2D_GRAPH (not for HASH). Every call returns a status; messages through
+ * swept2d_batch_last_error (NULL batch: the last failed create on this thread).
+ */
+typedef struct swept2d_batch swept2d_batch_t;
+int swept2d_batch_create(swept2d_batch_t **out, int count, const int *nx, const int *ny,
+                         const int *tile, int op, const double *params, int nparams, int dtype,
+                         void *stream);
+int swept2d_batch_set_state(swept2d_batch_t *b, const void *src, int src_is_device);
+int swept2d_batch_advance(swept2d_batch_t *b, long long nsteps, int mode);
+int swept2d_batch_get_state(swept2d_batch_t *b, void *dst, int dst_is_device);
+int swept2d_batch_set_tuning(swept2d_batch_t *b, int threads, int stage);
+int swept2d_batch_destroy(swept2d_batch_t *b);
+const char *swept2d_batch_last_error(const swept2d_batch_t *b);
+int swept2d_batch_query(const swept2d_batch_t *b, int what, double *out);
 
 /*
  * Allocation-free swept advance of the heat equation (FP64). The paper has no

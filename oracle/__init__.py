@@ -69,6 +69,7 @@ def _load():
                                            ctypes.POINTER(d), ctypes.POINTER(d)]
         lib.oracle_euler_rk2.argtypes = [i, i, d, d, d, d, d, d, ll, p]
         lib.oracle_heat_kahan_f32.argtypes = [i, i, d, ll, p, p]
+        lib.oracle_wave.argtypes = [i, i, d, ll, p, p]
         lib.oracle_heat_kahan_bf16.argtypes = [i, i, d, ll, p, p]
         lib.oracle_f32_to_bf16.argtypes = [ctypes.c_float]
         lib.oracle_f32_to_bf16.restype = ctypes.c_uint16
@@ -76,7 +77,7 @@ def _load():
         lib.oracle_bf16_to_f32.restype = ctypes.c_float
         for name in ("oracle_heat", "oracle_increment", "oracle_hash", "oracle_leveltag",
                      "oracle_wide2", "oracle_euler_setup", "oracle_euler_rk2",
-                     "oracle_heat_kahan_f32", "oracle_heat_kahan_bf16"):
+                     "oracle_heat_kahan_f32", "oracle_heat_kahan_bf16", "oracle_wave"):
             getattr(lib, name).restype = i
         _lib = lib
         return lib
@@ -190,3 +191,13 @@ def heat_kahan(u0, c0, r: float, nsteps: int, storage: str = "f32"):
     fn = _load().oracle_heat_kahan_f32 if storage == "f32" else _load().oracle_heat_kahan_bf16
     _check(fn(nx, ny, float(r), int(nsteps), u.ctypes.data, c.ctypes.data), "heat_kahan")
     return u, c
+
+
+def wave(u0, uold0, C2: float, nsteps: int):
+    """Leapfrog wave equation with squared Courant number C2; returns (u^n, u^{n-1})."""
+    u = _grid(u0, np.float64)
+    uo = _grid(uold0, np.float64)
+    ny, nx = u.shape
+    _check(_load().oracle_wave(nx, ny, float(C2), int(nsteps), u.ctypes.data, uo.ctypes.data),
+           "wave")
+    return u, uo

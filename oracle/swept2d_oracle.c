@@ -36,6 +36,8 @@
  *             (substep2), is what the swept path runs)
  *   euler     2D compressible Euler, central flux plus scalar dissipation,
  *             midpoint (2-stage) Runge-Kutta, dt fixed from the initial state
+ *   wave      the 2D wave equation u_tt = c^2 laplace(u), leapfrog in time with
+ *             Courant number C (Section 6's experiment), point state (u^n, u^{n-1})
  *   heat_kahan the heat update in binary32 arithmetic with the time update
  *             accumulated by Kahan's compensated summation, state (u, c) stored
  *             in binary32 or in bfloat16 (reduced-precision storage forms)
@@ -417,5 +419,39 @@ int oracle_heat_kahan_bf16(int nx, int ny, double r64, long long nsteps, uint16_
     }
     if (ua != u) { memcpy(u, ua, npts * sizeof(uint16_t)); memcpy(c, ca, npts * sizeof(uint16_t)); }
     free(u2); free(c2);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ wave
+ * u_tt = c^2 laplace(u) with the leapfrog scheme (second order in time):
+ *     d = ((u_E + u_S) + (u_W + u_N)) - 4u        (5-point Laplacian, same pairing as heat)
+ *     u^{n+1} = (2u - u^{n-1}) + C^2 d            (one rounding: fma)
+ * with C = c dt / dx the Courant number. The point state is (u^n, u^{n-1}), so
+ * each step is a radius-1 stencil with a 2-value point (Section 2, item 2). */
+int oracle_wave(int nx, int ny, double C2, long long nsteps, double *u, double *uold) {
+    if (nx < 1 || ny < 1 || nsteps < 0 || !u || !uold) return -1;
+    size_t npts = (size_t)nx * ny;
+    double *un = (double *)malloc(npts * sizeof(double));
+    double *uo = (double *)malloc(npts * sizeof(double));
+    if (!un || !uo) { free(un); free(uo); return -3; }
+    for (long long s = 0; s < nsteps; ++s) {
+#pragma omp parallel for schedule(static)
+        for (int j = 0; j < ny; ++j) {
+            int jn = wrapi(j - 1, ny), js = wrapi(j + 1, ny);
+            for (int i = 0; i < nx; ++i) {
+                int iw = wrapi(i - 1, nx), ie = wrapi(i + 1, nx);
+                size_t p = (size_t)j * nx + i;
+                double c = u[p];
+                double sum = (u[(size_t)j * nx + ie] + u[(size_t)js * nx + i]) +
+                             (u[(size_t)j * nx + iw] + u[(size_t)jn * nx + i]);
+                double d = sum - 4.0 * c;
+                un[p] = fma(C2, d, 2.0 * c - uold[p]);
+                uo[p] = c;
+            }
+        }
+        memcpy(u, un, npts * sizeof(double));
+        memcpy(uold, uo, npts * sizeof(double));
+    }
+    free(un); free(uo);
     return 0;
 }

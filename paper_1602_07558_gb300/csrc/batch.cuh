@@ -1,0 +1,192 @@
+// Batched kernels: many independent periodic grids of uneven sizes advanced
+// together, one launch per swept phase (or per naive sub-step) over the tiles
+// (or blocks) of every grid. Grids that use the same tile side n form a class;
+// a class's launches cover all of its grids' tiles, listed in a tile table
+// (tile -> grid). Each block looks up its grid's descriptor and runs the same
+// per-tile bodies as the single-grid kernels, on that grid's slice of the
+// pooled state and panel buffers.
+#pragma once
+#include "launch.cuh"
+
+namespace swept {
+
+struct GridDesc {
+    Geom G;                 // the grid's geometry (tile side n of its class)
+    long long state_off;    // first element of the grid's state in the pooled state
+    long long panel_off;    // first element of the grid's panel slots in each pool
+};
+// Tile and block tables hold (grid index, tile or block index within the grid).
+
+template <class Op>
+__global__ void __launch_bounds__(256) batch_up_kernel(Op op, const GridDesc *grids,
+                                                       const int2 *tile_grid,
+                                                       const typename Op::S *state,
+                                                       typename Op::S *up, int o, u64 g0) {
+    const int2 e = tile_grid[blockIdx.x];
+    const GridDesc gd = grids[e.x];
+    const int J = e.y / gd.G.T, I = e.y - J * gd.G.T;
+    up_tile(op, gd.G, state + gd.state_off, up + gd.panel_off, o, g0, I, J);
+}
+
+template <class Op, bool STG>
+__global__ void __launch_bounds__(256) batch_bridge_kernel(Op op, const GridDesc *grids,
+                                                           const int2 *tile_grid,
+                                                           const typename Op::S *up,
+                                                           typename Op::S *br, u64 g0, int *err) {
+    const int2 e = tile_grid[blockIdx.x];
+    const GridDesc gd = grids[e.x];
+    const int J = e.y / gd.G.T, I = e.y - J * gd.G.T;
+    bridge_tile<Op, STG>(op, gd.G, up + gd.panel_off, br + gd.panel_off, g0, err, I, J,
+                         blockIdx.y == 1);
+}
+
+template <class Op, bool STG>
+__global__ void __launch_bounds__(256) batch_octahedron_kernel(Op op, const GridDesc *grids,
+                                                               const int2 *tile_grid,
+                                                               const typename Op::S *br,
+                                                               typename Op::S *up, int o, u64 g0,
+                                                               int *err) {
+    const int2 e = tile_grid[blockIdx.x];
+    const GridDesc gd = grids[e.x];
+    const int J = e.y / gd.G.T, I = e.y - J * gd.G.T;
+    octahedron_tile<Op, STG>(op, gd.G, br + gd.panel_off, up + gd.panel_off, o, g0, err, I, J);
+}
+
+template <class Op, bool STG>
+__global__ void __launch_bounds__(256) batch_down_kernel(Op op, const GridDesc *grids,
+                                                         const int2 *tile_grid,
+                                                         const typename Op::S *br,
+                                                         typename Op::S *state, int o, u64 g0,
+                                                         int *err) {
+    const int2 e = tile_grid[blockIdx.x];
+    const GridDesc gd = grids[e.x];
+    const int J = e.y / gd.G.T, I = e.y - J * gd.G.T;
+    down_tile<Op, STG>(op, gd.G, br + gd.panel_off, state + gd.state_off, o, g0, err, I, J);
+}
+
+// One sub-step of every grid in a block table: block b covers a 32 x 8 patch of
+// its grid (the same per-point update as the single-grid naive kernel).
+template <class Op>
+__global__ void __launch_bounds__(256) batch_naive_kernel(Op op, const GridDesc *grids,
+                                                          const int2 *block_grid,
+                                                          const typename Op::S *in,
+                                                          typename Op::S *out, u64 g) {
+    typedef typename Op::S S;
+    const int2 e = block_grid[blockIdx.x];
+    const GridDesc gd = grids[e.x];
+    const int nbx = (gd.G.nx + 31) / 32;
+    const int by = e.y / nbx, bx = e.y - by * nbx;
+    const int x = bx * 32 + (threadIdx.x & 31);
+    const int y = by * 8 + (threadIdx.x >> 5);
+    if (x >= gd.G.nx || y >= gd.G.ny) return;
+    const size_t plane = (size_t)gd.G.nx * gd.G.ny;
+    GlobalAcc<S> acc(in + gd.state_off, plane, gd.G.nx, gd.G.ny, x, y);
+    S res[Op::NV];
+    op((int)(g % Op::NST), g, acc, res);
+    S *o = out + gd.state_off + (size_t)y * gd.G.nx + x;
+#pragma unroll
+    for (int v = 0; v < Op::NV; ++v) o[v * plane] = res[v];
+}
+
+// Launch functions of one point update for the batch.
+struct BatchTable {
+    int nv, nst, esize;
+    bool default_stage;
+    size_t (*smem_for)(int n, bool stage);
+    cudaError_t (*naive)(const GridDesc *, const int2 *block_grid, int nblocks, const double *c,
+                         const void *in, void *out, u64 g, cudaStream_t);
+    cudaError_t (*up)(const GridDesc *, const int2 *tile_grid, int ntiles, int n, const double *c,
+                      const void *state, void *up, int o, u64 g0, cudaStream_t);
+    cudaError_t (*bridge)(const GridDesc *, const int2 *tile_grid, int ntiles, int n,
+                          const double *c, const void *up, void *br, u64 g0, int *err,
+                          const Tuning &, cudaStream_t);
+    cudaError_t (*octahedron)(const GridDesc *, const int2 *tile_grid, int ntiles, int n,
+                              const double *c, const void *br, void *up, int o, u64 g0, int *err,
+                              const Tuning &, cudaStream_t);
+    cudaError_t (*down)(const GridDesc *, const int2 *tile_grid, int ntiles, int n,
+                        const double *c, const void *br, void *state, int o, u64 g0, int *err,
+                        const Tuning &, cudaStream_t);
+};
+
+template <class Op>
+struct BatchLaunch {
+    typedef typename Op::S S;
+    static cudaError_t naive(const GridDesc *d, const int2 *bg, int nblocks, const double *c,
+                             const void *in, void *out, u64 g, cudaStream_t st) {
+        batch_naive_kernel<Op><<<nblocks, kBlock, 0, st>>>(Op(c), d, bg, (const S *)in, (S *)out, g);
+        return cudaGetLastError();
+    }
+    static cudaError_t up(const GridDesc *d, const int2 *tg, int ntiles, int n, const double *c,
+                          const void *state, void *upp, int o, u64 g0, cudaStream_t st) {
+        const size_t sm = up_smem<Op>(n);
+        cudaError_t e = allow_smem(batch_up_kernel<Op>, sm);
+        if (e != cudaSuccess) return e;
+        batch_up_kernel<Op><<<ntiles, kBlock, sm, st>>>(Op(c), d, tg, (const S *)state, (S *)upp, o, g0);
+        return cudaGetLastError();
+    }
+    template <bool STG>
+    static cudaError_t bridge_t(const GridDesc *d, const int2 *tg, int ntiles, int n,
+                                const double *c, const void *upp, void *br, u64 g0, int *err,
+                                int threads, cudaStream_t st) {
+        const size_t sm = bridge_smem<Op>(n, STG);
+        cudaError_t e = allow_smem(batch_bridge_kernel<Op, STG>, sm);
+        if (e != cudaSuccess) return e;
+        batch_bridge_kernel<Op, STG><<<dim3(ntiles, 2), threads, sm, st>>>(Op(c), d, tg,
+                                                                           (const S *)upp, (S *)br,
+                                                                           g0, err);
+        return cudaGetLastError();
+    }
+    static cudaError_t bridge(const GridDesc *d, const int2 *tg, int ntiles, int n, const double *c,
+                              const void *upp, void *br, u64 g0, int *err, const Tuning &tn,
+                              cudaStream_t st) {
+        return tn.stage ? bridge_t<true>(d, tg, ntiles, n, c, upp, br, g0, err, tn.threads, st)
+                        : bridge_t<false>(d, tg, ntiles, n, c, upp, br, g0, err, tn.threads, st);
+    }
+    template <bool STG>
+    static cudaError_t oct_t(const GridDesc *d, const int2 *tg, int ntiles, int n, const double *c,
+                             const void *br, void *upp, int o, u64 g0, int *err, int threads,
+                             cudaStream_t st) {
+        const size_t sm = down_smem<Op>(n, STG);
+        cudaError_t e = allow_smem(batch_octahedron_kernel<Op, STG>, sm);
+        if (e != cudaSuccess) return e;
+        batch_octahedron_kernel<Op, STG><<<ntiles, threads, sm, st>>>(Op(c), d, tg, (const S *)br,
+                                                                      (S *)upp, o, g0, err);
+        return cudaGetLastError();
+    }
+    static cudaError_t octahedron(const GridDesc *d, const int2 *tg, int ntiles, int n,
+                                  const double *c, const void *br, void *upp, int o, u64 g0,
+                                  int *err, const Tuning &tn, cudaStream_t st) {
+        return tn.stage ? oct_t<true>(d, tg, ntiles, n, c, br, upp, o, g0, err, tn.threads, st)
+                        : oct_t<false>(d, tg, ntiles, n, c, br, upp, o, g0, err, tn.threads, st);
+    }
+    template <bool STG>
+    static cudaError_t down_t(const GridDesc *d, const int2 *tg, int ntiles, int n,
+                              const double *c, const void *br, void *state, int o, u64 g0,
+                              int *err, int threads, cudaStream_t st) {
+        const size_t sm = down_smem<Op>(n, STG);
+        cudaError_t e = allow_smem(batch_down_kernel<Op, STG>, sm);
+        if (e != cudaSuccess) return e;
+        batch_down_kernel<Op, STG><<<ntiles, threads, sm, st>>>(Op(c), d, tg, (const S *)br,
+                                                                (S *)state, o, g0, err);
+        return cudaGetLastError();
+    }
+    static cudaError_t down(const GridDesc *d, const int2 *tg, int ntiles, int n, const double *c,
+                            const void *br, void *state, int o, u64 g0, int *err,
+                            const Tuning &tn, cudaStream_t st) {
+        return tn.stage ? down_t<true>(d, tg, ntiles, n, c, br, state, o, g0, err, tn.threads, st)
+                        : down_t<false>(d, tg, ntiles, n, c, br, state, o, g0, err, tn.threads, st);
+    }
+    static const BatchTable *table() {
+        static const BatchTable t = {Op::NV, Op::NST, (int)sizeof(S), Op::STAGE,
+                                     &swept_smem_for<Op>, &naive, &up, &bridge, &octahedron,
+                                     &down};
+        return &t;
+    }
+};
+
+const BatchTable *batchtable_heat();
+const BatchTable *batchtable_heat_kahan_f32();
+const BatchTable *batchtable_heat_kahan_bf16();
+const BatchTable *batchtable_hash();
+
+}  // namespace swept

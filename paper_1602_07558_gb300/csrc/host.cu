@@ -29,6 +29,21 @@ struct TimedLaunch {
     cudaEvent_t start, stop;
 };
 
+// One captured advance: replaying it is valid while the state buffer, the step
+// count and the mode are the same (and, for the hash update, whose arithmetic
+// reads the sub-step index, the starting sub-step).
+struct GraphEntry {
+    long long nsteps;
+    int mode;
+    void *state;
+    long long g_start;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+    long long substeps_advanced;
+    long long kernels;
+    bool swaps_state;
+};
+
 struct swept2d {
     int nx = 0, ny = 0, nv = 0, nst = 0, n = 0, op = 0, dtype = 0, esize = 0;
     Geom G{};
@@ -49,6 +64,7 @@ struct swept2d {
     bool timing = false;
     std::vector<TimedLaunch> timed;
     std::vector<cudaEvent_t> event_pool;
+    std::vector<GraphEntry> graphs;
     long long k_launches[SWEPT2D_K_COUNT] = {0};
     double k_ms[SWEPT2D_K_COUNT] = {0};
     std::string err;
@@ -133,6 +149,7 @@ const OpTable *table_for(int op, int dtype) {
         case SWEPT2D_OP_HASH: return swept::optable_hash();
         case SWEPT2D_OP_LEVELTAG: return swept::optable_leveltag();
         case SWEPT2D_OP_WIDE2: return swept::optable_wide2();
+        case SWEPT2D_OP_WAVE: return swept::optable_wave();
         default: return nullptr;
     }
 }
@@ -155,6 +172,11 @@ void free_all(swept2d *h) {
         cudaEventDestroy(t.stop);
     }
     for (auto e : h->event_pool) cudaEventDestroy(e);
+    for (auto &g : h->graphs) {
+        cudaGraphExecDestroy(g.exec);
+        cudaGraphDestroy(g.graph);
+    }
+    h->graphs.clear();
     h->state = h->state2 = h->up = h->br = nullptr;
     h->scratch8 = nullptr;
     h->errword = nullptr;
@@ -209,6 +231,68 @@ int swept_substeps(swept2d *h, long long total) {
     return naive_substeps(h, rem);
 }
 
+int run_advance(swept2d *h, long long total, int mode) {
+    return mode == SWEPT2D_SWEPT ? swept_substeps(h, total) : naive_substeps(h, total);
+}
+
+// Advance through a captured CUDA graph of the whole launch sequence.
+int graph_advance(swept2d *h, long long nsteps, int mode) {
+    const long long g_key = h->op == SWEPT2D_OP_HASH ? h->substeps : 0;
+    for (auto &g : h->graphs) {
+        if (g.nsteps == nsteps && g.mode == mode && g.state == h->state && g.g_start == g_key) {
+            cudaError_t e = cudaGraphLaunch(g.exec, h->stream);
+            if (e != cudaSuccess) return cuda_fail(h, e, "graph launch");
+            h->substeps += g.substeps_advanced;
+            h->launches += g.kernels;
+            if (g.swaps_state) std::swap(h->state, h->state2);
+            return SWEPT2D_OK;
+        }
+    }
+    GraphEntry g{};
+    g.nsteps = nsteps;
+    g.mode = mode;
+    g.state = h->state;
+    g.g_start = g_key;
+    const long long sub0 = h->substeps, l0 = h->launches;
+    void *s0 = h->state, *s0b = h->state2;
+    const bool timing = h->timing;
+    h->timing = false;
+    cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        h->timing = timing;
+        return cuda_fail(h, e, "graph capture begin");
+    }
+    int rc = run_advance(h, nsteps * h->nst, mode);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(h->stream, &graph);
+    h->timing = timing;
+    // the capture ran nothing: undo the host bookkeeping, then replay it below
+    g.substeps_advanced = h->substeps - sub0;
+    g.kernels = h->launches - l0;
+    g.swaps_state = h->state != s0;
+    h->substeps = sub0;
+    h->launches = l0;
+    h->state = s0;
+    h->state2 = s0b;
+    if (rc != SWEPT2D_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "graph capture end");
+    g.graph = graph;
+    if ((e = cudaGraphInstantiate(&g.exec, graph, 0)) != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return cuda_fail(h, e, "graph instantiate");
+    }
+    if (h->graphs.size() >= 8) {
+        cudaGraphExecDestroy(h->graphs.front().exec);
+        cudaGraphDestroy(h->graphs.front().graph);
+        h->graphs.erase(h->graphs.begin());
+    }
+    h->graphs.push_back(g);
+    return graph_advance(h, nsteps, mode);
+}
+
 }  // namespace
 
 extern "C" {
@@ -225,7 +309,7 @@ int swept2d_create(swept2d_t **out, int nx, int ny, int nvars, int nstages, int 
         delete h;
         return code;
     };
-    if (op < 0 || op > SWEPT2D_OP_HEAT_KAHAN) { fail(h, 0, "unknown op"); return bail(SWEPT2D_EINVAL); }
+    if (op < 0 || op > SWEPT2D_OP_WAVE) { fail(h, 0, "unknown op"); return bail(SWEPT2D_EINVAL); }
     if (!dtype_ok(op, dtype)) { fail(h, 0, "dtype does not match the op"); return bail(SWEPT2D_EINVAL); }
     const OpTable *t = table_for(op, dtype);
     if (!t) { fail(h, 0, "unknown op"); return bail(SWEPT2D_EINVAL); }
@@ -271,6 +355,10 @@ int swept2d_create(swept2d_t **out, int nx, int ny, int nvars, int nstages, int 
         case SWEPT2D_OP_HEAT_KAHAN:
             if (nparams < 1) { fail(h, 0, "heat needs params {r}"); return bail(SWEPT2D_EINVAL); }
             h->consts[0] = params[0];
+            break;
+        case SWEPT2D_OP_WAVE:
+            if (nparams < 1) { fail(h, 0, "wave needs params {C}"); return bail(SWEPT2D_EINVAL); }
+            h->consts[0] = params[0] * params[0];
             break;
         case SWEPT2D_OP_EULER_RK2:
             if (nparams < 3) {
@@ -352,11 +440,16 @@ int swept2d_advance(swept2d_t *h, long long nsteps, int mode) {
     if (!h) return SWEPT2D_EINVAL;
     if (nsteps < 0) return fail(h, SWEPT2D_EINVAL, "advance: nsteps < 0");
     if (!h->has_state) return fail(h, SWEPT2D_ESTATE, "advance: no state set");
+    const bool graph = (mode & SWEPT2D_GRAPH) != 0;
+    mode &= ~SWEPT2D_GRAPH;
     if (mode != SWEPT2D_SWEPT && mode != SWEPT2D_NAIVE) return fail(h, SWEPT2D_EINVAL, "advance: bad mode");
     if (mode == SWEPT2D_SWEPT && h->n == 0)
         return fail(h, SWEPT2D_EINVAL, "advance: swept mode needs a tile (created with tile 0)");
-    const long long total = nsteps * h->nst;
-    return mode == SWEPT2D_SWEPT ? swept_substeps(h, total) : naive_substeps(h, total);
+    if (graph) {
+        if (!h->stream) return fail(h, SWEPT2D_EINVAL, "advance: graph mode needs a created stream");
+        return graph_advance(h, nsteps, mode);
+    }
+    return run_advance(h, nsteps * h->nst, mode);
 }
 
 int swept2d_get_state(swept2d_t *h, void *dst, int dst_is_device) {
@@ -398,6 +491,7 @@ int swept2d_query(const swept2d_t *h, int what, double *out) {
         case SWEPT2D_Q_STATE_BYTES: *out = (double)h->state_bytes; break;
         case SWEPT2D_Q_PANEL_BYTES: *out = (double)h->panel_bytes; break;
         case SWEPT2D_Q_SMEM_BYTES: *out = (double)h->smem_bytes; break;
+        case SWEPT2D_Q_CELLS: *out = (double)h->nx * h->ny; break;
         default: return SWEPT2D_EINVAL;
     }
     return SWEPT2D_OK;

@@ -150,6 +150,13 @@ __device__ __forceinline__ bool block_wait_bulk(unsigned long long *bar, int *er
 // t + 2T, ... in row order, T = blockDim), so warps stay full; the (column,
 // row) of the next point follows by adding (T mod W, T div W) with a carry,
 // so a level costs two integer divisions per thread, not one per point.
+// q = floor(e / d) for 0 <= e < 2^20 and 1 <= d <= 2^10 via a binary32
+// reciprocal: (e + 1/2) / d is at least 1/(2d) away from an integer, far more
+// than the two roundings' error, so the truncation is exact.
+__device__ __forceinline__ int div_small(int e, float rd) {
+    return (int)(((float)e + 0.5f) * rd);
+}
+
 struct LinearWalk {
     int xx, yy, dq, dr;
     __device__ __forceinline__ explicit LinearWalk(int W) {
@@ -232,14 +239,20 @@ __device__ __forceinline__ void compute_rect(const Op &op, int stage, u64 g,
 __device__ __forceinline__ void compute_rect(const HeatOp &op, int, u64, const double *src,
                                              double *dst, double *aux, int P, int x0, int y0,
                                              int W, int H) {
-    for (LinearWalk w(W + 1); w.yy <= H; w.next(W + 1)) {
-        const int off = (y0 + w.yy) * P + (x0 + w.xx);    // point (x0-1+xx, y0-1+yy)
+    // (FP64-pipe bound: the per-point decode by reciprocal keeps independent
+    // points per thread visible to the scheduler better than a carried walk)
+    const int W1 = W + 1, cnt1 = W1 * (H + 1);
+    const float rw1 = 1.0f / (float)W1, rw = 1.0f / (float)W;
+    for (int e = threadIdx.x; e < cnt1; e += blockDim.x) {
+        const int yy = div_small(e, rw1), xx = e - yy * W1;
+        const int off = (y0 + yy) * P + (x0 + xx);      // point (x0-1+xx, y0-1+yy)
         aux[off] = __dadd_rn(src[off + 1], src[off + P]);
     }
     __syncthreads();
-    if (W <= 0) return;
-    for (LinearWalk w(W); w.yy < H; w.next(W)) {
-        const int off = (y0 + w.yy + 1) * P + (x0 + w.xx + 1);
+    const int cnt = W * H;
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+        const int yy = div_small(e, rw), xx = e - yy * W;
+        const int off = (y0 + yy + 1) * P + (x0 + xx + 1);
         const double c = src[off];
         const double sum = __dadd_rn(aux[off], aux[off - P - 1]);
         dst[off] = __fma_rn(op.r, __fma_rn(-4.0, c, sum), c);
@@ -379,15 +392,14 @@ __device__ __forceinline__ void up_body(const Op &op, const Geom &G, typename Op
 
 // K1: first upward pyramid of an advance, frame offset o, reading the state.
 template <class Op>
-__global__ void __launch_bounds__(256) up_kernel(Op op, Geom G, const typename Op::S *state,
-                                                 typename Op::S *up, int o, u64 g0) {
+__device__ __forceinline__ void up_tile(const Op &op, const Geom &G, const typename Op::S *state,
+                                        typename Op::S *up, int o, u64 g0, int I, int J) {
     typedef typename Op::S S;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = G.n, P = n + 2, plane = P * P;
     S *buf0 = reinterpret_cast<S *>(smem_raw);
     S *buf1 = buf0 + Op::NV * plane;
     S *aux = buf1 + Op::NV * plane;
-    const int I = blockIdx.x, J = blockIdx.y;
     const size_t gplane = (size_t)G.nx * G.ny;
     const int x0 = o + I * n, y0 = o + J * n;
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
@@ -402,6 +414,12 @@ __global__ void __launch_bounds__(256) up_kernel(Op op, Geom G, const typename O
     up_body(op, G, buf0, buf1, aux, P, g0, up, J * G.T + I, 0);
 }
 
+template <class Op>
+__global__ void __launch_bounds__(256) up_kernel(Op op, Geom G, const typename Op::S *state,
+                                                 typename Op::S *up, int o, u64 g0) {
+    up_tile(op, G, state, up, o, g0, blockIdx.x, blockIdx.y);
+}
+
 // ------------------------------------------- Bridges (Algorithms 2 and 3)
 // blockIdx.z == 0: longitudinal (y-) bridge between Up(I,J) and Up(I,J+1),
 // frame (o, o+h); blockIdx.z == 1: latitudinal (x-) bridge between Up(I,J)
@@ -409,8 +427,9 @@ __global__ void __launch_bounds__(256) up_kernel(Op op, Geom G, const typename O
 // In "along/across" coordinates (u along the bridge, w across it) the two are
 // the same; (x, y) = (u, w) for the y-bridge and (w, u) for the x-bridge.
 template <class Op, bool STG>
-__global__ void __launch_bounds__(256) bridge_kernel(Op op, Geom G, const typename Op::S *up,
-                                                     typename Op::S *br, u64 g0, int *err) {
+__device__ __forceinline__ void bridge_tile(const Op &op, const Geom &G, const typename Op::S *up,
+                                            typename Op::S *br, u64 g0, int *err, int I, int J,
+                                            bool xb) {
     typedef typename Op::S S;
     constexpr int NV = Op::NV;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -419,8 +438,6 @@ __global__ void __launch_bounds__(256) bridge_kernel(Op op, Geom G, const typena
     bufs[0] = reinterpret_cast<S *>(smem_raw);
     bufs[1] = bufs[0] + NV * plane;
     S *aux = bufs[1] + NV * plane;
-    const int I = blockIdx.x, J = blockIdx.y;
-    const bool xb = blockIdx.z == 1;
     const int slot = J * G.T + I;
     // low tile: Up(I,J); high tile: Up(I,J+1) or Up(I+1,J)
     const int hi_slot = xb ? (J * G.T + (I + 1 == G.T ? 0 : I + 1))
@@ -515,6 +532,12 @@ __global__ void __launch_bounds__(256) bridge_kernel(Op op, Geom G, const typena
     }
 }
 
+template <class Op, bool STG>
+__global__ void __launch_bounds__(256) bridge_kernel(Op op, Geom G, const typename Op::S *up,
+                                                     typename Op::S *br, u64 g0, int *err) {
+    bridge_tile<Op, STG>(op, G, up, br, g0, err, blockIdx.x, blockIdx.y, blockIdx.z == 1);
+}
+
 // --------------------------------------------- DownwardPyramid (Algorithm 5)
 // Down(I,J) in frame (o+h, o+h): levels 1..h of half cycle g0 from the bridge
 // panels. Ends with the full tile at level h in buffer (h & 1).
@@ -522,11 +545,10 @@ template <class Op, bool STG>
 __device__ __forceinline__ bool down_body(const Op &op, const Geom &G, unsigned char *smem_raw,
                                           typename Op::S *buf0, typename Op::S *buf1,
                                           typename Op::S *aux, int P, const typename Op::S *br,
-                                          u64 g0, int *err) {
+                                          u64 g0, int *err, int I, int J) {
     typedef typename Op::S S;
     constexpr int NV = Op::NV;
     const int n = G.n, h = n / 2, plane = P * P;
-    const int I = blockIdx.x, J = blockIdx.y;
     const int slot = J * G.T + I;
     const int east = J * G.T + (I + 1 == G.T ? 0 : I + 1);
     const int south = (J + 1 == G.Q ? 0 : J + 1) * G.T + I;
@@ -601,19 +623,18 @@ __device__ __forceinline__ bool down_body(const Op &op, const Geom &G, unsigned 
 // K3: octahedron = Down of half cycle g0 (frame o+h) fused with the Up of half
 // cycle g0+h in the same tile and frame; writes the next up panels.
 template <class Op, bool STG>
-__global__ void __launch_bounds__(256) octahedron_kernel(Op op, Geom G, const typename Op::S *br,
-                                                         typename Op::S *up, int o, u64 g0,
-                                                         int *err) {
+__device__ __forceinline__ void octahedron_tile(const Op &op, const Geom &G,
+                                                const typename Op::S *br, typename Op::S *up,
+                                                int o, u64 g0, int *err, int I, int J) {
     typedef typename Op::S S;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = G.n, h = n / 2, P = n + 2, plane = P * P;
     S *buf0 = reinterpret_cast<S *>(smem_raw);
     S *buf1 = buf0 + Op::NV * plane;
     S *aux = buf1 + Op::NV * plane;
-    if (!down_body<Op, STG>(op, G, smem_raw, buf0, buf1, aux, P, br, g0, err)) return;
+    if (!down_body<Op, STG>(op, G, smem_raw, buf0, buf1, aux, P, br, g0, err, I, J)) return;
     // Down(I,J) in frame o+h is Up(I,J) of frame h when o = 0, and Up(I+1,J+1)
     // of frame 0 when o = h.
-    int I = blockIdx.x, J = blockIdx.y;
     if (o != 0) {
         I = I + 1 == G.T ? 0 : I + 1;
         J = J + 1 == G.Q ? 0 : J + 1;
@@ -621,20 +642,28 @@ __global__ void __launch_bounds__(256) octahedron_kernel(Op op, Geom G, const ty
     up_body(op, G, buf0, buf1, aux, P, g0 + h, up, J * G.T + I, h & 1);
 }
 
+template <class Op, bool STG>
+__global__ void __launch_bounds__(256) octahedron_kernel(Op op, Geom G, const typename Op::S *br,
+                                                         typename Op::S *up, int o, u64 g0,
+                                                         int *err) {
+    octahedron_tile<Op, STG>(op, G, br, up, o, g0, err, blockIdx.x, blockIdx.y);
+}
+
 // K4: final Down of an advance; writes the tile at level h to the state.
 template <class Op, bool STG>
-__global__ void __launch_bounds__(256) down_kernel(Op op, Geom G, const typename Op::S *br,
-                                                   typename Op::S *state, int o, u64 g0, int *err) {
+__device__ __forceinline__ void down_tile(const Op &op, const Geom &G, const typename Op::S *br,
+                                          typename Op::S *state, int o, u64 g0, int *err, int I,
+                                          int J) {
     typedef typename Op::S S;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = G.n, h = n / 2, P = n + 2, plane = P * P;
     S *buf0 = reinterpret_cast<S *>(smem_raw);
     S *buf1 = buf0 + Op::NV * plane;
     S *aux = buf1 + Op::NV * plane;
-    if (!down_body<Op, STG>(op, G, smem_raw, buf0, buf1, aux, P, br, g0, err)) return;
+    if (!down_body<Op, STG>(op, G, smem_raw, buf0, buf1, aux, P, br, g0, err, I, J)) return;
     const S *fin = (h & 1) ? buf1 : buf0;
     const size_t gplane = (size_t)G.nx * G.ny;
-    const int x0 = o + h + blockIdx.x * n, y0 = o + h + blockIdx.y * n;
+    const int x0 = o + h + I * n, y0 = o + h + J * n;
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
         const int b = e / n, a = e - b * n;
         int x = x0 + a; x -= x >= G.nx ? G.nx : 0;
@@ -643,6 +672,12 @@ __global__ void __launch_bounds__(256) down_kernel(Op op, Geom G, const typename
         for (int v = 0; v < Op::NV; ++v)
             state[v * gplane + (size_t)y * G.nx + x] = fin[v * plane + (b + 1) * P + (a + 1)];
     }
+}
+
+template <class Op, bool STG>
+__global__ void __launch_bounds__(256) down_kernel(Op op, Geom G, const typename Op::S *br,
+                                                   typename Op::S *state, int o, u64 g0, int *err) {
+    down_tile<Op, STG>(op, G, br, state, o, g0, err, blockIdx.x, blockIdx.y);
 }
 
 }  // namespace swept

@@ -170,6 +170,7 @@ const OpTable *optable_increment();
 const OpTable *optable_hash();
 const OpTable *optable_leveltag();
 const OpTable *optable_wide2();
+const OpTable *optable_wave();
 const OpTable *optable_heat_kahan_f32();
 const OpTable *optable_heat_kahan_bf16();
 

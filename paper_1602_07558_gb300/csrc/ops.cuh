@@ -86,6 +86,27 @@ struct HeatKahanOp {
     }
 };
 
+// 2D wave equation u_tt = c^2 laplace(u), leapfrog in time (Section 6's
+// experiment); point state (u^n, u^{n-1}):
+//   d = ((u_E + u_S) + (u_W + u_N)) - 4u,  u^{n+1} = (2u - u^{n-1}) + C^2 d (fused)
+// C2 = (c dt / dx)^2 is formed on the host.
+struct WaveOp {
+    typedef double S;
+    static constexpr int NV = 2, NST = 1, AUX = 0;
+    static constexpr bool STAGE = false;
+    double C2;
+    __host__ __device__ explicit WaveOp(const double *c) : C2(c[0]) {}
+    template <class A>
+    __device__ __forceinline__ void operator()(int, u64, const A &a, S *out) const {
+        const double c = a(0, 0, 0);
+        const double pe = __dadd_rn(a(1, 0, 0), a(0, 1, 0));
+        const double pw = __dadd_rn(a(-1, 0, 0), a(0, -1, 0));
+        const double d = __fma_rn(-4.0, c, __dadd_rn(pe, pw));
+        out[0] = __fma_rn(C2, d, __dsub_rn(__dmul_rn(2.0, c), a(0, 0, 1)));
+        out[1] = c;
+    }
+};
+
 // Section 3.1 worked example: u' = u + 1.
 struct IncrementOp {
     typedef double S;

@@ -17,6 +17,8 @@ Generators (numpy ``default_rng``, PCG64):
   returned as the conserved variables (rho, rho u, rho v, E) with
   E = p / (gamma - 1).
 * ``random_words`` -- i.i.d. 64-bit words.
+* ``wave_source``  -- a Gaussian bump of width ``sigma`` grid points at the
+  centre of the grid (the wave equation's initial source), at rest.
 """
 from __future__ import annotations
 
@@ -66,3 +68,11 @@ def euler_pulse(nx: int, ny: int, seed: int, gamma: float = 1.4, literal: bool =
 def random_words(nx: int, ny: int, seed: int, nv: int = 1) -> np.ndarray:
     rng = np.random.default_rng(seed)
     return rng.integers(0, 2**64, size=(nv, ny, nx), dtype=np.uint64)
+
+
+def wave_source(nx: int, ny: int, sigma: float = 4.0) -> np.ndarray:
+    """(u^0, u^{-1}) of a source at rest at the grid centre, shape (2, ny, nx)."""
+    x = np.arange(nx, dtype=np.float64)[None, :] - nx / 2
+    y = np.arange(ny, dtype=np.float64)[:, None] - ny / 2
+    u = np.exp(-(x * x + y * y) / (sigma * sigma))
+    return np.stack([u, u.copy()])

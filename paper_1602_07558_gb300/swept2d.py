@@ -22,7 +22,7 @@ from . import build as _build
 
 OK, EINVAL, ECUDA, ENOMEM, ETIMEOUT, ESTATE = 0, -1, -2, -3, -4, -5
 OPS = {"heat": 0, "euler_rk2": 1, "increment": 2, "hash": 3, "leveltag": 4, "wide2": 5,
-       "heat_kahan": 6}
+       "heat_kahan": 6, "wave": 7}
 DTYPES = {"f64": (0, np.float64), "f32": (1, np.float32), "bf16": (2, np.uint16),
           "u64": (3, np.uint64)}
 # (nvars, nstages, default dtype) of each point update; bf16 states are passed
@@ -35,10 +35,12 @@ OP_SHAPE = {
     "leveltag": (1, 1, "f64"),
     "wide2": (5, 2, "u64"),
     "heat_kahan": (2, 1, "f32"),
+    "wave": (2, 1, "f64"),
 }
 MODES = {"swept": 0, "naive": 1}
+GRAPH = 0x100
 Q = {"dt": 0, "wavespeed": 1, "substeps": 2, "launches": 3, "state_bytes": 4,
-     "panel_bytes": 5, "smem_bytes": 6}
+     "panel_bytes": 5, "smem_bytes": 6, "cells": 7}
 KERNELS = {"naive": 0, "up": 1, "bridge": 2, "octahedron": 3, "down": 4, "reduce": 5}
 
 _lock = threading.Lock()
@@ -159,8 +161,11 @@ class Swept2D:
         self._check(lib().swept2d_set_state(self._h, ptr, dev))
         del keep
 
-    def advance(self, nsteps, mode="swept"):
-        self._check(lib().swept2d_advance(self._h, int(nsteps), MODES[mode]))
+    def advance(self, nsteps, mode="swept", graph=False):
+        """``graph=True`` replays a captured CUDA graph of the launch sequence
+        (needs a handle created with a non-default stream)."""
+        m = MODES[mode] | (GRAPH if graph else 0)
+        self._check(lib().swept2d_advance(self._h, int(nsteps), m))
 
     def get_state(self, out=None):
         if out is None:
@@ -228,3 +233,121 @@ def heat_advance_static(u_in, u_out, nx, ny, tile, r, nsteps, stream=None):
             _stream_handle(stream), err, 256)
     if rc != OK:
         raise SweptError(rc, err.value.decode())
+
+
+class SweptBatch:
+    """Many independent periodic grids of uneven sizes advanced together
+    (swept2d_batch_*). ``tiles[i]`` is grid i's tile side (0: naive only).
+    States are numpy arrays or torch tensors holding the grids' states
+    concatenated in grid order; ``split`` cuts such a buffer into per-grid
+    (nvars, ny, nx) views."""
+
+    def __init__(self, nx, ny, tiles, op="heat", params=(), stream=None, dtype=None):
+        if op not in OPS:
+            raise ValueError(f"unknown op {op!r}")
+        self.nx = [int(v) for v in nx]
+        self.ny = [int(v) for v in ny]
+        self.tiles = [int(v) for v in tiles]
+        if not (len(self.nx) == len(self.ny) == len(self.tiles)):
+            raise ValueError("nx, ny and tiles differ in length")
+        self.op = op
+        self.nvars, self.nstages, default = OP_SHAPE[op]
+        self.dtype = dtype or default
+        self._dtype_code, self.np_dtype = DTYPES[self.dtype]
+        self.params = tuple(float(p) for p in params)
+        self._stream = _stream_handle(stream)
+        L = lib()
+        self._fns(L)
+        n = len(self.nx)
+        arr = lambda v: (ctypes.c_int * n)(*v)
+        prm = (ctypes.c_double * max(1, len(self.params)))(*self.params)
+        self._h = ctypes.c_void_p()
+        rc = L.swept2d_batch_create(ctypes.byref(self._h), n, arr(self.nx), arr(self.ny),
+                                    arr(self.tiles), OPS[op], prm, len(self.params),
+                                    self._dtype_code, self._stream)
+        if rc != OK:
+            raise SweptError(rc, L.swept2d_batch_last_error(None).decode())
+        self.sizes = [self.nvars * a * b for a, b in zip(self.nx, self.ny)]
+        self.total = sum(self.sizes)
+
+    @staticmethod
+    def _fns(L):
+        if getattr(L, "_batch_ready", False):
+            return
+        vp, i, ll, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong, ctypes.c_double
+        ip = ctypes.POINTER(ctypes.c_int)
+        L.swept2d_batch_create.argtypes = [ctypes.POINTER(vp), i, ip, ip, ip, i,
+                                           ctypes.POINTER(d), i, i, vp]
+        L.swept2d_batch_set_state.argtypes = [vp, vp, i]
+        L.swept2d_batch_advance.argtypes = [vp, ll, i]
+        L.swept2d_batch_get_state.argtypes = [vp, vp, i]
+        L.swept2d_batch_set_tuning.argtypes = [vp, i, i]
+        L.swept2d_batch_destroy.argtypes = [vp]
+        L.swept2d_batch_last_error.argtypes = [vp]
+        L.swept2d_batch_last_error.restype = ctypes.c_char_p
+        L.swept2d_batch_query.argtypes = [vp, i, ctypes.POINTER(d)]
+        for name in ("swept2d_batch_create", "swept2d_batch_set_state", "swept2d_batch_advance",
+                     "swept2d_batch_get_state", "swept2d_batch_set_tuning",
+                     "swept2d_batch_destroy", "swept2d_batch_query"):
+            getattr(L, name).restype = i
+        L._batch_ready = True
+
+    def _check(self, rc):
+        if rc != OK:
+            raise SweptError(rc, lib().swept2d_batch_last_error(self._h).decode())
+
+    def split(self, flat):
+        out, off = [], 0
+        for a, b, n in zip(self.nx, self.ny, self.sizes):
+            out.append(flat[off:off + n].reshape(self.nvars, b, a))
+            off += n
+        return out
+
+    def pack(self, states):
+        return np.concatenate([np.ascontiguousarray(s, dtype=self.np_dtype).reshape(-1)
+                               for s in states])
+
+    def set_state(self, state):
+        if isinstance(state, (list, tuple)):
+            state = self.pack(state)
+        nbytes = self.total * np.dtype(self.np_dtype).itemsize
+        ptr, dev, keep = _buffer(state, self.np_dtype, nbytes)
+        self._check(lib().swept2d_batch_set_state(self._h, ptr, dev))
+        del keep
+
+    def advance(self, nsteps, mode="swept", graph=False):
+        m = MODES[mode] | (GRAPH if graph else 0)
+        self._check(lib().swept2d_batch_advance(self._h, int(nsteps), m))
+
+    def get_state(self, out=None):
+        if out is None:
+            out = np.empty(self.total, dtype=self.np_dtype)
+        nbytes = self.total * np.dtype(self.np_dtype).itemsize
+        ptr, dev, keep = _buffer(out, self.np_dtype, nbytes)
+        self._check(lib().swept2d_batch_get_state(self._h, ptr, dev))
+        return out
+
+    def set_tuning(self, threads=256, stage=False):
+        self._check(lib().swept2d_batch_set_tuning(self._h, int(threads), 1 if stage else 0))
+
+    def query(self, what):
+        v = ctypes.c_double()
+        self._check(lib().swept2d_batch_query(self._h, Q[what], ctypes.byref(v)))
+        return v.value
+
+    def close(self):
+        if self._h:
+            lib().swept2d_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -211,6 +211,52 @@ def test_tuning_gives_identical_bits(op, dtype, params, threads, stage):
     assert np.array_equal(got, naive)
 
 
+# ----------------------------------------------------------------------- wave
+
+@pytest.mark.parametrize("nx,ny,tile,nsteps", [(64, 64, 16, 100), (96, 64, 32, 45), (48, 32, 8, 19)])
+def test_wave_swept_equals_naive_and_oracle(oracle_lib, nx, ny, tile, nsteps):
+    """Leapfrog wave (Section 6's experiment, Courant number 0.3): the 2-value
+    point state (u^n, u^{n-1}) through every swept component, bitwise."""
+    u0 = inputs.wave_source(nx, ny)
+    ref_u, ref_uo = oracle_lib.wave(u0[0], u0[1], 0.3 * 0.3, nsteps)
+    swept = run("wave", u0, nsteps, tile, "swept", (0.3,))
+    naive = run("wave", u0, nsteps, tile, "naive", (0.3,))
+    assert np.array_equal(swept, naive)
+    assert np.array_equal(swept[0], ref_u) and np.array_equal(swept[1], ref_uo)
+
+
+# ------------------------------------------------------------- CUDA graphs
+
+@pytest.mark.parametrize("op,mode,nsteps", [
+    ("heat", "swept", 40), ("heat", "naive", 13), ("heat", "swept", 37),
+    ("hash", "swept", 21), ("heat_kahan", "swept", 45),
+])
+def test_graph_replay_gives_the_same_bits(op, mode, nsteps):
+    """The first graph-mode advance is captured, the next ones replay it; an
+    odd naive tail swaps the state buffers between replays, and the hash
+    update keys its graphs by the starting sub-step. Three advances in a row
+    must equal three plain advances bit for bit."""
+    nx, ny, tile = 64, 48, 16
+    rng = np.random.default_rng(5)
+    dtype = {"heat": "f64", "hash": "u64", "heat_kahan": "f32"}[op]
+    params = () if op == "hash" else (0.2,)
+    if op == "hash":
+        u0 = rng.integers(0, 2**64, size=(1, ny, nx), dtype=np.uint64)
+    elif op == "heat":
+        u0 = rng.random((1, ny, nx))
+    else:
+        u0 = np.stack([rng.random((ny, nx)), np.zeros((ny, nx))]).astype(np.float32)
+    plain = run(op, u0, None, tile, mode, params, chunks=[nsteps] * 3, dtype=dtype)
+    stream = torch.cuda.Stream()
+    with Swept2D(nx, ny, op=op, tile=tile, params=params, dtype=dtype, stream=stream) as s:
+        s.set_state(np.ascontiguousarray(u0))
+        for _ in range(3):
+            s.advance(nsteps, mode=mode, graph=True)
+        got = s.get_state()
+        assert s.query("substeps") == 3 * nsteps
+    assert np.array_equal(got, plain)
+
+
 # ------------------------------------------------------ full-size sampled check
 
 def test_heat_4096_tile_32_full_grid_matches_oracle(oracle_lib):

@@ -70,3 +70,19 @@ def test_null_handles_are_rejected_without_a_device():
     assert L.swept2d_destroy(None) == swept2d.OK
     out = ctypes.c_double()
     assert L.swept2d_query(None, 0, ctypes.byref(out)) == swept2d.EINVAL
+
+
+@pytest.mark.parametrize("tiles,needle", [
+    ([16, 10], "tile 10"),        # 10 does not divide 48
+    ([16, 5], "tile 5"),
+])
+def test_batch_create_rejects_bad_tiles(tiles, needle):
+    with pytest.raises(swept2d.SweptError) as ei:
+        swept2d.SweptBatch([32, 48], [32, 48], tiles, op="heat", params=(0.2,))
+    assert ei.value.code == swept2d.EINVAL and needle in str(ei.value)
+
+
+def test_batch_create_rejects_unsupported_ops():
+    with pytest.raises(swept2d.SweptError) as ei:
+        swept2d.SweptBatch([32], [32], [16], op="euler_rk2", params=(1.4, 0.3, 0.5))
+    assert "not supported" in str(ei.value)

@@ -374,3 +374,39 @@ def test_heat_kahan_bf16_storage_keeps_small_increments(oracle_lib):
     assert np.max(np.abs(ref - 1.0)) < 0.25 * 0.2          # the mode really decayed
     assert err_kahan < 3 * rep_err
     assert err_plain > 10 * err_kahan
+
+
+# ------------------------------------------------------------------------ wave
+
+@pytest.mark.parametrize("T", [50, 400])
+def test_wave_single_mode_oscillates_with_the_leapfrog_frequency(oracle_lib, T):
+    """For a mode with discrete Laplacian eigenvalue lam, the leapfrog recurrence
+    u^{n+1} = (2 + C^2 lam) u^n - u^{n-1} has u^n = cos(n th) mode with
+    cos th = 1 + C^2 lam / 2 when u^{-1} = cos(th) mode (Section 6's CFL 0.3)."""
+    n, p, q, C2 = 32, 2, 3, 0.3 ** 2
+    mode = inputs.fourier_mode(n, n, p, q)
+    lam = -4 * (np.sin(np.pi * p / n) ** 2 + np.sin(np.pi * q / n) ** 2)
+    th = np.arccos(1 + C2 * lam / 2)
+    u, uo = oracle_lib.wave(mode, np.cos(th) * mode, C2, T)
+    assert np.max(np.abs(u - np.cos(T * th) * mode)) < 4 * T * EPS * 4
+    assert np.max(np.abs(uo - np.cos((T - 1) * th) * mode)) < 4 * T * EPS * 4
+
+
+def test_wave_impulse_response_and_mean_velocity(oracle_lib):
+    """One step from a unit impulse at rest: 2 - 1 - 4C^2 at the centre, C^2 at
+    the 4 edge neighbours; over many steps the mean velocity sum(u^n - u^{n-1})
+    is conserved (the Laplacian sums to zero on the periodic grid)."""
+    C2 = 0.09
+    u0 = np.zeros((9, 11))
+    u0[4, 5] = 1.0
+    u1, uo1 = oracle_lib.wave(u0, u0, C2, 1)
+    expect = np.zeros_like(u0)
+    expect[4, 5] = 1.0 - 4.0 * C2      # 4 C^2 is exact: one rounding, as in the fused form
+    for dj, di in [(0, 1), (0, -1), (1, 0), (-1, 0)]:
+        expect[4 + dj, 5 + di] = C2
+    assert np.allclose(u1, expect, rtol=0, atol=1e-16) and np.array_equal(uo1, u0)
+    rng = np.random.default_rng(3)
+    a, b = rng.random((20, 24)), rng.random((20, 24))
+    v0 = np.sum(a - b)
+    u, uo = oracle_lib.wave(a, b, C2, 300)
+    assert abs(np.sum(u - uo) - v0) < 1e-10
