@@ -60,7 +60,11 @@ class Workload:
     init: str
     seed: int
     describe: str = ""
-    # algorithmic FP64 pipe operations per cell-update (0 = not an FP64-pipe workload)
+    # algorithmic FP64 pipe operations per point and sub-step (0 = not an FP64-pipe
+    # workload): heat 4 (one own pair sum, one sum, two fused multiply-adds);
+    # wave 6 (the same Laplacian, 2u - u_old, one fused multiply-add); Euler 64
+    # per stage (one evaluation of each point's fluxes, 16 with the division
+    # counted as one, shared by its 4 neighbours, and 12 per conserved variable)
     fp64_ops: int = 0
     extra: dict = field(default_factory=dict)
 
@@ -80,14 +84,14 @@ WORKLOADS = {
                               "heat 2048x2048, bfloat16 storage, binary32 arithmetic, Kahan-"
                               "compensated update, r=0.2, 100000 steps"),
     "euler2048": Workload("euler_rk2", "f64", 2048, 5_000, 16, (GAMMA, CFL, KAPPA), "euler", 2,
-                          "Euler 2048x2048 FP64, midpoint RK2, CFL 0.3, 5000 steps"),
+                          "Euler 2048x2048 FP64, midpoint RK2, CFL 0.3, 5000 steps", 64),
     "batch1024": Workload("heat_kahan", "f32", 0, 20_000, 0, (0.2,), "batch", 3,
                           "1024 independent periodic grids, nx and ny uniform in {32,48,...,512} "
                           "(seed 3), heat with binary32 storage and Kahan-compensated update, "
                           "r=0.2, 20000 steps"),
     "wave1024": Workload("wave", "f64", 1024, 10_000, 32, (0.3,), "source", 0,
                          "wave 1024x1024 FP64 leapfrog, Courant 0.3, Gaussian source at the "
-                         "centre, 10000 steps"),
+                         "centre, 10000 steps", 6),
 }
 
 
@@ -264,6 +268,23 @@ def run_reference(args, w, rank):
     }), flush=True)
 
 
+# ------------------------------------------------------------- ranks
+
+def aggregate_over_ranks(ms_local, cells_local, nsteps, dist=None, device="cpu"):
+    """Replicas only: every rank advanced its own grid of ``cells_local`` points
+    by ``nsteps`` steps in ``ms_local`` ms. The job's time is the slowest
+    rank's; ``value`` counts the points of all ranks (Gcell-updates/s)."""
+    if dist is None:
+        return ms_local, cells_local * nsteps / (ms_local * 1e-3) / 1e9
+    import torch
+    t = torch.tensor([ms_local, float(cells_local)], dtype=torch.float64, device=device)
+    tmax = t.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    ms = float(tmax[0].item())
+    return ms, float(t[1].item()) * nsteps / (ms * 1e-3) / 1e9
+
+
 # ------------------------------------------------------------- rooflines
 
 def octahedron_updates(n):
@@ -398,17 +419,9 @@ def main():
         t_sw, launches = timed_steps(sw, "swept", args.steps, args.warmup)
         t_nv = timed_steps(nv, "naive", max(1, args.steps - 1), 1)[0] if nv else None
 
-    def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    ms_sw = max_over_ranks(statistics.mean(t_sw))
-    ms_nv = max_over_ranks(statistics.mean(t_nv)) if t_nv else None
-    value = world * cells * w.nsteps / (ms_sw * 1e-3) / 1e9
-    naive_value = world * cells * w.nsteps / (ms_nv * 1e-3) / 1e9 if ms_nv else None
+    ms_sw, value = aggregate_over_ranks(statistics.mean(t_sw), cells, w.nsteps, dist, "cuda")
+    ms_nv, naive_value = (aggregate_over_ranks(statistics.mean(t_nv), cells, w.nsteps, dist,
+                                               "cuda") if t_nv else (None, None))
 
     out_sw = sw.get_state()
     same = bool(np.array_equal(out_sw, nv.get_state())) if nv is not None else None
@@ -604,8 +617,9 @@ def run_batch(args, w, world, rank, local):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     torch.cuda.synchronize()
     nsteps = w.nsteps
-    tiles, stage, tune_table = autotune_batch(nx, ny, w.op, w.params, dtype=w.dtype,
-                                              stream=stream)
+    tiles, class_tuning, tune_table = autotune_batch(nx, ny, w.op, w.params, dtype=w.dtype,
+                                                     stream=stream)
+    stage = {str(k): v for k, v in class_tuning.items()}
 
     def timed(b, mode, k, wu):
         ev0 = torch.cuda.Event(enable_timing=True)
@@ -629,7 +643,8 @@ def run_batch(args, w, world, rank, local):
     with ClockSampler(local) as clocks:
         with SweptBatch(nx, ny, tiles, op=w.op, params=w.params, stream=stream,
                         dtype=w.dtype) as sb:
-            sb.set_tuning(256, stage)
+            for tile_n, (thr, stg) in class_tuning.items():
+                sb.set_tuning(thr, stg, tile=tile_n)
             ms_sw, launches = timed(sb, "swept", args.steps, max(1, args.warmup // 3))
             out_sw = sb.get_state()
             h_in = torch.from_numpy(flat.copy()).pin_memory()
@@ -700,7 +715,8 @@ def run_batch(args, w, world, rank, local):
             "warmup": max(1, args.warmup // 3), "ms_per_step": ms_sw, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": w.dtype, "data": "synthetic",
             "config": {"workload": w.describe, "grids": count, "cells": cells,
-                       "tiles_chosen": class_counts, "stage": stage, "autotune": tune_table,
+                       "tiles_chosen": class_counts, "class_tuning (threads, stage)": stage,
+                       "autotune": tune_table,
                        "cuda_graph": True, "l2": "flushed (256 MB write) between timed steps"},
             "naive_batched": {"value": naive_value, "unit": UNIT, "ms_per_step": naive_ms,
                               "note": "one naive launch per sub-step covering all grids, graph"},

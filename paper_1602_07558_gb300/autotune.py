@@ -87,11 +87,11 @@ def size_class(nx, ny, tiles=(16, 32, 64)):
 
 
 def autotune_batch(nx, ny, op, params, dtype=None, state=None, stream=None, probe_steps=64,
-                   tiles=(16, 32, 64), stages=(False, True), threads=256):
+                   tiles=(16, 32, 64), stages=(False, True), threads=(64, 128, 256)):
     """Per size class (grids sharing the same candidate tiles), time each
-    candidate tile on that class's own grids (a batch of them, so the probe
-    launches have the real width) and keep the fastest. Returns
-    (tiles per grid, stage, table)."""
+    candidate tile, threads per block and staging on that class's own grids (a
+    batch of them, so the probe launches have the real width) and keep the
+    fastest. Returns (tiles per grid, {tile: (threads, stage)}, table)."""
     import numpy as np
     import torch
 
@@ -110,39 +110,38 @@ def autotune_batch(nx, ny, op, params, dtype=None, state=None, stream=None, prob
         sub_ny = [ny[i] for i in members]
         best = None
         for n in cand:
-            for st in stages:
-                try:
-                    b = SweptBatch(sub_nx, sub_ny, [n] * len(members), op=op, params=params,
-                                   stream=stream, dtype=dtype)
-                except SweptError:
-                    continue
-                with b:
-                    try:
-                        b.set_tuning(threads, st)
-                    except SweptError:
-                        continue
-                    zeros = torch.zeros(b.total, device="cuda",
-                                        dtype=_torch_dtype(b.np_dtype))
-                    ev0 = torch.cuda.Event(enable_timing=True)
-                    ev1 = torch.cuda.Event(enable_timing=True)
-                    ms = None
-                    for rep in range(2):
-                        with torch.cuda.stream(stream):
-                            b.set_state(zeros)
-                            ev0.record(stream)
-                            b.advance(probe_steps, graph=True)
-                            ev1.record(stream)
-                        ev1.synchronize()
-                        ms = ev0.elapsed_time(ev1)
-                    cells = float(np.sum(np.array(sub_nx) * np.array(sub_ny)))
-                    row = {"class": list(cand), "grids": len(members), "tile": n, "stage": st,
-                           "ms": ms, "gcell_per_s": cells * probe_steps / (ms * 1e-3) / 1e9}
-                    table.append(row)
-                    if best is None or ms < best["ms"]:
-                        best = row
+            try:
+                b = SweptBatch(sub_nx, sub_ny, [n] * len(members), op=op, params=params,
+                               stream=stream, dtype=dtype)
+            except SweptError:
+                continue
+            with b:
+                zeros = torch.zeros(b.total, device="cuda", dtype=_torch_dtype(b.np_dtype))
+                for t in threads:
+                    for st in stages:
+                        try:
+                            b.set_tuning(t, st)
+                        except SweptError:
+                            continue
+                        ev0 = torch.cuda.Event(enable_timing=True)
+                        ev1 = torch.cuda.Event(enable_timing=True)
+                        ms = None
+                        for rep in range(2):
+                            with torch.cuda.stream(stream):
+                                b.set_state(zeros)
+                                ev0.record(stream)
+                                b.advance(probe_steps, graph=True)
+                                ev1.record(stream)
+                            ev1.synchronize()
+                            ms = ev0.elapsed_time(ev1)
+                        cells = float(np.sum(np.array(sub_nx) * np.array(sub_ny)))
+                        row = {"class": list(cand), "grids": len(members), "tile": n,
+                               "threads": t, "stage": st, "ms": ms,
+                               "gcell_per_s": cells * probe_steps / (ms * 1e-3) / 1e9}
+                        table.append(row)
+                        if best is None or ms < best["ms"]:
+                            best = row
         for i in members:
             choice[i] = best["tile"]
-        best_stage[cand] = best["stage"]
-    # one staging choice for the whole batch: the one most classes preferred
-    stage = sum(best_stage.values()) * 2 > len(best_stage)
-    return choice, stage, table
+        best_stage[best["tile"]] = (best["threads"], best["stage"])
+    return choice, best_stage, table

@@ -26,6 +26,7 @@ namespace {
 
 struct BatchClass {
     int n = 0;                 // tile side (0: naive-only grids)
+    swept::Tuning tune;        // launch shape of this class's swept kernels
     std::vector<int> members;  // grid indices
     std::vector<int2> tiles;   // (grid, tile) for the swept launches
     std::vector<int2> blocks;  // (grid, 32x8 block) for the naive tail
@@ -154,18 +155,18 @@ int batch_run(swept2d_batch *b, long long total, int mode) {
                 const int o = (j & 1) ? half : 0;
                 rc = blaunch(b, "batched bridge kernel", [&] {
                     return b->bt->bridge(b->d_grids, c.d_tiles, nt, c.n, b->consts, b->up, b->br,
-                                         g0, b->errword, b->tune, b->stream);
+                                         g0, b->errword, c.tune, b->stream);
                 });
                 if (rc) return rc;
                 if (j + 1 < H)
                     rc = blaunch(b, "batched octahedron kernel", [&] {
                         return b->bt->octahedron(b->d_grids, c.d_tiles, nt, c.n, b->consts, b->br,
-                                                 b->up, o, g0, b->errword, b->tune, b->stream);
+                                                 b->up, o, g0, b->errword, c.tune, b->stream);
                     });
                 else
                     rc = blaunch(b, "batched down kernel", [&] {
                         return b->bt->down(b->d_grids, c.d_tiles, nt, c.n, b->consts, b->br,
-                                           b->state, o, g0, b->errword, b->tune, b->stream);
+                                           b->state, o, g0, b->errword, c.tune, b->stream);
                     });
                 if (rc) return rc;
             }
@@ -303,6 +304,7 @@ int swept2d_batch_create(swept2d_batch_t **out, int count, const int *nx, const 
             b->classes.emplace_back();
             cls = &b->classes.back();
             cls->n = n;
+            cls->tune = b->tune;
         }
         cls->members.push_back(i);
         for (int t = 0; t < gd.G.T * gd.G.Q; ++t) cls->tiles.push_back(make_int2(i, t));
@@ -408,7 +410,27 @@ int swept2d_batch_set_tuning(swept2d_batch_t *b, int threads, int stage) {
             return bfail(b, SWEPT2D_EINVAL, "set_tuning: staged panels do not fit");
     b->tune.threads = threads;
     b->tune.stage = stage != 0;
+    for (auto &c : b->classes) c.tune = b->tune;
     return SWEPT2D_OK;
+}
+
+int swept2d_batch_set_class_tuning(swept2d_batch_t *b, int tile, int threads, int stage) {
+    if (!b) return SWEPT2D_EINVAL;
+    if (threads != 64 && threads != 128 && threads != 256)
+        return bfail(b, SWEPT2D_EINVAL, "set_class_tuning: threads must be 64, 128 or 256");
+    for (auto &c : b->classes) {
+        if (c.n != tile || tile == 0) continue;
+        int dev = 0, optin = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+            optin = 227 * 1024;
+        if (b->bt->smem_for(c.n, stage != 0) > (size_t)optin)
+            return bfail(b, SWEPT2D_EINVAL, "set_class_tuning: staged panels do not fit");
+        c.tune.threads = threads;
+        c.tune.stage = stage != 0;
+        return SWEPT2D_OK;
+    }
+    return bfail(b, SWEPT2D_EINVAL, "set_class_tuning: no class with that tile");
 }
 
 int swept2d_batch_destroy(swept2d_batch_t *b) {

@@ -259,6 +259,48 @@ __device__ __forceinline__ void compute_rect(const HeatOp &op, int, u64, const d
     }
 }
 
+// Euler: the x- and y-fluxes of every point of the rectangle grown by one are
+// formed once per level into 8 aux planes (pass 1, one evaluation of the
+// primitives per point), and each point then combines its neighbours' fluxes
+// (pass 2): each point's fluxes are used by its 4 neighbours instead of being
+// recomputed by each of them. Same values as EulerOp::operator().
+__device__ __forceinline__ void compute_rect(const EulerOp &op, int stage, u64, const double *src,
+                                             double *dst, double *aux, int P, int x0, int y0,
+                                             int W, int H) {
+    const int plane = P * P, w0 = stage == 0 ? 0 : 4;
+    if (W <= 0 || H <= 0) return;
+    for (LinearWalk w(W + 2); w.yy < H + 2; w.next(W + 2)) {
+        const int off = (y0 + w.yy) * P + (x0 + w.xx);     // point (x0-1+xx, y0-1+yy)
+        double F[4], G[4];
+        op.fluxes(src[w0 * plane + off], src[(w0 + 1) * plane + off],
+                  src[(w0 + 2) * plane + off], src[(w0 + 3) * plane + off], F, G);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            aux[c * plane + off] = F[c];
+            aux[(4 + c) * plane + off] = G[c];
+        }
+    }
+    __syncthreads();
+    for (LinearWalk w(W); w.yy < H; w.next(W)) {
+        const int off = (y0 + w.yy + 1) * P + (x0 + w.xx + 1);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const double *Wc = src + (w0 + c) * plane + off;
+            const double *F = aux + c * plane + off, *G = aux + (4 + c) * plane + off;
+            double res;
+            op.combine(stage, c, Wc[0], Wc[1], Wc[-1], Wc[P], Wc[-P], __dsub_rn(F[1], F[-1]),
+                       __dsub_rn(G[P], G[-P]), src[c * plane + off], res);
+            if (stage == 0) {
+                dst[c * plane + off] = src[c * plane + off];
+                dst[(4 + c) * plane + off] = res;
+            } else {
+                dst[c * plane + off] = res;
+                dst[(4 + c) * plane + off] = src[(4 + c) * plane + off];
+            }
+        }
+    }
+}
+
 // Local coordinates of element (d, p) of an up panel side at level k.
 __device__ __forceinline__ void up_panel_xy(int side, int n, int k, int d, int p, int &a, int &b) {
     switch (side) {

@@ -196,7 +196,7 @@ struct Wide2Op {
 // Host-precomputed constants c[] = {gamma-1, cx, cy, kax, kay, tau0, tau1}.
 struct EulerOp {
     typedef double S;
-    static constexpr int NV = 8, NST = 2, AUX = 0;
+    static constexpr int NV = 8, NST = 2, AUX = 8;   // aux: F and G of a level
     static constexpr bool STAGE = false;
     double gm1, cx, cy, kax, kay, tau0, tau1;
     __host__ __device__ explicit EulerOp(const double *c)
@@ -219,6 +219,33 @@ struct EulerOp {
         F[2] = __dmul_rn(q, u);
         F[3] = __dmul_rn(Ep, u);
     }
+    // F and G of one point from one evaluation of its primitives (the same
+    // values xflux and yflux give)
+    __device__ __forceinline__ void fluxes(double r, double m, double q, double E, double *F,
+                                           double *G) const {
+        double u, v, pr, Ep;
+        prims(r, m, q, E, u, v, pr, Ep);
+        F[0] = m;
+        F[1] = __fma_rn(m, u, pr);
+        F[2] = __dmul_rn(q, u);
+        F[3] = __dmul_rn(Ep, u);
+        G[0] = q;
+        G[1] = __dmul_rn(m, v);
+        G[2] = __fma_rn(q, v, pr);
+        G[3] = __dmul_rn(Ep, v);
+    }
+    // the stage update of one point from its fluxes' differences (shared by the
+    // per-point operator below and the swept level computation)
+    __device__ __forceinline__ void combine(int stage, int c, double wc, double wE, double wW,
+                                            double wS, double wN, double dF, double dG,
+                                            double ubase, double &res) const {
+        const double tau = stage == 0 ? tau0 : tau1;
+        const double lx = __fma_rn(-2.0, wc, __dadd_rn(wE, wW));
+        const double ly = __fma_rn(-2.0, wc, __dadd_rn(wS, wN));
+        const double diss = __fma_rn(kax, lx, __dmul_rn(kay, ly));
+        const double flux = __fma_rn(cx, dF, __dmul_rn(cy, dG));
+        res = __fma_rn(tau, __dsub_rn(diss, flux), ubase);
+    }
     __device__ __forceinline__ void yflux(double r, double m, double q, double E, double *G) const {
         double u, v, pr, Ep;
         prims(r, m, q, E, u, v, pr, Ep);
@@ -230,7 +257,6 @@ struct EulerOp {
     template <class A>
     __device__ __forceinline__ void operator()(int stage, u64, const A &a, S *out) const {
         const int w0 = stage == 0 ? 0 : 4;
-        const double tau = stage == 0 ? tau0 : tau1;
         double FW[4], FE[4], GN[4], GS[4];
         xflux(a(-1, 0, w0), a(-1, 0, w0 + 1), a(-1, 0, w0 + 2), a(-1, 0, w0 + 3), FW);
         xflux(a(1, 0, w0), a(1, 0, w0 + 1), a(1, 0, w0 + 2), a(1, 0, w0 + 3), FE);
@@ -238,14 +264,10 @@ struct EulerOp {
         yflux(a(0, 1, w0), a(0, 1, w0 + 1), a(0, 1, w0 + 2), a(0, 1, w0 + 3), GS);
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-            const double wc = a(0, 0, w0 + c);
-            const double lx = __fma_rn(-2.0, wc, __dadd_rn(a(1, 0, w0 + c), a(-1, 0, w0 + c)));
-            const double ly = __fma_rn(-2.0, wc, __dadd_rn(a(0, 1, w0 + c), a(0, -1, w0 + c)));
-            const double diss = __fma_rn(kax, lx, __dmul_rn(kay, ly));
-            const double flux = __fma_rn(cx, __dsub_rn(FE[c], FW[c]),
-                                         __dmul_rn(cy, __dsub_rn(GS[c], GN[c])));
-            const double L = __dsub_rn(diss, flux);
-            const double res = __fma_rn(tau, L, a(0, 0, c));
+            double res;
+            combine(stage, c, a(0, 0, w0 + c), a(1, 0, w0 + c), a(-1, 0, w0 + c),
+                    a(0, 1, w0 + c), a(0, -1, w0 + c), __dsub_rn(FE[c], FW[c]),
+                    __dsub_rn(GS[c], GN[c]), a(0, 0, c), res);
             if (stage == 0) {
                 out[c] = a(0, 0, c);
                 out[4 + c] = res;

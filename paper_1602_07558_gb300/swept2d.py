@@ -282,12 +282,14 @@ class SweptBatch:
         L.swept2d_batch_advance.argtypes = [vp, ll, i]
         L.swept2d_batch_get_state.argtypes = [vp, vp, i]
         L.swept2d_batch_set_tuning.argtypes = [vp, i, i]
+        L.swept2d_batch_set_class_tuning.argtypes = [vp, i, i, i]
         L.swept2d_batch_destroy.argtypes = [vp]
         L.swept2d_batch_last_error.argtypes = [vp]
         L.swept2d_batch_last_error.restype = ctypes.c_char_p
         L.swept2d_batch_query.argtypes = [vp, i, ctypes.POINTER(d)]
         for name in ("swept2d_batch_create", "swept2d_batch_set_state", "swept2d_batch_advance",
                      "swept2d_batch_get_state", "swept2d_batch_set_tuning",
+                     "swept2d_batch_set_class_tuning",
                      "swept2d_batch_destroy", "swept2d_batch_query"):
             getattr(L, name).restype = i
         L._batch_ready = True
@@ -327,8 +329,13 @@ class SweptBatch:
         self._check(lib().swept2d_batch_get_state(self._h, ptr, dev))
         return out
 
-    def set_tuning(self, threads=256, stage=False):
-        self._check(lib().swept2d_batch_set_tuning(self._h, int(threads), 1 if stage else 0))
+    def set_tuning(self, threads=256, stage=False, tile=None):
+        """Launch shape of every class, or of the class with tile side ``tile``."""
+        if tile is None:
+            self._check(lib().swept2d_batch_set_tuning(self._h, int(threads), 1 if stage else 0))
+        else:
+            self._check(lib().swept2d_batch_set_class_tuning(self._h, int(tile), int(threads),
+                                                             1 if stage else 0))
 
     def query(self, what):
         v = ctypes.c_double()
