@@ -149,7 +149,7 @@ __device__ __forceinline__ bool block_wait_bulk(unsigned long long *bar, int *er
 // Threads take consecutive points of a W-wide rectangle (point e = t, t + T,
 // t + 2T, ... in row order, T = blockDim), so warps stay full; the (column,
 // row) of the next point follows by adding (T mod W, T div W) with a carry,
-// so a level costs two integer divisions per thread, not one per point.
+// so a level costs two reciprocal divisions per thread, not one per point.
 // q = floor(e / d) for 0 <= e < 2^20 and 1 <= d <= 2^10 via a binary32
 // reciprocal: (e + 1/2) / d is at least 1/(2d) away from an integer, far more
 // than the two roundings' error, so the truncation is exact.
@@ -161,9 +161,10 @@ struct LinearWalk {
     int xx, yy, dq, dr;
     __device__ __forceinline__ explicit LinearWalk(int W) {
         const int T = blockDim.x;
-        yy = (int)threadIdx.x / W;
+        const float rw = 1.0f / (float)W;
+        yy = div_small((int)threadIdx.x, rw);
         xx = (int)threadIdx.x - yy * W;
-        dq = T / W;
+        dq = div_small(T, rw);
         dr = T - dq * W;
     }
     __device__ __forceinline__ void next(int W) {
@@ -298,6 +299,32 @@ __device__ __forceinline__ void compute_rect(const EulerOp &op, int stage, u64, 
                 dst[(4 + c) * plane + off] = src[(4 + c) * plane + off];
             }
         }
+    }
+}
+
+// Wave: the same pair-sum sharing as the heat update (pass 1 forms the
+// east+south pair sums of the rectangle grown by one into the aux plane), then
+// u' = (2u - u_old) + C^2 d, u_old' = u.
+__device__ __forceinline__ void compute_rect(const WaveOp &op, int, u64, const double *src,
+                                             double *dst, double *aux, int P, int x0, int y0,
+                                             int W, int H) {
+    const int plane = P * P;
+    const int W1 = W + 1, cnt1 = W1 * (H + 1);
+    const float rw1 = 1.0f / (float)W1, rw = 1.0f / (float)W;
+    for (int e = threadIdx.x; e < cnt1; e += blockDim.x) {
+        const int yy = div_small(e, rw1), xx = e - yy * W1;
+        const int off = (y0 + yy) * P + (x0 + xx);      // point (x0-1+xx, y0-1+yy)
+        aux[off] = __dadd_rn(src[off + 1], src[off + P]);
+    }
+    __syncthreads();
+    const int cnt = W * H;
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+        const int yy = div_small(e, rw), xx = e - yy * W;
+        const int off = (y0 + yy + 1) * P + (x0 + xx + 1);
+        const double c = src[off];
+        const double d = __fma_rn(-4.0, c, __dadd_rn(aux[off], aux[off - P - 1]));
+        dst[off] = __fma_rn(op.C2, d, __dsub_rn(__dmul_rn(2.0, c), src[plane + off]));
+        dst[plane + off] = c;
     }
 }
 

@@ -92,7 +92,7 @@ struct HeatKahanOp {
 // C2 = (c dt / dx)^2 is formed on the host.
 struct WaveOp {
     typedef double S;
-    static constexpr int NV = 2, NST = 1, AUX = 0;
+    static constexpr int NV = 2, NST = 1, AUX = 1;   // aux: pair sums of a level
     static constexpr bool STAGE = false;
     double C2;
     __host__ __device__ explicit WaveOp(const double *c) : C2(c[0]) {}
