@@ -116,6 +116,8 @@ def parse():
                    help="pick tile, threads and staging by timing short runs first")
     p.add_argument("--graph", action="store_true",
                    help="run each advance (swept and naive) as a captured CUDA graph")
+    p.add_argument("--persistent", action="store_true",
+                   help="swept arm: one persistent launch per advance")
     a = p.parse_args()
     w = WORKLOADS[a.workload]
     for k in ("grid", "nsteps", "tile"):
@@ -416,7 +418,8 @@ def main():
         return times, int(s.query("launches") - launches0)
 
     with ClockSampler(local) as clocks:
-        t_sw, launches = timed_steps(sw, "swept", args.steps, args.warmup)
+        t_sw, launches = timed_steps(sw, "persistent" if args.persistent else "swept",
+                                     args.steps, args.warmup)
         t_nv = timed_steps(nv, "naive", max(1, args.steps - 1), 1)[0] if nv else None
 
     ms_sw, value = aggregate_over_ranks(statistics.mean(t_sw), cells, w.nsteps, dist, "cuda")
@@ -481,6 +484,7 @@ def main():
                        "stage": args.stage, "autotune": tune_table,
                        "parallelism": "replicas" if world > 1 else "single",
                        "cuda_graph": bool(args.graph),
+                       "persistent": bool(args.persistent),
                        "l2": "flushed (256 MB write) between timed steps"},
             "naive": {"value": naive_value, "unit": UNIT, "ms_per_step": ms_nv,
                       "roofline": naive_rf} if ms_nv else None,

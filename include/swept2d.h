@@ -106,6 +106,12 @@ typedef struct swept2d swept2d_t;
  * stream) and cached (up to 8 per handle); later ones replay it with one graph
  * launch. Results are the same bits as without the flag. */
 #define SWEPT2D_GRAPH 0x100
+/* Flag OR-ed into SWEPT2D_SWEPT: run all half cycles of the advance as one
+ * persistent launch (resident blocks take tile work items in phase order and
+ * wait, with bounded spins, only for their 3 x 3 tile neighbourhood to finish
+ * the previous phase), instead of two launches per half cycle. Needs the
+ * staged panel set to fit in shared memory (EINVAL otherwise). Same bits. */
+#define SWEPT2D_PERSISTENT 0x200
 
 /*
  * Create a handle for an nx x ny grid.
@@ -214,7 +220,10 @@ int swept2d_batch_create(swept2d_batch_t **out, int count, const int *nx, const 
 int swept2d_batch_set_state(swept2d_batch_t *b, const void *src, int src_is_device);
 int swept2d_batch_advance(swept2d_batch_t *b, long long nsteps, int mode);
 int swept2d_batch_get_state(swept2d_batch_t *b, void *dst, int dst_is_device);
+/* Launch shape (as swept2d_set_tuning) of every class, or of the class of one
+ * tile side (EINVAL if no grid uses it); never changes results. */
 int swept2d_batch_set_tuning(swept2d_batch_t *b, int threads, int stage);
+int swept2d_batch_set_class_tuning(swept2d_batch_t *b, int tile, int threads, int stage);
 int swept2d_batch_destroy(swept2d_batch_t *b);
 const char *swept2d_batch_last_error(const swept2d_batch_t *b);
 int swept2d_batch_query(const swept2d_batch_t *b, int what, double *out);

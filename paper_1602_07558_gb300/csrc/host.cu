@@ -52,6 +52,7 @@ struct swept2d {
     void *state = nullptr, *state2 = nullptr, *up = nullptr, *br = nullptr;
     unsigned long long *scratch8 = nullptr;
     int *errword = nullptr;   // set by a kernel whose bounded wait gave up
+    int *sched = nullptr;     // persistent form: T*Q phase counters + queue counter
     swept::Tuning tune;
     size_t state_bytes = 0, panel_bytes = 0, smem_bytes = 0;
     double consts[8] = {0};
@@ -167,6 +168,7 @@ void free_all(swept2d *h) {
     if (h->br) cudaFree(h->br);
     if (h->scratch8) cudaFree(h->scratch8);
     if (h->errword) cudaFree(h->errword);
+    if (h->sched) cudaFree(h->sched);
     for (auto &t : h->timed) {
         cudaEventDestroy(t.start);
         cudaEventDestroy(t.stop);
@@ -180,6 +182,7 @@ void free_all(swept2d *h) {
     h->state = h->state2 = h->up = h->br = nullptr;
     h->scratch8 = nullptr;
     h->errword = nullptr;
+    h->sched = nullptr;
 }
 
 int naive_substeps(swept2d *h, long long count) {
@@ -195,11 +198,22 @@ int naive_substeps(swept2d *h, long long count) {
     return SWEPT2D_OK;
 }
 
-int swept_substeps(swept2d *h, long long total) {
+int swept_substeps(swept2d *h, long long total, bool persistent) {
     const int half = h->n / 2;
     const long long H = total / half;
     const long long rem = total - H * half;
-    if (H > 0) {
+    if (H > 0 && persistent) {
+        const u64 g_start = (u64)h->substeps;
+        const size_t nsched = (size_t)h->G.T * h->G.Q + 1;
+        cudaError_t e = cudaMemsetAsync(h->sched, 0, nsched * sizeof(int), h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "persistent schedule reset");
+        int rc = launch(h, SWEPT2D_K_OCTAHEDRON, "persistent kernel", [&] {
+            return h->ops->persistent(h->G, h->consts, h->state, h->up, h->br, h->sched, (int)H,
+                                      g_start, h->errword, h->tune.threads, h->stream);
+        });
+        if (rc) return rc;
+        h->substeps += H * half;
+    } else if (H > 0) {
         const u64 g_start = (u64)h->substeps;
         int rc = launch(h, SWEPT2D_K_UP, "up kernel", [&] {
             return h->ops->up(h->G, h->consts, h->state, h->up, 0, g_start, h->stream);
@@ -232,7 +246,9 @@ int swept_substeps(swept2d *h, long long total) {
 }
 
 int run_advance(swept2d *h, long long total, int mode) {
-    return mode == SWEPT2D_SWEPT ? swept_substeps(h, total) : naive_substeps(h, total);
+    const bool persistent = (mode & SWEPT2D_PERSISTENT) != 0;
+    mode &= ~SWEPT2D_PERSISTENT;
+    return mode == SWEPT2D_SWEPT ? swept_substeps(h, total, persistent) : naive_substeps(h, total);
 }
 
 // Advance through a captured CUDA graph of the whole launch sequence.
@@ -441,10 +457,29 @@ int swept2d_advance(swept2d_t *h, long long nsteps, int mode) {
     if (nsteps < 0) return fail(h, SWEPT2D_EINVAL, "advance: nsteps < 0");
     if (!h->has_state) return fail(h, SWEPT2D_ESTATE, "advance: no state set");
     const bool graph = (mode & SWEPT2D_GRAPH) != 0;
-    mode &= ~SWEPT2D_GRAPH;
+    const int persistent = mode & SWEPT2D_PERSISTENT;
+    mode &= ~(SWEPT2D_GRAPH | SWEPT2D_PERSISTENT);
     if (mode != SWEPT2D_SWEPT && mode != SWEPT2D_NAIVE) return fail(h, SWEPT2D_EINVAL, "advance: bad mode");
     if (mode == SWEPT2D_SWEPT && h->n == 0)
         return fail(h, SWEPT2D_EINVAL, "advance: swept mode needs a tile (created with tile 0)");
+    if (persistent) {
+        if (mode != SWEPT2D_SWEPT) return fail(h, SWEPT2D_EINVAL, "advance: persistent needs the swept mode");
+        int dev = 0, optin = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+            optin = 227 * 1024;
+        if (h->ops->smem_for(h->n, true) > (size_t)optin)
+            return fail(h, SWEPT2D_EINVAL, "advance: persistent form needs staged panels, which do not fit");
+        const long long nitems =
+            (long long)h->G.T * h->G.Q * (2 * (nsteps * h->nst / (h->n / 2)) + 1);
+        if (nitems >= (1LL << 31))
+            return fail(h, SWEPT2D_EINVAL, "advance: too many work items for one persistent launch");
+        if (!h->sched) {
+            cudaError_t e = cudaMalloc(&h->sched, ((size_t)h->G.T * h->G.Q + 1) * sizeof(int));
+            if (e != cudaSuccess) return cuda_fail(h, e, "persistent schedule allocation");
+        }
+        mode |= persistent;
+    }
     if (graph) {
         if (!h->stream) return fail(h, SWEPT2D_EINVAL, "advance: graph mode needs a created stream");
         return graph_advance(h, nsteps, mode);

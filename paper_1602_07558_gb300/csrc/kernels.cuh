@@ -128,6 +128,10 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned 
         : "memory");
     return ok != 0;
 }
+__device__ __forceinline__ void mbar_inval(unsigned long long *bar) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+
 // Every thread waits for phase 0 of `bar`; returns false (the same for the
 // whole block) if the wait gave up, after recording it in *err.
 __device__ __forceinline__ bool block_wait_bulk(unsigned long long *bar, int *err) {
@@ -537,6 +541,7 @@ __device__ __forceinline__ void bridge_tile(const Op &op, const Geom &G, const t
                     bulk_g2s(st + (w * NV + v) * G.PS, seg[w] + (size_t)v * G.PS, bytes, bar);
         }
         if (!block_wait_bulk(bar, err)) return;
+        if (threadIdx.x == 0) mbar_inval(bar);   // the block may stage again (persistent form)
         stg = st;
     }
     const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -640,6 +645,7 @@ __device__ __forceinline__ bool down_body(const Op &op, const Geom &G, unsigned 
                     bulk_g2s(st + (side * NV + v) * G.PS, seg[side] + (size_t)v * G.PS, bytes, bar);
         }
         if (!block_wait_bulk(bar, err)) return false;
+        if (threadIdx.x == 0) mbar_inval(bar);
         stg = st;
     }
     const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -747,6 +753,110 @@ template <class Op, bool STG>
 __global__ void __launch_bounds__(256) down_kernel(Op op, Geom G, const typename Op::S *br,
                                                    typename Op::S *state, int o, u64 g0, int *err) {
     down_tile<Op, STG>(op, G, br, state, o, g0, err, blockIdx.x, blockIdx.y);
+}
+
+// ------------------------------------------------------- persistent form
+// One launch runs a whole swept advance: resident blocks take work items from
+// an atomic queue in phase order (phase 1: every tile's first Up; then per half
+// cycle j a bridge item (both bridges of a slot) and an octahedron item per
+// tile, or the final Down items), and an item of phase p on tile t starts once
+// every tile of t's periodic 3 x 3 neighbourhood has finished phase p-1. That
+// neighbourhood holds every producer of the item's inputs and every reader of
+// the panels it overwrites (the frame shift moves a tile's panels by at most
+// one slot), so the kernel boundaries of the launch-per-phase schedule are
+// replaced by those waits. Items are taken in index order and every dependency
+// has a smaller index, so the lowest unfinished item can always run: no
+// deadlock, whatever number of blocks is resident. Panels written by one block
+// are read by another through TMA bulk copies (L2) after an acquire and a
+// generic-to-async proxy fence, so no stale L1 line is ever read. Waits are
+// bounded: on timeout the error word is set and the block stops.
+// a dependency is at most one work item away (about a millisecond): the
+// bound (about a second of 64 ns naps) only catches a block that never finishes
+constexpr long long kPersistSpinLimit = 1LL << 24;
+
+__device__ __forceinline__ int ld_acquire(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(int *p, int v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;\n" ::"l"(p), "r"(v) : "memory");
+}
+
+template <class Op>
+__global__ void __launch_bounds__(256) persistent_kernel(Op op, Geom G, typename Op::S *state,
+                                                         typename Op::S *upp, typename Op::S *br,
+                                                         int *stage, int *queue, int H, u64 g0,
+                                                         int *err) {
+    __shared__ int s_item, s_fail;
+    const int NT = G.T * G.Q, h = G.n / 2;
+    const int nitems = NT * (2 * H + 1);
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_item = atomicAdd(queue, 1);
+            s_fail = 0;
+        }
+        __syncthreads();
+        const int item = s_item;
+        if (item >= nitems) return;
+        const int p = item / NT + 1, t = item - (p - 1) * NT;
+        const int J = t / G.T, I = t - J * G.T;
+        if (p > 1 && threadIdx.x == 0) {
+            for (int dj = -1; dj <= 1 && !s_fail; ++dj) {
+                const int jj = J + dj < 0 ? G.Q - 1 : (J + dj == G.Q ? 0 : J + dj);
+                for (int di = -1; di <= 1 && !s_fail; ++di) {
+                    const int ii = I + di < 0 ? G.T - 1 : (I + di == G.T ? 0 : I + di);
+                    const int *flag = stage + jj * G.T + ii;
+                    long long it = 0;
+                    while (ld_acquire(flag) < p - 1) {
+                        // give up after the bound, or at once when another
+                        // block has already recorded a failure
+                        const bool other = err && (++it & 255) == 0 && ld_acquire(err) != 0;
+                        if (other || it > kPersistSpinLimit) {
+                            if (err) atomicExch(err, 2);
+                            s_fail = 1;
+                            break;
+                        }
+                        __nanosleep(64);
+                    }
+                }
+            }
+            asm volatile("fence.proxy.async.global;\n" ::: "memory");
+        }
+        __syncthreads();
+        if (s_fail) return;
+        if (p == 1) {
+            up_tile(op, G, state, upp, 0, g0, I, J);
+        } else {
+            const int j = (p - 2) / 2;              // half cycle
+            const u64 gj = g0 + (u64)j * h;
+            const int o = (j & 1) ? h : 0;
+            if ((p & 1) == 0) {                     // bridges of half cycle j
+                bridge_tile<Op, true>(op, G, upp, br, gj, err, I, J, false);
+                __syncthreads();
+                bridge_tile<Op, true>(op, G, upp, br, gj, err, I, J, true);
+            } else if (j + 1 < H) {
+                octahedron_tile<Op, true>(op, G, br, upp, o, gj, err, I, J);
+            } else {
+                down_tile<Op, true>(op, G, br, state, o, gj, err, I, J);
+            }
+        }
+        // make this item's panel (and state) stores visible, to the generic and
+        // the async proxy, before the release of its phase; order this item's
+        // shared-memory accesses before the next item's bulk copies into it
+        asm volatile("fence.proxy.async.global;\n" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            st_release(stage + t, p);
+            // a failed bulk wait in this item ends the block (its waiters see
+            // the error word and stop too)
+            s_fail = err ? ld_acquire(err) : 0;
+        }
+        __syncthreads();
+        if (s_fail) return;
+    }
 }
 
 }  // namespace swept

@@ -34,6 +34,10 @@ struct OpTable {
                         int *err, const Tuning &tn, cudaStream_t);
     bool default_stage;
     size_t (*smem_for)(int n, bool stage);   // largest swept block's shared memory
+    // the whole swept part of an advance (H half cycles) as one persistent
+    // launch; sched: T*Q phase counters followed by the queue counter, zeroed
+    cudaError_t (*persistent)(const Geom &, const double *c, void *state, void *up, void *br,
+                              int *sched, int H, u64 g0, int *err, int threads, cudaStream_t);
 };
 
 constexpr int kBlock = 256;
@@ -155,10 +159,31 @@ struct Launch {
         return tn.stage ? down_t<true>(G, c, br, state, o, g0, err, tn.threads, st)
                         : down_t<false>(G, c, br, state, o, g0, err, tn.threads, st);
     }
+    static cudaError_t persistent(const Geom &G, const double *c, void *state, void *upp,
+                                  void *br, int *sched, int H, u64 g0, int *err, int threads,
+                                  cudaStream_t st) {
+        const size_t sm = down_smem<Op>(G.n, true);
+        cudaError_t e = allow_smem(persistent_kernel<Op>, sm);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0, dev = 0, nsm = 0;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel<Op>,
+                                                               threads, sm)) != cudaSuccess)
+            return e;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        const long long nitems = (long long)G.T * G.Q * (2 * H + 1);
+        long long grid = (long long)(per_sm > 0 ? per_sm : 1) * nsm;
+        if (grid > nitems) grid = nitems;
+        const int NT = G.T * G.Q;
+        persistent_kernel<Op><<<(int)grid, threads, sm, st>>>(Op(c), G, (S *)state, (S *)upp,
+                                                              (S *)br, sched, sched + NT, H, g0,
+                                                              err);
+        return cudaGetLastError();
+    }
     static const OpTable *table() {
         static const OpTable t = {Op::NV,      Op::NST,     (int)sizeof(S), &swept_smem_bytes<Op>,
                                   &naive,      &up,         &bridge,        &octahedron,
-                                  &down,       Op::STAGE,   &swept_smem_for<Op>};
+                                  &down,       Op::STAGE,   &swept_smem_for<Op>, &persistent};
         return &t;
     }
 };

@@ -37,7 +37,7 @@ OP_SHAPE = {
     "heat_kahan": (2, 1, "f32"),
     "wave": (2, 1, "f64"),
 }
-MODES = {"swept": 0, "naive": 1}
+MODES = {"swept": 0, "naive": 1, "persistent": 0x200}
 GRAPH = 0x100
 Q = {"dt": 0, "wavespeed": 1, "substeps": 2, "launches": 3, "state_bytes": 4,
      "panel_bytes": 5, "smem_bytes": 6, "cells": 7}

@@ -225,6 +225,48 @@ def test_wave_swept_equals_naive_and_oracle(oracle_lib, nx, ny, tile, nsteps):
     assert np.array_equal(swept[0], ref_u) and np.array_equal(swept[1], ref_uo)
 
 
+# ---------------------------------------------------------- persistent form
+
+@pytest.mark.parametrize("op,dtype,nx,ny,tile,nsteps", [
+    ("hash", "u64", 64, 48, 16, 61),      # all 9 neighbours: any missed dependency shows
+    ("hash", "u64", 32, 16, 8, 40),       # fewer than 3 tiles across: neighbourhoods wrap
+    ("hash", "u64", 16, 16, 16, 33),      # a single tile borders itself
+    ("heat", "f64", 128, 96, 32, 77),
+    ("heat", "f64", 128, 128, 64, 100),
+    ("heat_kahan", "f32", 96, 64, 16, 45),
+    ("heat_kahan", "bf16", 64, 64, 32, 50),
+    ("wide2", "u64", 48, 32, 8, 19),      # nstages = 2
+    ("wave", "f64", 64, 64, 16, 70),
+    ("euler_rk2", "f64", 32, 32, 16, 9),
+])
+def test_persistent_form_gives_the_same_bits(oracle_lib, op, dtype, nx, ny, tile, nsteps):
+    """One persistent launch per advance (work items with neighbourhood waits)
+    equals the naive path bit for bit, also through a captured graph."""
+    rng = np.random.default_rng(nx + ny + tile)
+    nv = {"hash": 1, "heat": 1, "heat_kahan": 2, "wide2": 5, "wave": 2, "euler_rk2": 8}[op]
+    params = {"hash": (), "wide2": (), "heat": (0.2,), "heat_kahan": (0.2,), "wave": (0.3,),
+              "euler_rk2": (GAMMA, CFL, KAPPA)}[op]
+    if dtype == "u64":
+        u0 = rng.integers(0, 2**64, size=(nv, ny, nx), dtype=np.uint64)
+    elif dtype == "f32":
+        u0 = np.stack([rng.random((ny, nx)), np.zeros((ny, nx))]).astype(np.float32)
+    elif dtype == "bf16":
+        u0 = np.stack([_to_bf16_bits(rng.random((ny, nx))), np.zeros((ny, nx), np.uint16)])
+    elif op == "euler_rk2":
+        u0 = _euler_u0(nx, ny, seed=4)[0]
+    else:
+        u0 = rng.random((nv, ny, nx))
+    naive = run(op, u0, nsteps, tile, "naive", params, dtype=dtype)
+    stream = torch.cuda.Stream()
+    with Swept2D(nx, ny, op=op, tile=tile, params=params, dtype=dtype, stream=stream) as s:
+        s.set_state(np.ascontiguousarray(u0))
+        s.advance(nsteps, mode="persistent")
+        assert np.array_equal(s.get_state(), naive)
+        s.set_state(np.ascontiguousarray(u0))
+        s.advance(nsteps, mode="persistent", graph=True)
+        assert np.array_equal(s.get_state(), naive)
+
+
 # ------------------------------------------------------------- CUDA graphs
 
 @pytest.mark.parametrize("op,mode,nsteps", [
