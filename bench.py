@@ -14,7 +14,7 @@ Other workloads: heat64 (64 x 64 FP64, 512 steps, tile 16, U[0,1) field);
 heat2048_f32 / heat2048_bf16 (2048 x 2048, binary32 arithmetic with Kahan-
 compensated time update, binary32 / bfloat16 storage, 100,000 steps, error
 against the FP64 solution reported); euler2048 (2048 x 2048 compressible Euler,
-midpoint RK2, 5,000 steps, tile 16); wave1024 (the paper's Section 6 wave
+midpoint RK2, 5,000 steps, tile 32); wave1024 (the paper's Section 6 wave
 equation, leapfrog, Courant number 0.3, source at the centre, 1024 x 1024);
 batch1024 (1,024 independent grids of uneven sizes, binary32 storage, one
 graph-captured swept launch sequence for all of them, tile autotuned per size
@@ -77,13 +77,13 @@ WORKLOADS = {
                          "heat 4096x4096 FP64 r=0.2, 10000 steps, 32-mode smooth field", 4),
     "heat64": Workload("heat", "f64", 64, 512, 16, (0.2,), "uniform", 0,
                        "heat 64x64 FP64 r=0.2, 512 steps, U[0,1) field (seed 0)", 4),
-    "heat2048_f32": Workload("heat_kahan", "f32", 2048, 100_000, 32, (0.2,), "smooth", 1,
+    "heat2048_f32": Workload("heat_kahan", "f32", 2048, 100_000, 64, (0.2,), "smooth", 1,
                              "heat 2048x2048, binary32 storage and arithmetic, Kahan-"
                              "compensated update, r=0.2, 100000 steps"),
-    "heat2048_bf16": Workload("heat_kahan", "bf16", 2048, 100_000, 32, (0.2,), "smooth", 1,
+    "heat2048_bf16": Workload("heat_kahan", "bf16", 2048, 100_000, 64, (0.2,), "smooth", 1,
                               "heat 2048x2048, bfloat16 storage, binary32 arithmetic, Kahan-"
                               "compensated update, r=0.2, 100000 steps"),
-    "euler2048": Workload("euler_rk2", "f64", 2048, 5_000, 16, (GAMMA, CFL, KAPPA), "euler", 2,
+    "euler2048": Workload("euler_rk2", "f64", 2048, 5_000, 32, (GAMMA, CFL, KAPPA), "euler", 2,
                           "Euler 2048x2048 FP64, midpoint RK2, CFL 0.3, 5000 steps", 64),
     "batch1024": Workload("heat_kahan", "f32", 0, 20_000, 0, (0.2,), "batch", 3,
                           "1024 independent periodic grids, nx and ny uniform in {32,48,...,512} "

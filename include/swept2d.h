@@ -149,6 +149,21 @@ int swept2d_advance(swept2d_t *h, long long nsteps, int mode);
  * unspecified). */
 int swept2d_get_state(swept2d_t *h, void *dst, int dst_is_device);
 
+/*
+ * Self-test of the persistent form's bounded waits (no counterpart in the
+ * paper; Section 4's exchanges are the dependencies being waited for): runs the
+ * persistent kernel for one half cycle with its first phase skipped, so the
+ * phase counters those waits read are never released. Every block's wait gives
+ * up after spin_limit polls (>= 1; each poll is a load plus a ~64 ns pause, so
+ * a few thousand take milliseconds), records the timeout in the handle's error
+ * word and returns. No work item runs, so the state is unchanged; the error
+ * word is cleared again before the call returns.
+ * Returns SWEPT2D_ETIMEOUT when the kernel reported the timed-out wait (the
+ * expected outcome), SWEPT2D_ESTATE if it did not, EINVAL (no tile, bad
+ * spin_limit, staged panels too large), ECUDA.
+ */
+int swept2d_selftest_wait_timeout(swept2d_t *h, long long spin_limit);
+
 /* Free all device memory of the handle and the handle itself (NULL is a no-op).
  * Synchronises the handle's stream first. */
 int swept2d_destroy(swept2d_t *h);

@@ -209,7 +209,8 @@ int swept_substeps(swept2d *h, long long total, bool persistent) {
         if (e != cudaSuccess) return cuda_fail(h, e, "persistent schedule reset");
         int rc = launch(h, SWEPT2D_K_OCTAHEDRON, "persistent kernel", [&] {
             return h->ops->persistent(h->G, h->consts, h->state, h->up, h->br, h->sched, (int)H,
-                                      g_start, h->errword, h->tune.threads, h->stream);
+                                      g_start, h->errword, h->tune.threads, 0,
+                                      swept::kPersistSpinLimit, h->stream);
         });
         if (rc) return rc;
         h->substeps += H * half;
@@ -452,6 +453,53 @@ int swept2d_set_state(swept2d_t *h, const void *src, int src_is_device) {
     return SWEPT2D_OK;
 }
 
+// Checks and scratch of the persistent form for H half cycles: the staged
+// shared-memory plan must fit, the work items must fit an int, and the phase
+// counters (T*Q + 1 ints) are allocated on first use.
+static int persistent_prepare(swept2d *h, long long H) {
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        optin = 227 * 1024;
+    if (h->ops->smem_for(h->n, true) > (size_t)optin)
+        return fail(h, SWEPT2D_EINVAL, "advance: persistent form needs staged panels, which do not fit");
+    if ((long long)h->G.T * h->G.Q * (2 * H + 1) >= (1LL << 31))
+        return fail(h, SWEPT2D_EINVAL, "advance: too many work items for one persistent launch");
+    if (!h->sched) {
+        cudaError_t e = cudaMalloc(&h->sched, ((size_t)h->G.T * h->G.Q + 1) * sizeof(int));
+        if (e != cudaSuccess) return cuda_fail(h, e, "persistent schedule allocation");
+    }
+    return SWEPT2D_OK;
+}
+
+int swept2d_selftest_wait_timeout(swept2d_t *h, long long spin_limit) {
+    if (!h) return SWEPT2D_EINVAL;
+    if (h->n == 0) return fail(h, SWEPT2D_EINVAL, "selftest: needs a handle created with a tile");
+    if (spin_limit < 1) return fail(h, SWEPT2D_EINVAL, "selftest: spin_limit < 1");
+    int rc = persistent_prepare(h, 1);
+    if (rc) return rc;
+    const int NT = h->G.T * h->G.Q;
+    cudaError_t e = cudaMemsetAsync(h->sched, 0, ((size_t)NT + 1) * sizeof(int), h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "selftest schedule reset");
+    // one half cycle with the NT first-phase items skipped: every item taken
+    // waits for a phase-1 counter that nothing releases
+    rc = launch(h, SWEPT2D_K_OCTAHEDRON, "persistent kernel (wait-timeout self-test)", [&] {
+        return h->ops->persistent(h->G, h->consts, h->state, h->up, h->br, h->sched, 1,
+                                  (u64)h->substeps, h->errword, h->tune.threads, NT, spin_limit,
+                                  h->stream);
+    });
+    if (rc) return rc;
+    if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return cuda_fail(h, e, "selftest sync");
+    int flag = 0;
+    if ((e = cudaMemcpy(&flag, h->errword, sizeof flag, cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(h, e, "selftest error word");
+    if ((e = cudaMemset(h->errword, 0, sizeof(int))) != cudaSuccess)
+        return cuda_fail(h, e, "selftest error word reset");
+    if (flag == 2)
+        return fail(h, SWEPT2D_ETIMEOUT, "selftest: the persistent kernel's neighbourhood wait gave up, as intended");
+    return fail(h, SWEPT2D_ESTATE, "selftest: the persistent kernel did not report a timed-out wait");
+}
+
 int swept2d_advance(swept2d_t *h, long long nsteps, int mode) {
     if (!h) return SWEPT2D_EINVAL;
     if (nsteps < 0) return fail(h, SWEPT2D_EINVAL, "advance: nsteps < 0");
@@ -464,20 +512,8 @@ int swept2d_advance(swept2d_t *h, long long nsteps, int mode) {
         return fail(h, SWEPT2D_EINVAL, "advance: swept mode needs a tile (created with tile 0)");
     if (persistent) {
         if (mode != SWEPT2D_SWEPT) return fail(h, SWEPT2D_EINVAL, "advance: persistent needs the swept mode");
-        int dev = 0, optin = 0;
-        cudaGetDevice(&dev);
-        if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
-            optin = 227 * 1024;
-        if (h->ops->smem_for(h->n, true) > (size_t)optin)
-            return fail(h, SWEPT2D_EINVAL, "advance: persistent form needs staged panels, which do not fit");
-        const long long nitems =
-            (long long)h->G.T * h->G.Q * (2 * (nsteps * h->nst / (h->n / 2)) + 1);
-        if (nitems >= (1LL << 31))
-            return fail(h, SWEPT2D_EINVAL, "advance: too many work items for one persistent launch");
-        if (!h->sched) {
-            cudaError_t e = cudaMalloc(&h->sched, ((size_t)h->G.T * h->G.Q + 1) * sizeof(int));
-            if (e != cudaSuccess) return cuda_fail(h, e, "persistent schedule allocation");
-        }
+        const int rc = persistent_prepare(h, nsteps * h->nst / (h->n / 2));
+        if (rc) return rc;
         mode |= persistent;
     }
     if (graph) {
@@ -499,6 +535,8 @@ int swept2d_get_state(swept2d_t *h, void *dst, int dst_is_device) {
     int flag = 0;
     if ((e = cudaMemcpy(&flag, h->errword, sizeof flag, cudaMemcpyDeviceToHost)) != cudaSuccess)
         return cuda_fail(h, e, "get_state error word");
+    if (flag == 2)
+        return fail(h, SWEPT2D_ETIMEOUT, "the persistent kernel's bounded wait for its tile neighbourhood gave up; the state is unspecified");
     if (flag) return fail(h, SWEPT2D_ETIMEOUT, "a kernel's bounded wait for its panel copies gave up; the state is unspecified");
     return SWEPT2D_OK;
 }

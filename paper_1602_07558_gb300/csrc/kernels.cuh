@@ -770,8 +770,9 @@ __global__ void __launch_bounds__(256) down_kernel(Op op, Geom G, const typename
 // are read by another through TMA bulk copies (L2) after an acquire and a
 // generic-to-async proxy fence, so no stale L1 line is ever read. Waits are
 // bounded: on timeout the error word is set and the block stops.
-// a dependency is at most one work item away (about a millisecond): the
-// bound (about a second of 64 ns naps) only catches a block that never finishes
+// A dependency is at most one work item away (tens of microseconds); the
+// default bound (about a second of 64 ns naps and polls) only catches a block
+// that never finishes.
 constexpr long long kPersistSpinLimit = 1LL << 24;
 
 __device__ __forceinline__ int ld_acquire(const int *p) {
@@ -779,21 +780,30 @@ __device__ __forceinline__ int ld_acquire(const int *p) {
     asm volatile("ld.acquire.gpu.global.s32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
+__device__ __forceinline__ int ld_relaxed(const int *p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
 __device__ __forceinline__ void st_release(int *p, int v) {
     asm volatile("st.release.gpu.global.s32 [%0], %1;\n" ::"l"(p), "r"(v) : "memory");
 }
 
+// `first` is the first work item taken (0; a positive value skips items, which
+// only the wait-timeout self-test does: the skipped items' phases are never
+// released, so every wait runs out).
 template <class Op>
 __global__ void __launch_bounds__(256) persistent_kernel(Op op, Geom G, typename Op::S *state,
                                                          typename Op::S *upp, typename Op::S *br,
                                                          int *stage, int *queue, int H, u64 g0,
-                                                         int *err) {
+                                                         int *err, int first, long long spin_limit) {
     __shared__ int s_item, s_fail;
     const int NT = G.T * G.Q, h = G.n / 2;
     const int nitems = NT * (2 * H + 1);
     for (;;) {
         if (threadIdx.x == 0) {
-            s_item = atomicAdd(queue, 1);
+            const int it = atomicAdd(queue, 1) + first;
+            s_item = ld_relaxed(err) ? nitems : it;   // another block's failure ends this one
             s_fail = 0;
         }
         __syncthreads();
@@ -801,30 +811,35 @@ __global__ void __launch_bounds__(256) persistent_kernel(Op op, Geom G, typename
         if (item >= nitems) return;
         const int p = item / NT + 1, t = item - (p - 1) * NT;
         const int J = t / G.T, I = t - J * G.T;
-        if (p > 1 && threadIdx.x == 0) {
-            for (int dj = -1; dj <= 1 && !s_fail; ++dj) {
+        if (p > 1 && threadIdx.x < 32) {
+            // lanes 0..8 wait for one tile each of the periodic 3 x 3 neighbourhood
+            bool bad = false;
+            if (threadIdx.x < 9) {
+                const int dj = (int)threadIdx.x / 3 - 1, di = (int)threadIdx.x % 3 - 1;
                 const int jj = J + dj < 0 ? G.Q - 1 : (J + dj == G.Q ? 0 : J + dj);
-                for (int di = -1; di <= 1 && !s_fail; ++di) {
-                    const int ii = I + di < 0 ? G.T - 1 : (I + di == G.T ? 0 : I + di);
-                    const int *flag = stage + jj * G.T + ii;
-                    long long it = 0;
-                    while (ld_acquire(flag) < p - 1) {
-                        // give up after the bound, or at once when another
-                        // block has already recorded a failure
-                        const bool other = err && (++it & 255) == 0 && ld_acquire(err) != 0;
-                        if (other || it > kPersistSpinLimit) {
-                            if (err) atomicExch(err, 2);
-                            s_fail = 1;
-                            break;
-                        }
-                        __nanosleep(64);
+                const int ii = I + di < 0 ? G.T - 1 : (I + di == G.T ? 0 : I + di);
+                const int *flag = stage + jj * G.T + ii;
+                long long it = 0;
+                while (ld_acquire(flag) < p - 1) {
+                    // give up after the bound, or at once when another block
+                    // has already recorded a failure
+                    if (++it > spin_limit || ((it & 255) == 0 && ld_relaxed(err) != 0)) {
+                        bad = true;
+                        break;
                     }
+                    __nanosleep(64);
                 }
             }
-            asm volatile("fence.proxy.async.global;\n" ::: "memory");
+            bad = __any_sync(0xffffffffu, bad);
+            if (threadIdx.x == 0 && bad) {
+                atomicExch(err, 2);
+                s_fail = 1;
+            }
         }
         __syncthreads();
         if (s_fail) return;
+        // the acquired panels are read next by bulk copies (the async proxy)
+        if (threadIdx.x == 0) asm volatile("fence.proxy.async.global;\n" ::: "memory");
         if (p == 1) {
             up_tile(op, G, state, upp, 0, g0, I, J);
         } else {
@@ -848,14 +863,7 @@ __global__ void __launch_bounds__(256) persistent_kernel(Op op, Geom G, typename
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         __threadfence();
         __syncthreads();
-        if (threadIdx.x == 0) {
-            st_release(stage + t, p);
-            // a failed bulk wait in this item ends the block (its waiters see
-            // the error word and stop too)
-            s_fail = err ? ld_acquire(err) : 0;
-        }
-        __syncthreads();
-        if (s_fail) return;
+        if (threadIdx.x == 0) st_release(stage + t, p);
     }
 }
 

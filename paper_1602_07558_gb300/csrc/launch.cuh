@@ -37,7 +37,8 @@ struct OpTable {
     // the whole swept part of an advance (H half cycles) as one persistent
     // launch; sched: T*Q phase counters followed by the queue counter, zeroed
     cudaError_t (*persistent)(const Geom &, const double *c, void *state, void *up, void *br,
-                              int *sched, int H, u64 g0, int *err, int threads, cudaStream_t);
+                              int *sched, int H, u64 g0, int *err, int threads, int first,
+                              long long spin_limit, cudaStream_t);
 };
 
 constexpr int kBlock = 256;
@@ -161,7 +162,7 @@ struct Launch {
     }
     static cudaError_t persistent(const Geom &G, const double *c, void *state, void *upp,
                                   void *br, int *sched, int H, u64 g0, int *err, int threads,
-                                  cudaStream_t st) {
+                                  int first, long long spin_limit, cudaStream_t st) {
         const size_t sm = down_smem<Op>(G.n, true);
         cudaError_t e = allow_smem(persistent_kernel<Op>, sm);
         if (e != cudaSuccess) return e;
@@ -177,7 +178,7 @@ struct Launch {
         const int NT = G.T * G.Q;
         persistent_kernel<Op><<<(int)grid, threads, sm, st>>>(Op(c), G, (S *)state, (S *)upp,
                                                               (S *)br, sched, sched + NT, H, g0,
-                                                              err);
+                                                              err, first, spin_limit);
         return cudaGetLastError();
     }
     static const OpTable *table() {

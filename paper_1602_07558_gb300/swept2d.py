@@ -75,10 +75,11 @@ def lib():
         L.swept2d_set_tuning.argtypes = [vp, i, i]
         L.swept2d_kernel_stats.argtypes = [vp, i, ctypes.POINTER(ll), ctypes.POINTER(d)]
         L.swept2d_measure_fp64_rate.argtypes = [vp, ctypes.POINTER(d)]
+        L.swept2d_selftest_wait_timeout.argtypes = [vp, ll]
         for name in ("swept2d_create", "swept2d_set_state", "swept2d_advance",
                      "swept2d_get_state", "swept2d_destroy", "swept2d_query",
                      "swept2d_set_timing", "swept2d_kernel_stats", "swept2d_measure_fp64_rate",
-                     "swept2d_set_tuning"):
+                     "swept2d_set_tuning", "swept2d_selftest_wait_timeout"):
             getattr(L, name).restype = i
         _lib = L
         return L
@@ -191,6 +192,11 @@ class Swept2D:
         self._check(lib().swept2d_kernel_stats(self._h, KERNELS[kind], ctypes.byref(n),
                                                ctypes.byref(ms)))
         return n.value, ms.value
+
+    def selftest_wait_timeout(self, spin_limit=4096):
+        """Run the persistent kernel with waits that can never be satisfied;
+        returns the status code (ETIMEOUT when the bounded wait gave up)."""
+        return lib().swept2d_selftest_wait_timeout(self._h, int(spin_limit))
 
     def close(self):
         if self._h:

@@ -267,6 +267,21 @@ def test_persistent_form_gives_the_same_bits(oracle_lib, op, dtype, nx, ny, tile
         assert np.array_equal(s.get_state(), naive)
 
 
+def test_persistent_wait_timeout_is_reported_and_the_context_stays_usable(oracle_lib):
+    """A neighbourhood wait that can never be satisfied gives up after its
+    bound, the host reads ETIMEOUT, and the same handle then advances
+    correctly."""
+    from paper_1602_07558_gb300.swept2d import ETIMEOUT
+    u0 = inputs.uniform(64, 64, seed=8)
+    ref = oracle_lib.heat(u0, 0.2, 40)
+    with Swept2D(64, 64, op="heat", tile=16, params=(0.2,)) as s:
+        s.set_state(u0.reshape(s.shape))
+        assert s.selftest_wait_timeout(4096) == ETIMEOUT
+        assert np.array_equal(s.get_state().reshape(64, 64), u0)    # no work item ran
+        s.advance(40, mode="persistent")
+        assert np.array_equal(s.get_state().reshape(64, 64), ref)
+
+
 # ------------------------------------------------------------- CUDA graphs
 
 @pytest.mark.parametrize("op,mode,nsteps", [
