@@ -71,6 +71,7 @@ def _load():
         lib.oracle_heat_kahan_f32.argtypes = [i, i, d, ll, p, p]
         lib.oracle_wave.argtypes = [i, i, d, ll, p, p]
         lib.oracle_heat_kahan_bf16.argtypes = [i, i, d, ll, p, p]
+        lib.oracle_euler_kahan.argtypes = [i, i, i, d, d, d, d, d, d, ll, p]
         lib.oracle_f32_to_bf16.argtypes = [ctypes.c_float]
         lib.oracle_f32_to_bf16.restype = ctypes.c_uint16
         lib.oracle_bf16_to_f32.argtypes = [ctypes.c_uint16]
@@ -191,6 +192,38 @@ def heat_kahan(u0, c0, r: float, nsteps: int, storage: str = "f32"):
     fn = _load().oracle_heat_kahan_f32 if storage == "f32" else _load().oracle_heat_kahan_bf16
     _check(fn(nx, ny, float(r), int(nsteps), u.ctypes.data, c.ctypes.data), "heat_kahan")
     return u, c
+
+
+def bf16_bits_to_f32(bits) -> np.ndarray:
+    """bfloat16 bits (uint16) -> float32 values (exact)."""
+    return (np.asarray(bits, dtype=np.uint16).astype(np.uint32) << 16).view(np.float32)
+
+
+def f32_to_bf16_bits(x) -> np.ndarray:
+    """float32 values that bfloat16 represents exactly -> their bits."""
+    w = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32)
+    if np.any(w & 0xFFFF):
+        raise ValueError("value not representable in bfloat16")
+    return (w >> 16).astype(np.uint16)
+
+
+def euler_kahan(S0, gamma: float, dt: float, kappa: float, a: float, nsteps: int,
+                storage: str = "f32", lx: float = 1.0, ly: float = 1.0) -> np.ndarray:
+    """``nsteps`` compensated binary32 midpoint-RK2 steps of the Euler system on
+    the 12-plane state (U, U*, C), shape (12, ny, nx): float32 values for
+    ``storage`` "f32", uint16 bfloat16 bits for "bf16". Returns the same type."""
+    if storage not in ("f32", "bf16"):
+        raise ValueError("storage is 'f32' or 'bf16'")
+    S0 = np.asarray(S0)
+    if S0.ndim != 3 or S0.shape[0] != 12:
+        raise ValueError("expected a (12, ny, nx) array")
+    S = np.ascontiguousarray(bf16_bits_to_f32(S0) if storage == "bf16"
+                             else np.array(S0, dtype=np.float32, copy=True))
+    _, ny, nx = S.shape
+    _check(_load().oracle_euler_kahan(nx, ny, 1 if storage == "bf16" else 0, float(gamma),
+                                      float(dt), float(lx), float(ly), float(kappa), float(a),
+                                      int(nsteps), S.ctypes.data), "euler_kahan")
+    return f32_to_bf16_bits(S) if storage == "bf16" else S
 
 
 def wave(u0, uold0, C2: float, nsteps: int):

@@ -41,6 +41,8 @@
  *   heat_kahan the heat update in binary32 arithmetic with the time update
  *             accumulated by Kahan's compensated summation, state (u, c) stored
  *             in binary32 or in bfloat16 (reduced-precision storage forms)
+ *   euler_kahan the Euler system in binary32 arithmetic, state (U, U*, C)
+ *             stored in binary32 or bfloat16, compensated time accumulation
  */
 #include <math.h>
 #include <stdint.h>
@@ -419,6 +421,112 @@ int oracle_heat_kahan_bf16(int nx, int ny, double r64, long long nsteps, uint16_
     }
     if (ua != u) { memcpy(u, ua, npts * sizeof(uint16_t)); memcpy(c, ca, npts * sizeof(uint16_t)); }
     free(u2); free(c2);
+    return 0;
+}
+
+/* ----------------------------------------------------------------- euler_kahan
+ * The Euler system above in binary32 arithmetic with reduced-precision storage,
+ * each step's time accumulation compensated as in heat_kahan (the precision
+ * forms of the scheme; the paper fixes no precision). Point state: 12 planes,
+ * U (0-3), U* (4-7) and the compensation C (8-11), each value stored as a
+ * binary32 or (bf16 != 0) as a value representable in bfloat16; store() rounds
+ * a binary32 to the storage format (identity, or round to nearest even).
+ * Constants: the FP64 constants of euler (cx, cy, kax, kay, gamma-1, dt/2, dt)
+ * rounded once to binary32. L is the FP64 formula in binary32 arithmetic with
+ * the same fused operations. One step:
+ *   stage 0: U* = store(U + (dt/2) L(U))              (one fused multiply-add)
+ *   stage 1: y = dt L(U*) - C;  t = U + y;  U' = store(t);  C' = store((U' - U) - y)
+ * U and C pass through stage 0 unchanged, U* through stage 1; the stencil reads
+ * the stored values. */
+typedef struct { float cx, cy, kax, kay, gm1; } euler_consts_f;
+
+static float store_f(float x, int bf16) {
+    return bf16 ? oracle_bf16_to_f32(oracle_f32_to_bf16(x)) : x;
+}
+
+static void euler_flux_f(const float *W, size_t p, size_t np, float gm1, float *F, float *G) {
+    float r = W[p], m = W[np + p], q = W[2 * np + p], E = W[3 * np + p];
+    float iv = 1.0f / r;
+    float u = m * iv, v = q * iv;
+    float ke = 0.5f * fmaf(m, u, q * v);
+    float pr = gm1 * (E - ke);
+    float Ep = E + pr;
+    F[0] = m; F[1] = fmaf(m, u, pr); F[2] = q * u; F[3] = Ep * u;
+    G[0] = q; G[1] = m * v; G[2] = fmaf(q, v, pr); G[3] = Ep * v;
+}
+
+/* L(W) at point (i, j) of the 4-plane field W. */
+static void euler_L_f(const float *W, int nx, int ny, int i, int j, const euler_consts_f *k,
+                      float *L) {
+    size_t np = (size_t)nx * ny;
+    int jn = wrapi(j - 1, ny), js = wrapi(j + 1, ny);
+    int iw = wrapi(i - 1, nx), ie = wrapi(i + 1, nx);
+    size_t pc = (size_t)j * nx + i, pw = (size_t)j * nx + iw, pe = (size_t)j * nx + ie;
+    size_t pn = (size_t)jn * nx + i, ps = (size_t)js * nx + i;
+    float FW[4], GW[4], FE[4], GE[4], FN[4], GN[4], FS[4], GS[4];
+    euler_flux_f(W, pw, np, k->gm1, FW, GW);
+    euler_flux_f(W, pe, np, k->gm1, FE, GE);
+    euler_flux_f(W, pn, np, k->gm1, FN, GN);
+    euler_flux_f(W, ps, np, k->gm1, FS, GS);
+    for (int c = 0; c < 4; ++c) {
+        float wc = W[c * np + pc];
+        float lx = (W[c * np + pe] + W[c * np + pw]) - 2.0f * wc;
+        float ly = (W[c * np + ps] + W[c * np + pn]) - 2.0f * wc;
+        float diss = fmaf(k->kax, lx, k->kay * ly);
+        float flux = fmaf(k->cx, FE[c] - FW[c], k->cy * (GS[c] - GN[c]));
+        L[c] = diss - flux;
+    }
+}
+
+/* nsteps of the compensated binary32 midpoint RK2 on the 12-plane state S. */
+int oracle_euler_kahan(int nx, int ny, int bf16, double gamma, double dt, double lx, double ly,
+                       double kappa, double a, long long nsteps, float *S) {
+    if (nx < 1 || ny < 1 || nsteps < 0 || !S) return -1;
+    size_t np = (size_t)nx * ny;
+    double dx = lx / nx, dy = ly / ny;
+    euler_consts_f k;
+    k.cx = (float)(0.5 / dx); k.cy = (float)(0.5 / dy);
+    k.kax = (float)((kappa * a) / dx); k.kay = (float)((kappa * a) / dy);
+    k.gm1 = (float)(gamma - 1.0);
+    float tau0 = (float)(0.5 * dt), tau1 = (float)dt;
+    float *T = (float *)malloc(12 * np * sizeof(float));
+    if (!T) return -3;
+    float *A = S, *B = T;
+    for (long long s = 0; s < nsteps; ++s) {
+        /* stage 0: U* = store(U + (dt/2) L(U)) */
+#pragma omp parallel for schedule(static)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                size_t pc = (size_t)j * nx + i;
+                float L[4];
+                euler_L_f(A, nx, ny, i, j, &k, L);
+                for (int c = 0; c < 4; ++c) {
+                    B[c * np + pc] = A[c * np + pc];
+                    B[(4 + c) * np + pc] = store_f(fmaf(tau0, L[c], A[c * np + pc]), bf16);
+                    B[(8 + c) * np + pc] = A[(8 + c) * np + pc];
+                }
+            }
+        { float *t = A; A = B; B = t; }
+        /* stage 1: compensated U += dt L(U*) */
+#pragma omp parallel for schedule(static)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                size_t pc = (size_t)j * nx + i;
+                float L[4];
+                euler_L_f(A + 4 * np, nx, ny, i, j, &k, L);
+                for (int c = 0; c < 4; ++c) {
+                    float u = A[c * np + pc], cc = A[(8 + c) * np + pc];
+                    float y = tau1 * L[c] - cc;
+                    float un = store_f(u + y, bf16);
+                    B[c * np + pc] = un;
+                    B[(4 + c) * np + pc] = A[(4 + c) * np + pc];
+                    B[(8 + c) * np + pc] = store_f((un - u) - y, bf16);
+                }
+            }
+        { float *t = A; A = B; B = t; }
+    }
+    if (A != S) memcpy(S, A, 12 * np * sizeof(float));
+    free(A == S ? B : A);
     return 0;
 }
 

@@ -376,6 +376,95 @@ def test_heat_kahan_bf16_storage_keeps_small_increments(oracle_lib):
     assert err_plain > 10 * err_kahan
 
 
+# --------------------------------------------------- Euler, precision forms
+
+EPS32 = float(np.finfo(np.float32).eps)
+
+
+def _ek_state(U, storage, oracle_lib):
+    """(U, U*, C) with U* = U and C = 0, U rounded to the storage format;
+    returns (state, U as float64)."""
+    U32 = np.asarray(U, dtype=np.float32)
+    if storage == "bf16":
+        bits = np.vectorize(lambda v: oracle_lib.f32_to_bf16(float(v)), otypes=[np.uint16])(U32)
+        U32 = oracle_lib.bf16_bits_to_f32(bits)
+    S = np.concatenate([U32, U32, np.zeros_like(U32)])
+    if storage == "bf16":
+        S = oracle_lib.f32_to_bf16_bits(S)
+    return S, U32.astype(np.float64)
+
+
+def _ek_values(S, storage, oracle_lib):
+    return (oracle_lib.bf16_bits_to_f32(S) if storage == "bf16" else S).astype(np.float64)
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_euler_kahan_free_stream_and_gas_at_rest_are_exact(oracle_lib, storage):
+    """A uniform moving state is a fixed point bit for bit (every difference
+    is 0, so the increments and the compensation stay 0); a gas at rest with
+    uniform pressure keeps m = q = 0 and E exactly, whatever the storage."""
+    ny, nx = 8, 12
+    one = np.ones((ny, nx))
+    U0 = _euler_state(1.25 * one, 0.375 * one, -0.125 * one, 0.875 * one)
+    S, Uf = _ek_state(U0, storage, oracle_lib)
+    a, dt = oracle_lib.euler_setup(Uf, GAMMA, CFL)
+    assert np.array_equal(oracle_lib.euler_kahan(S, GAMMA, dt, KAPPA, a, 20, storage), S)
+    x = np.arange(32)
+    rho = np.tile(1.0 + 0.1 * np.cos(2 * np.pi * 2 * x / 32), (6, 1))
+    S, Uf = _ek_state(_euler_state(rho, 0 * rho, 0 * rho, np.ones_like(rho)), storage, oracle_lib)
+    a, dt = oracle_lib.euler_setup(Uf, GAMMA, CFL)
+    V = _ek_values(oracle_lib.euler_kahan(S, GAMMA, dt, KAPPA, a, 40, storage), storage, oracle_lib)
+    assert np.all(V[1] == 0) and np.all(V[2] == 0) and np.all(V[5] == 0) and np.all(V[6] == 0)
+    assert np.array_equal(V[3], Uf[3]) and np.all(V[11] == 0)
+    assert np.max(np.abs(V[0] - 1.0)) < 0.1          # rho diffuses towards its mean
+
+
+@pytest.mark.parametrize("T", [100, 1000])
+def test_euler_kahan_f32_tracks_the_fp64_scheme(oracle_lib, T):
+    """From the same (binary32) initial pressure pulse, the binary32 form stays
+    within a few binary32 roundings (8 eps32 of max |U|) of the FP64 oracle,
+    far below each variable's own change over the first 100 steps: a dropped
+    term, a wrong sign or a swapped flux would leave errors of that size."""
+    n = 32
+    S, Uf = _ek_state(inputs.euler_pulse(n, n, 2, gamma=GAMMA), "f32", oracle_lib)
+    a, dt = oracle_lib.euler_setup(Uf, GAMMA, CFL)
+    ref = oracle_lib.euler_rk2(Uf, GAMMA, dt, KAPPA, a, T)
+    V = _ek_values(oracle_lib.euler_kahan(S, GAMMA, dt, KAPPA, a, T, "f32"), "f32", oracle_lib)
+    err = np.max(np.abs(V[:4] - ref), axis=(1, 2))
+    change = np.max(np.abs(ref - Uf), axis=(1, 2))
+    assert np.all(err <= 8 * EPS32 * np.max(np.abs(ref)))
+    if T == 100:          # later the momentum of the pulse has decayed to ~1e-9
+        assert np.all(err <= 0.01 * change)
+
+
+def test_euler_kahan_bf16_compensation_keeps_the_small_increments(oracle_lib):
+    """bfloat16 storage (8-bit significand): the per-step increments of the
+    decaying pulse fall below half an ulp of U. With the compensation reset
+    before every step (the same oracle, one step at a time: plain rounding) the
+    field stagnates far from the FP64 solution; compensated it stays within
+    half a bfloat16 ulp of max |U| and 20x closer, and the compensated sums
+    sum(U - C) drift 10x less than the stored sums sum(U)."""
+    n, T = 32, 1000
+    S, Uf = _ek_state(inputs.euler_pulse(n, n, 2, gamma=GAMMA), "bf16", oracle_lib)
+    a, dt = oracle_lib.euler_setup(Uf, GAMMA, CFL)
+    ref = oracle_lib.euler_rk2(Uf, GAMMA, dt, KAPPA, a, T)
+    K = _ek_values(oracle_lib.euler_kahan(S, GAMMA, dt, KAPPA, a, T, "bf16"), "bf16", oracle_lib)
+    P = S.copy()
+    for _ in range(T):
+        P = oracle_lib.euler_kahan(P, GAMMA, dt, KAPPA, a, 1, "bf16")
+        P[8:] = 0
+    P = _ek_values(P, "bf16", oracle_lib)
+    err_k = np.max(np.abs(K[:4] - ref))
+    err_p = np.max(np.abs(P[:4] - ref))
+    half_ulp = 2.0 ** np.floor(np.log2(np.max(np.abs(ref)))) * 2.0 ** -8
+    assert err_k < half_ulp
+    assert err_p > 20 * err_k
+    s0 = Uf.sum(axis=(1, 2))
+    drift_comp = np.abs((K[:4] - K[8:]).sum(axis=(1, 2)) - s0)
+    drift_stored = np.abs(K[:4].sum(axis=(1, 2)) - s0)
+    assert drift_comp[0] * 10 < drift_stored[0] and drift_comp[3] * 10 < drift_stored[3]
+
+
 # ------------------------------------------------------------------------ wave
 
 @pytest.mark.parametrize("T", [50, 400])
