@@ -2,8 +2,8 @@
 path beside it), printing one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload heat4096|heat64|heat2048_f32|heat2048_bf16|euler2048|wave1024|
-                              batch1024]
+                  [--workload heat4096|heat64|heat2048_f32|heat2048_bf16|euler2048|
+                              euler2048_f32|euler2048_bf16|wave1024|batch1024]
 
 The default workload is the headline one: 2D heat, periodic 4096 x 4096 FP64,
 r = 0.2, 10,000 steps, smooth 32-mode initial field, tile 32. One bench step =
@@ -14,7 +14,9 @@ Other workloads: heat64 (64 x 64 FP64, 512 steps, tile 16, U[0,1) field);
 heat2048_f32 / heat2048_bf16 (2048 x 2048, binary32 arithmetic with Kahan-
 compensated time update, binary32 / bfloat16 storage, 100,000 steps, error
 against the FP64 solution reported); euler2048 (2048 x 2048 compressible Euler,
-midpoint RK2, 5,000 steps, tile 32); wave1024 (the paper's Section 6 wave
+midpoint RK2, 5,000 steps, tile 32); euler2048_f32 / euler2048_bf16 (the
+same in binary32 arithmetic with Kahan-compensated time update, binary32 /
+bfloat16 storage, error against the FP64 solution reported); wave1024 (the paper's Section 6 wave
 equation, leapfrog, Courant number 0.3, source at the centre, 1024 x 1024);
 batch1024 (1,024 independent grids of uneven sizes, binary32 storage, one
 graph-captured swept launch sequence for all of them, tile autotuned per size
@@ -85,6 +87,13 @@ WORKLOADS = {
                               "compensated update, r=0.2, 100000 steps"),
     "euler2048": Workload("euler_rk2", "f64", 2048, 5_000, 32, (GAMMA, CFL, KAPPA), "euler", 2,
                           "Euler 2048x2048 FP64, midpoint RK2, CFL 0.3, 5000 steps", 64),
+    "euler2048_f32": Workload("euler_kahan", "f32", 2048, 5_000, 32, (GAMMA, CFL, KAPPA),
+                              "euler", 2, "Euler 2048x2048, binary32 storage and arithmetic, "
+                              "Kahan-compensated update, midpoint RK2, CFL 0.3, 5000 steps"),
+    "euler2048_bf16": Workload("euler_kahan", "bf16", 2048, 5_000, 32, (GAMMA, CFL, KAPPA),
+                               "euler", 2, "Euler 2048x2048, bfloat16 storage, binary32 "
+                               "arithmetic, Kahan-compensated update, midpoint RK2, CFL 0.3, "
+                               "5000 steps"),
     "batch1024": Workload("heat_kahan", "f32", 0, 20_000, 0, (0.2,), "batch", 3,
                           "1024 independent periodic grids, nx and ny uniform in {32,48,...,512} "
                           "(seed 3), heat with binary32 storage and Kahan-compensated update, "
@@ -135,16 +144,26 @@ def initial_state(w: Workload, rank: int = 0) -> np.ndarray:
     if w.op == "euler_rk2":
         U = inputs.euler_pulse(N, N, seed, gamma=GAMMA)
         return np.concatenate([U, U])
+    if w.op == "euler_kahan":           # (U, U*, C) with C = 0
+        U = to_storage(inputs.euler_pulse(N, N, seed, gamma=GAMMA).astype(np.float32), w.dtype)
+        return np.concatenate([U, U, np.zeros_like(U)])
     if w.op == "wave":
         return inputs.wave_source(N, N)
     f = inputs.smooth_field(N, N, seed) if w.init == "smooth" else inputs.uniform(N, N, seed)
     if w.op == "heat":
         return f[None]
-    u32 = f.astype(np.float32)
-    if w.dtype == "bf16":
-        import torch
-        u32 = torch.from_numpy(u32).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
+    u32 = to_storage(f.astype(np.float32), w.dtype)
     return np.stack([u32, np.zeros_like(u32)])
+
+
+def to_storage(u32: np.ndarray, dtype: str) -> np.ndarray:
+    """binary32 values -> the storage type (bfloat16 bits by torch's round to
+    nearest even)."""
+    if dtype != "bf16":
+        return u32
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(u32)).to(torch.bfloat16).view(torch.int16) \
+        .numpy().view(np.uint16)
 
 
 def storage_to_f64(a: np.ndarray, dtype: str) -> np.ndarray:
@@ -227,6 +246,9 @@ def oracle_advance(w: Workload, state: np.ndarray, nsteps: int) -> np.ndarray:
     if w.op == "wave":
         u, uo = oracle.wave(state[0], state[1], w.params[0] * w.params[0], nsteps)
         return np.stack([u, uo])
+    if w.op == "euler_kahan":
+        a, dt = oracle.euler_setup(storage_to_f64(state[:4], w.dtype), GAMMA, CFL)
+        return oracle.euler_kahan(state, GAMMA, dt, KAPPA, a, nsteps, storage=w.dtype)
     raise ValueError(w.op)
 
 
@@ -378,13 +400,14 @@ def main():
     if args.threads is not None or args.stage is not None:
         sw.set_tuning(args.threads or 256,
                       bool(args.stage) if args.stage is not None else w.op == "heat_kahan")
+    two_stage = w.op in ("euler_rk2", "euler_kahan")
     nv = None if args.no_naive else mk(0)
 
     if args.profile_case:
         with torch.cuda.stream(stream):
             for s in filter(None, (sw, nv)):
                 s.set_state(state_dev)
-                s.advance(4 * w.tile // (2 if w.op == "euler_rk2" else 1),
+                s.advance(4 * w.tile // (2 if two_stage else 1),
                           mode="swept" if s is sw else "naive")
         torch.cuda.synchronize()
         print(json.dumps({"profile_case": True, "workload": w.describe, "grid": N,
@@ -518,7 +541,7 @@ def accuracy_report(w, sw, state_host, state_dev, out_sw, stream, Swept2D):
     import torch
     N = w.grid
     rep = {}
-    nchk = 53 if w.op != "euler_rk2" else 20
+    nchk = 20 if w.op in ("euler_rk2", "euler_kahan") else 53
     with torch.cuda.stream(stream):
         sw.set_state(state_dev)
         sw.advance(nchk)
@@ -543,6 +566,25 @@ def accuracy_report(w, sw, state_host, state_dev, out_sw, stream, Swept2D):
             "u_l2_rel": float(np.linalg.norm(u - ref64) / np.linalg.norm(ref64)),
             "u_minus_c_max_rel": float(np.max(np.abs((u - c) - ref64)) / denom),
         })
+    if w.op == "euler_kahan":
+        U0 = storage_to_f64(state_host[:4], w.dtype)
+        with Swept2D(N, N, op="euler_rk2", tile=w.tile, params=w.params, stream=stream) as f64:
+            f64.set_state(np.ascontiguousarray(np.concatenate([U0, U0])))
+            f64.advance(w.nsteps)
+            ref64 = f64.get_state()[:4]
+        U = storage_to_f64(out_sw[:4], w.dtype)
+        C = storage_to_f64(out_sw[8:12], w.dtype)
+        names = ("rho", "m", "q", "E")
+        rep["fp64_reference"] = (f"GPU FP64 Euler path, {w.nsteps} steps from the same "
+                                 "initial values")
+        for v in range(4):
+            denom = max(np.max(np.abs(ref64[v])), np.max(np.abs(U0[v])))
+            rep[f"{names[v]}_max_rel"] = float(np.max(np.abs(U[v] - ref64[v])) / denom)
+            rep[f"{names[v]}_l2_rel"] = float(np.linalg.norm(U[v] - ref64[v])
+                                              / max(np.linalg.norm(ref64[v]), 1e-300))
+        denom = max(np.max(np.abs(ref64)), np.max(np.abs(U0)))
+        rep["U_max_rel_to_max_abs"] = float(np.max(np.abs(U - ref64)) / denom)
+        rep["U_minus_C_max_rel_to_max_abs"] = float(np.max(np.abs((U - C) - ref64)) / denom)
     return rep
 
 
@@ -551,7 +593,7 @@ def naive_kernel_ms(nv, state_dev, stream, w):
     nv.set_timing(True)
     with torch.cuda.stream(stream):
         nv.set_state(state_dev)
-        nv.advance(200 if w.op != "euler_rk2" else 20, mode="naive")
+        nv.advance(20 if w.op in ("euler_rk2", "euler_kahan") else 200, mode="naive")
     n, ms = nv.kernel_stats("naive")
     nv.set_timing(False)
     return ms / max(1, n)

@@ -81,6 +81,13 @@ typedef struct swept2d swept2d_t;
  *             Courant number; plane 0 = u^n, plane 1 = u^{n-1}:
  *             d = ((u_E + u_S) + (u_W + u_N)) - 4u, u' = (2u - u_old) + C^2 d
  *             (fused), and the new u_old is u. C^2 is formed as C*C.
+ *  EULER_KAHAN nvars 12, nstages 2, dtype F32 or BF16, params as EULER_RK2:
+ *             the same scheme in binary32 arithmetic with the time update
+ *             compensated as in HEAT_KAHAN; planes 0-3 = U, 4-7 = U*, 8-11 =
+ *             the compensation C of U (start it at 0). Stage 0 writes U* =
+ *             store(U + dt/2 L(U)); stage 1: y = dt L(U*) - C, U' = store(U +
+ *             y), C' = store((U' - U) - y). The constants (and a, dt) are formed
+ *             in binary64 as for EULER_RK2 and rounded once to binary32.
  */
 #define SWEPT2D_OP_HEAT       0
 #define SWEPT2D_OP_EULER_RK2  1
@@ -90,6 +97,7 @@ typedef struct swept2d swept2d_t;
 #define SWEPT2D_OP_WIDE2      5
 #define SWEPT2D_OP_HEAT_KAHAN 6
 #define SWEPT2D_OP_WAVE       7
+#define SWEPT2D_OP_EULER_KAHAN 8
 
 /* Element types of the state. */
 #define SWEPT2D_F64  0

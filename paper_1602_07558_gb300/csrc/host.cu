@@ -144,6 +144,9 @@ const OpTable *table_for(int op, int dtype) {
         case SWEPT2D_OP_HEAT_KAHAN:
             return dtype == SWEPT2D_F32 ? swept::optable_heat_kahan_f32()
                  : dtype == SWEPT2D_BF16 ? swept::optable_heat_kahan_bf16() : nullptr;
+        case SWEPT2D_OP_EULER_KAHAN:
+            return dtype == SWEPT2D_F32 ? swept::optable_euler_kahan_f32()
+                 : dtype == SWEPT2D_BF16 ? swept::optable_euler_kahan_bf16() : nullptr;
         case SWEPT2D_OP_HEAT: return swept::optable_heat();
         case SWEPT2D_OP_EULER_RK2: return swept::optable_euler();
         case SWEPT2D_OP_INCREMENT: return swept::optable_increment();
@@ -157,7 +160,8 @@ const OpTable *table_for(int op, int dtype) {
 
 bool dtype_ok(int op, int dtype) {
     if (op == SWEPT2D_OP_HASH || op == SWEPT2D_OP_WIDE2) return dtype == SWEPT2D_U64;
-    if (op == SWEPT2D_OP_HEAT_KAHAN) return dtype == SWEPT2D_F32 || dtype == SWEPT2D_BF16;
+    if (op == SWEPT2D_OP_HEAT_KAHAN || op == SWEPT2D_OP_EULER_KAHAN)
+        return dtype == SWEPT2D_F32 || dtype == SWEPT2D_BF16;
     return dtype == SWEPT2D_F64;
 }
 
@@ -326,7 +330,7 @@ int swept2d_create(swept2d_t **out, int nx, int ny, int nvars, int nstages, int 
         delete h;
         return code;
     };
-    if (op < 0 || op > SWEPT2D_OP_WAVE) { fail(h, 0, "unknown op"); return bail(SWEPT2D_EINVAL); }
+    if (op < 0 || op > SWEPT2D_OP_EULER_KAHAN) { fail(h, 0, "unknown op"); return bail(SWEPT2D_EINVAL); }
     if (!dtype_ok(op, dtype)) { fail(h, 0, "dtype does not match the op"); return bail(SWEPT2D_EINVAL); }
     const OpTable *t = table_for(op, dtype);
     if (!t) { fail(h, 0, "unknown op"); return bail(SWEPT2D_EINVAL); }
@@ -378,6 +382,7 @@ int swept2d_create(swept2d_t **out, int nx, int ny, int nvars, int nstages, int 
             h->consts[0] = params[0] * params[0];
             break;
         case SWEPT2D_OP_EULER_RK2:
+        case SWEPT2D_OP_EULER_KAHAN:
             if (nparams < 3) {
                 fail(h, 0, "euler needs params {gamma, cfl, kappa[, lx, ly]}");
                 return bail(SWEPT2D_EINVAL);
@@ -427,14 +432,14 @@ int swept2d_set_state(swept2d_t *h, const void *src, int src_is_device) {
     h->substeps = 0;
     if ((e = cudaMemsetAsync(h->errword, 0, sizeof(int), h->stream)) != cudaSuccess)
         return cuda_fail(h, e, "set_state error word");
-    if (h->op == SWEPT2D_OP_EULER_RK2) {
+    if (h->op == SWEPT2D_OP_EULER_RK2 || h->op == SWEPT2D_OP_EULER_KAHAN) {
         const double gamma = h->params[0], cfl = h->params[1], kappa = h->params[2];
         const double lx = h->nparams >= 5 ? h->params[3] : 1.0;
         const double ly = h->nparams >= 5 ? h->params[4] : 1.0;
         const double dx = lx / h->nx, dy = ly / h->ny;
         double a = 0.0;
         int rc = launch(h, SWEPT2D_K_REDUCE, "wave speed", [&] {
-            return swept::euler_wavespeed((const double *)h->state, h->nx, h->ny, gamma,
+            return swept::euler_wavespeed(h->state, h->esize, h->nx, h->ny, gamma,
                                           h->scratch8, &a, h->stream);
         });
         if (rc) return rc;

@@ -306,6 +306,51 @@ __device__ __forceinline__ void compute_rect(const EulerOp &op, int stage, u64, 
     }
 }
 
+// Euler in binary32 with reduced-precision storage: the same two passes as
+// EulerOp (binary32 fluxes of the grown rectangle in the aux planes, then the
+// per-point combination). Same values as EulerKahanOp::operator().
+template <class SS>
+__device__ __forceinline__ void compute_rect(const EulerKahanOp<SS> &op, int stage, u64,
+                                             const SS *src, SS *dst, SS *aux_s, int P, int x0,
+                                             int y0, int W, int H) {
+    typedef Store<SS> St;
+    float *aux = reinterpret_cast<float *>(aux_s);
+    const int plane = P * P, w0 = stage == 0 ? 0 : 4;
+    if (W <= 0 || H <= 0) return;
+    for (LinearWalk w(W + 2); w.yy < H + 2; w.next(W + 2)) {
+        const int off = (y0 + w.yy) * P + (x0 + w.xx);     // point (x0-1+xx, y0-1+yy)
+        float F[4], G[4];
+        op.fluxes(St::ld(src[w0 * plane + off]), St::ld(src[(w0 + 1) * plane + off]),
+                  St::ld(src[(w0 + 2) * plane + off]), St::ld(src[(w0 + 3) * plane + off]), F, G);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            aux[c * plane + off] = F[c];
+            aux[(4 + c) * plane + off] = G[c];
+        }
+    }
+    __syncthreads();
+    for (LinearWalk w(W); w.yy < H; w.next(W)) {
+        const int off = (y0 + w.yy + 1) * P + (x0 + w.xx + 1);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const SS *Wc = src + (w0 + c) * plane + off;
+            const float *F = aux + c * plane + off, *G = aux + (4 + c) * plane + off;
+            const float L = op.rate(St::ld(Wc[0]), St::ld(Wc[1]), St::ld(Wc[-1]), St::ld(Wc[P]),
+                                    St::ld(Wc[-P]), __fsub_rn(F[1], F[-1]),
+                                    __fsub_rn(G[P], G[-P]));
+            if (stage == 0) {
+                dst[c * plane + off] = src[c * plane + off];
+                dst[(4 + c) * plane + off] = op.midpoint(L, St::ld(src[c * plane + off]));
+                dst[(8 + c) * plane + off] = src[(8 + c) * plane + off];
+            } else {
+                op.accumulate(L, St::ld(src[c * plane + off]), St::ld(src[(8 + c) * plane + off]),
+                              dst[c * plane + off], dst[(8 + c) * plane + off]);
+                dst[(4 + c) * plane + off] = src[(4 + c) * plane + off];
+            }
+        }
+    }
+}
+
 // Wave: the same pair-sum sharing as the heat update (pass 1 forms the
 // east+south pair sums of the rectangle grown by one into the aux plane), then
 // u' = (2u - u_old) + C^2 d, u_old' = u.

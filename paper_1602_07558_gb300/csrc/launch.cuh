@@ -199,9 +199,12 @@ const OpTable *optable_wide2();
 const OpTable *optable_wave();
 const OpTable *optable_heat_kahan_f32();
 const OpTable *optable_heat_kahan_bf16();
+const OpTable *optable_euler_kahan_f32();
+const OpTable *optable_euler_kahan_bf16();
 
-// Euler helpers (euler.cu): the max wave speed of planes 0-3 of a state.
-cudaError_t euler_wavespeed(const double *state, int nx, int ny, double gamma,
+// Euler helper (op_euler.cu): the max wave speed of planes 0-3 of a state whose
+// elements are esize bytes (8 binary64, 4 binary32, 2 bfloat16).
+cudaError_t euler_wavespeed(const void *state, int esize, int nx, int ny, double gamma,
                             unsigned long long *d_scratch, double *a_out, cudaStream_t st);
 
 }  // namespace swept

@@ -86,6 +86,92 @@ struct HeatKahanOp {
     }
 };
 
+// The Euler system of EulerOp in binary32 arithmetic with reduced-precision
+// storage SS (float or bfloat16) and the time accumulation of each step
+// compensated as in HeatKahanOp. Point state: U (0-3), U* (4-7), C (8-11).
+//   stage 0: U* = store(U + (dt/2) L(U))            (one fused multiply-add)
+//   stage 1: y = dt L(U*) - C;  t = U + y;  U' = store(t);  C' = store((U' - U) - y)
+// L is EulerOp's formula with the same fused operations, in binary32; the
+// constants are EulerOp's (FP64, from the host) rounded once to binary32.
+template <class SS>
+struct EulerKahanOp {
+    typedef SS S;
+    // aux: the 8 binary32 flux planes of a level, counted in SS elements
+    static constexpr int NV = 12, NST = 2, AUX = 8 * (int)(sizeof(float) / sizeof(SS));
+    static constexpr bool STAGE = false;
+    float gm1, cx, cy, kax, kay, tau0, tau1;
+    __host__ __device__ explicit EulerKahanOp(const double *c)
+        : gm1((float)c[0]), cx((float)c[1]), cy((float)c[2]), kax((float)c[3]),
+          kay((float)c[4]), tau0((float)c[5]), tau1((float)c[6]) {}
+
+    __device__ __forceinline__ void fluxes(float r, float m, float q, float E, float *F,
+                                           float *G) const {
+        const float iv = __fdiv_rn(1.0f, r);
+        const float u = __fmul_rn(m, iv), v = __fmul_rn(q, iv);
+        const float ke = __fmul_rn(0.5f, __fmaf_rn(m, u, __fmul_rn(q, v)));
+        const float pr = __fmul_rn(gm1, __fsub_rn(E, ke));
+        const float Ep = __fadd_rn(E, pr);
+        F[0] = m;
+        F[1] = __fmaf_rn(m, u, pr);
+        F[2] = __fmul_rn(q, u);
+        F[3] = __fmul_rn(Ep, u);
+        G[0] = q;
+        G[1] = __fmul_rn(m, v);
+        G[2] = __fmaf_rn(q, v, pr);
+        G[3] = __fmul_rn(Ep, v);
+    }
+    // L of one conserved variable from the stencil values and flux differences
+    __device__ __forceinline__ float rate(float wc, float wE, float wW, float wS, float wN,
+                                          float dF, float dG) const {
+        const float lx = __fmaf_rn(-2.0f, wc, __fadd_rn(wE, wW));
+        const float ly = __fmaf_rn(-2.0f, wc, __fadd_rn(wS, wN));
+        const float diss = __fmaf_rn(kax, lx, __fmul_rn(kay, ly));
+        const float flux = __fmaf_rn(cx, dF, __fmul_rn(cy, dG));
+        return __fsub_rn(diss, flux);
+    }
+    // stage 0: the midpoint value of variable c from its rate
+    __device__ __forceinline__ S midpoint(float L, float u) const {
+        return Store<S>::st(__fmaf_rn(tau0, L, u));
+    }
+    // stage 1: the compensated update of (u, c) from the rate
+    __device__ __forceinline__ void accumulate(float L, float u, float cc, S &u_out,
+                                               S &c_out) const {
+        typedef Store<S> St;
+        const float y = __fsub_rn(__fmul_rn(tau1, L), cc);
+        u_out = St::st(__fadd_rn(u, y));
+        c_out = St::st(__fsub_rn(__fsub_rn(St::ld(u_out), u), y));
+    }
+    template <class A>
+    __device__ __forceinline__ void operator()(int stage, u64, const A &a, S *out) const {
+        typedef Store<S> St;
+        const int w0 = stage == 0 ? 0 : 4;
+        float FW[4], GW[4], FE[4], GE[4], FN[4], GN[4], FS[4], GS[4];
+        fluxes(St::ld(a(-1, 0, w0)), St::ld(a(-1, 0, w0 + 1)), St::ld(a(-1, 0, w0 + 2)),
+               St::ld(a(-1, 0, w0 + 3)), FW, GW);
+        fluxes(St::ld(a(1, 0, w0)), St::ld(a(1, 0, w0 + 1)), St::ld(a(1, 0, w0 + 2)),
+               St::ld(a(1, 0, w0 + 3)), FE, GE);
+        fluxes(St::ld(a(0, -1, w0)), St::ld(a(0, -1, w0 + 1)), St::ld(a(0, -1, w0 + 2)),
+               St::ld(a(0, -1, w0 + 3)), FN, GN);
+        fluxes(St::ld(a(0, 1, w0)), St::ld(a(0, 1, w0 + 1)), St::ld(a(0, 1, w0 + 2)),
+               St::ld(a(0, 1, w0 + 3)), FS, GS);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const float L = rate(St::ld(a(0, 0, w0 + c)), St::ld(a(1, 0, w0 + c)),
+                                 St::ld(a(-1, 0, w0 + c)), St::ld(a(0, 1, w0 + c)),
+                                 St::ld(a(0, -1, w0 + c)), __fsub_rn(FE[c], FW[c]),
+                                 __fsub_rn(GS[c], GN[c]));
+            if (stage == 0) {
+                out[c] = a(0, 0, c);
+                out[4 + c] = midpoint(L, St::ld(a(0, 0, c)));
+                out[8 + c] = a(0, 0, 8 + c);
+            } else {
+                accumulate(L, St::ld(a(0, 0, c)), St::ld(a(0, 0, 8 + c)), out[c], out[8 + c]);
+                out[4 + c] = a(0, 0, 4 + c);
+            }
+        }
+    }
+};
+
 // 2D wave equation u_tt = c^2 laplace(u), leapfrog in time (Section 6's
 // experiment); point state (u^n, u^{n-1}):
 //   d = ((u_E + u_S) + (u_W + u_N)) - 4u,  u^{n+1} = (2u - u^{n-1}) + C^2 d (fused)

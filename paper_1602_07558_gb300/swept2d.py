@@ -22,7 +22,7 @@ from . import build as _build
 
 OK, EINVAL, ECUDA, ENOMEM, ETIMEOUT, ESTATE = 0, -1, -2, -3, -4, -5
 OPS = {"heat": 0, "euler_rk2": 1, "increment": 2, "hash": 3, "leveltag": 4, "wide2": 5,
-       "heat_kahan": 6, "wave": 7}
+       "heat_kahan": 6, "wave": 7, "euler_kahan": 8}
 DTYPES = {"f64": (0, np.float64), "f32": (1, np.float32), "bf16": (2, np.uint16),
           "u64": (3, np.uint64)}
 # (nvars, nstages, default dtype) of each point update; bf16 states are passed
@@ -36,6 +36,7 @@ OP_SHAPE = {
     "wide2": (5, 2, "u64"),
     "heat_kahan": (2, 1, "f32"),
     "wave": (2, 1, "f64"),
+    "euler_kahan": (12, 2, "f32"),
 }
 MODES = {"swept": 0, "naive": 1, "persistent": 0x200}
 GRAPH = 0x100

@@ -225,6 +225,35 @@ def test_wave_swept_equals_naive_and_oracle(oracle_lib, nx, ny, tile, nsteps):
     assert np.array_equal(swept[0], ref_u) and np.array_equal(swept[1], ref_uo)
 
 
+def _euler_kahan_state(nx, ny, storage, seed):
+    U = inputs.euler_pulse(nx, ny, seed, gamma=GAMMA).astype(np.float32)
+    if storage == "bf16":
+        U = _to_bf16_bits(U)
+    return np.concatenate([U, U, np.zeros_like(U)])
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+@pytest.mark.parametrize("nx,ny,tile,nsteps", [(64, 48, 16, 21), (32, 32, 8, 13), (64, 64, 32, 20)])
+def test_euler_kahan_swept_equals_naive_and_oracle(oracle_lib, storage, nx, ny, tile, nsteps):
+    """Euler in binary32 arithmetic with compensated update and binary32 /
+    bfloat16 storage: all 12 planes (U, U*, C) bit for bit the oracle's, and
+    swept == naive; a and dt (formed in FP64 from the stored values) exactly
+    the oracle's."""
+    S = _euler_kahan_state(nx, ny, storage, seed=5)
+    Uf = (oracle_lib.bf16_bits_to_f32(S[:4]) if storage == "bf16" else S[:4]).astype(np.float64)
+    a, dt = oracle_lib.euler_setup(Uf, GAMMA, CFL)
+    ref = oracle_lib.euler_kahan(S, GAMMA, dt, KAPPA, a, nsteps, storage)
+    params = (GAMMA, CFL, KAPPA)
+    with Swept2D(nx, ny, op="euler_kahan", tile=tile, params=params, dtype=storage) as s:
+        s.set_state(S)
+        assert s.query("wavespeed") == a and s.query("dt") == dt
+        s.advance(nsteps, mode="swept")
+        swept = s.get_state()
+    naive = run("euler_kahan", S, nsteps, tile, "naive", params, dtype=storage)
+    assert np.array_equal(swept, naive)
+    assert np.array_equal(swept, ref)
+
+
 # ---------------------------------------------------------- persistent form
 
 @pytest.mark.parametrize("op,dtype,nx,ny,tile,nsteps", [
@@ -238,15 +267,20 @@ def test_wave_swept_equals_naive_and_oracle(oracle_lib, nx, ny, tile, nsteps):
     ("wide2", "u64", 48, 32, 8, 19),      # nstages = 2
     ("wave", "f64", 64, 64, 16, 70),
     ("euler_rk2", "f64", 32, 32, 16, 9),
+    ("euler_kahan", "f32", 32, 32, 16, 11),
+    ("euler_kahan", "bf16", 64, 32, 16, 12),
 ])
 def test_persistent_form_gives_the_same_bits(oracle_lib, op, dtype, nx, ny, tile, nsteps):
     """One persistent launch per advance (work items with neighbourhood waits)
     equals the naive path bit for bit, also through a captured graph."""
     rng = np.random.default_rng(nx + ny + tile)
-    nv = {"hash": 1, "heat": 1, "heat_kahan": 2, "wide2": 5, "wave": 2, "euler_rk2": 8}[op]
+    nv = {"hash": 1, "heat": 1, "heat_kahan": 2, "wide2": 5, "wave": 2, "euler_rk2": 8,
+          "euler_kahan": 12}[op]
     params = {"hash": (), "wide2": (), "heat": (0.2,), "heat_kahan": (0.2,), "wave": (0.3,),
-              "euler_rk2": (GAMMA, CFL, KAPPA)}[op]
-    if dtype == "u64":
+              "euler_rk2": (GAMMA, CFL, KAPPA), "euler_kahan": (GAMMA, CFL, KAPPA)}[op]
+    if op == "euler_kahan":
+        u0 = _euler_kahan_state(nx, ny, dtype, seed=6)
+    elif dtype == "u64":
         u0 = rng.integers(0, 2**64, size=(nv, ny, nx), dtype=np.uint64)
     elif dtype == "f32":
         u0 = np.stack([rng.random((ny, nx)), np.zeros((ny, nx))]).astype(np.float32)
