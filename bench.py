@@ -398,8 +398,9 @@ def main():
         args.stage = int(stage)
     sw = mk(w.tile)
     if args.threads is not None or args.stage is not None:
-        sw.set_tuning(args.threads or 256,
-                      bool(args.stage) if args.stage is not None else w.op == "heat_kahan")
+        sw.set_tuning(args.threads or int(sw.query("threads")),
+                      bool(args.stage) if args.stage is not None else bool(sw.query("stage")))
+    args.threads, args.stage = int(sw.query("threads")), int(sw.query("stage"))
     two_stage = w.op in ("euler_rk2", "euler_kahan")
     nv = None if args.no_naive else mk(0)
 
@@ -503,7 +504,7 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": w.dtype, "data": "synthetic",
             "config": {"workload": f"{w.describe}, swept tile {w.tile}", "grid": N,
-                       "nsteps": w.nsteps, "tile": w.tile, "threads": args.threads or 256,
+                       "nsteps": w.nsteps, "tile": w.tile, "threads": args.threads,
                        "stage": args.stage, "autotune": tune_table,
                        "parallelism": "replicas" if world > 1 else "single",
                        "cuda_graph": bool(args.graph),

@@ -117,8 +117,8 @@ typedef struct swept2d swept2d_t;
 /* Flag OR-ed into SWEPT2D_SWEPT: run all half cycles of the advance as one
  * persistent launch (resident blocks take tile work items in phase order and
  * wait, with bounded spins, only for their 3 x 3 tile neighbourhood to finish
- * the previous phase), instead of two launches per half cycle. Needs the
- * staged panel set to fit in shared memory (EINVAL otherwise). Same bits. */
+ * the previous phase), instead of two launches per half cycle. Uses the
+ * handle's tuning (threads, staging); same bits. */
 #define SWEPT2D_PERSISTENT 0x200
 
 /*
@@ -168,7 +168,7 @@ int swept2d_get_state(swept2d_t *h, void *dst, int dst_is_device);
  * word is cleared again before the call returns.
  * Returns SWEPT2D_ETIMEOUT when the kernel reported the timed-out wait (the
  * expected outcome), SWEPT2D_ESTATE if it did not, EINVAL (no tile, bad
- * spin_limit, staged panels too large), ECUDA.
+ * spin_limit, shared memory too large), ECUDA.
  */
 int swept2d_selftest_wait_timeout(swept2d_t *h, long long spin_limit);
 
@@ -189,6 +189,8 @@ const char *swept2d_last_error(const swept2d_t *h);
 #define SWEPT2D_Q_PANEL_BYTES   5   /* bytes of one panel buffer (0 if naive-only) */
 #define SWEPT2D_Q_SMEM_BYTES    6   /* dynamic shared memory per swept block */
 #define SWEPT2D_Q_CELLS         7   /* points of the grid (of all grids, for a batch) */
+#define SWEPT2D_Q_THREADS       8   /* swept threads per block (swept2d_set_tuning) */
+#define SWEPT2D_Q_STAGE         9   /* 1 if the swept kernels stage panels by TMA */
 int swept2d_query(const swept2d_t *h, int what, double *out);
 
 /* Launch shape of the swept kernels of a handle (a tuning knob, not a change

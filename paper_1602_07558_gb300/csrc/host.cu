@@ -213,7 +213,7 @@ int swept_substeps(swept2d *h, long long total, bool persistent) {
         if (e != cudaSuccess) return cuda_fail(h, e, "persistent schedule reset");
         int rc = launch(h, SWEPT2D_K_OCTAHEDRON, "persistent kernel", [&] {
             return h->ops->persistent(h->G, h->consts, h->state, h->up, h->br, h->sched, (int)H,
-                                      g_start, h->errword, h->tune.threads, 0,
+                                      g_start, h->errword, h->tune, 0,
                                       swept::kPersistSpinLimit, h->stream);
         });
         if (rc) return rc;
@@ -466,8 +466,8 @@ static int persistent_prepare(swept2d *h, long long H) {
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
         optin = 227 * 1024;
-    if (h->ops->smem_for(h->n, true) > (size_t)optin)
-        return fail(h, SWEPT2D_EINVAL, "advance: persistent form needs staged panels, which do not fit");
+    if (h->ops->smem_for(h->n, h->tune.stage) > (size_t)optin)
+        return fail(h, SWEPT2D_EINVAL, "advance: the persistent form's shared memory does not fit");
     if ((long long)h->G.T * h->G.Q * (2 * H + 1) >= (1LL << 31))
         return fail(h, SWEPT2D_EINVAL, "advance: too many work items for one persistent launch");
     if (!h->sched) {
@@ -490,7 +490,7 @@ int swept2d_selftest_wait_timeout(swept2d_t *h, long long spin_limit) {
     // waits for a phase-1 counter that nothing releases
     rc = launch(h, SWEPT2D_K_OCTAHEDRON, "persistent kernel (wait-timeout self-test)", [&] {
         return h->ops->persistent(h->G, h->consts, h->state, h->up, h->br, h->sched, 1,
-                                  (u64)h->substeps, h->errword, h->tune.threads, NT, spin_limit,
+                                  (u64)h->substeps, h->errword, h->tune, NT, spin_limit,
                                   h->stream);
     });
     if (rc) return rc;
@@ -570,6 +570,8 @@ int swept2d_query(const swept2d_t *h, int what, double *out) {
         case SWEPT2D_Q_PANEL_BYTES: *out = (double)h->panel_bytes; break;
         case SWEPT2D_Q_SMEM_BYTES: *out = (double)h->smem_bytes; break;
         case SWEPT2D_Q_CELLS: *out = (double)h->nx * h->ny; break;
+        case SWEPT2D_Q_THREADS: *out = h->tune.threads; break;
+        case SWEPT2D_Q_STAGE: *out = h->tune.stage ? 1.0 : 0.0; break;
         default: return SWEPT2D_EINVAL;
     }
     return SWEPT2D_OK;

@@ -160,12 +160,17 @@ __device__ __forceinline__ bool block_wait_bulk(unsigned long long *bar, int *er
 __device__ __forceinline__ int div_small(int e, float rd) {
     return (int)(((float)e + 0.5f) * rd);
 }
+// The reciprocal div_small takes: an approximate binary32 reciprocal (within 2
+// ulp, 2^-22 relative) keeps the truncation exact for e < 2^20, since the
+// total relative error (under 1.25 * 2^-22) times (e + 1/2) / d stays below the
+// 1/(2d) margin.
+__device__ __forceinline__ float recip_small(int d) { return __fdividef(1.0f, (float)d); }
 
 struct LinearWalk {
     int xx, yy, dq, dr;
     __device__ __forceinline__ explicit LinearWalk(int W) {
         const int T = blockDim.x;
-        const float rw = 1.0f / (float)W;
+        const float rw = recip_small(W);
         yy = div_small((int)threadIdx.x, rw);
         xx = (int)threadIdx.x - yy * W;
         dq = div_small(T, rw);
@@ -247,7 +252,7 @@ __device__ __forceinline__ void compute_rect(const HeatOp &op, int, u64, const d
     // (FP64-pipe bound: the per-point decode by reciprocal keeps independent
     // points per thread visible to the scheduler better than a carried walk)
     const int W1 = W + 1, cnt1 = W1 * (H + 1);
-    const float rw1 = 1.0f / (float)W1, rw = 1.0f / (float)W;
+    const float rw1 = recip_small(W1), rw = recip_small(W);
     for (int e = threadIdx.x; e < cnt1; e += blockDim.x) {
         const int yy = div_small(e, rw1), xx = e - yy * W1;
         const int off = (y0 + yy) * P + (x0 + xx);      // point (x0-1+xx, y0-1+yy)
@@ -261,6 +266,55 @@ __device__ __forceinline__ void compute_rect(const HeatOp &op, int, u64, const d
         const double c = src[off];
         const double sum = __dadd_rn(aux[off], aux[off - P - 1]);
         dst[off] = __fma_rn(op.r, __fma_rn(-4.0, c, sum), c);
+    }
+}
+
+// Reduced-precision heat: each thread updates a column strip of up to R
+// points of the rectangle. All of the strip's loads (R + 2 centre-column
+// values, R compensations, R east and R west values: 4 per point instead of 6)
+// are issued before its R independent updates, so they overlap, and the index
+// walk runs once per strip; full strips take a path without per-row guards.
+// Same values as HeatKahanOp::operator().
+template <class SS, int R, bool FULL>
+__device__ __forceinline__ void heat_kahan_strip(const HeatKahanOp<SS> &op,
+                                                 const SS *__restrict__ src, SS *__restrict__ dst,
+                                                 int P, int plane, int off, int rows) {
+    typedef Store<SS> St;
+    float u[R + 2], cv[R], ue[R], uw[R];
+#pragma unroll
+    for (int r = 0; r < R + 2; ++r)              // u[r]: row r - 1 of the strip, -1 .. rows
+        u[r] = (FULL || r <= rows + 1) ? St::ld(src[off + (r - 1) * P]) : 0.0f;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int o = off + r * P;
+        const bool in = FULL || r < rows;
+        cv[r] = in ? St::ld(src[plane + o]) : 0.0f;
+        ue[r] = in ? St::ld(src[o + 1]) : 0.0f;
+        uw[r] = in ? St::ld(src[o - 1]) : 0.0f;
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+        if (FULL || r < rows)
+            op.update(u[r + 1], cv[r], ue[r], u[r + 2], uw[r], u[r], dst[off + r * P],
+                      dst[plane + off + r * P]);
+}
+
+template <class SS>
+__device__ __forceinline__ void compute_rect(const HeatKahanOp<SS> &op, int, u64,
+                                             const SS *__restrict__ src, SS *__restrict__ dst,
+                                             SS *, int P, int x0, int y0, int W, int H) {
+    constexpr int R = 4;
+    const int plane = P * P;
+    if (W <= 0 || H <= 0) return;
+    const int nb = (H + R - 1) / R;
+    for (LinearWalk w(W); w.yy < nb; w.next(W)) {
+        const int yb = w.yy * R;
+        const int rows = H - yb;
+        const int off = (y0 + yb + 1) * P + (x0 + w.xx + 1);
+        if (rows >= R)
+            heat_kahan_strip<SS, R, true>(op, src, dst, P, plane, off, R);
+        else
+            heat_kahan_strip<SS, R, false>(op, src, dst, P, plane, off, rows);
     }
 }
 
@@ -359,7 +413,7 @@ __device__ __forceinline__ void compute_rect(const WaveOp &op, int, u64, const d
                                              int W, int H) {
     const int plane = P * P;
     const int W1 = W + 1, cnt1 = W1 * (H + 1);
-    const float rw1 = 1.0f / (float)W1, rw = 1.0f / (float)W;
+    const float rw1 = recip_small(W1), rw = recip_small(W);
     for (int e = threadIdx.x; e < cnt1; e += blockDim.x) {
         const int yy = div_small(e, rw1), xx = e - yy * W1;
         const int off = (y0 + yy) * P + (x0 + xx);      // point (x0-1+xx, y0-1+yy)
@@ -397,11 +451,18 @@ __device__ __forceinline__ void write_up_panels(const S *cur, int P, const Geom 
     for (int line = threadIdx.x >> 5; line < 8; line += nw) {   // 4 sides x 2 lines
         const int side = line >> 1, d = line & 1;
         S *dst = up + ((size_t)slot * 4 + side) * NV * G.PS + off + d * L;
-        for (int p = lane; p < L; p += 32) {
-            int a, b;
-            up_panel_xy(side, n, k, d, p, a, b);
+        // buffer index of element p: base + p * step (up_panel_xy, plus the halo)
+        int a0, b0, a1, b1;
+        up_panel_xy(side, n, k, d, 0, a0, b0);
+        up_panel_xy(side, n, k, d, 1, a1, b1);
+        const int base = (b0 + 1) * P + (a0 + 1), step = (b1 - b0) * P + (a1 - a0);
+        S *dv[NV];
 #pragma unroll
-            for (int v = 0; v < NV; ++v) dst[(size_t)v * G.PS + p] = cur[v * plane + (b + 1) * P + (a + 1)];
+        for (int v = 0; v < NV; ++v) dv[v] = dst + (size_t)v * G.PS;
+        for (int p = lane; p < L; p += 32) {
+            const S *src = cur + base + p * step;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) dv[v][p] = src[v * plane];
         }
     }
 }
@@ -613,8 +674,16 @@ __device__ __forceinline__ void bridge_tile(const Op &op, const Geom &G, const t
         }
         if constexpr (!STG) async_commit();
     };
-    load_strips(0, bufs[0]);
-    if constexpr (!STG) async_wait();
+    if constexpr (STG) {
+        load_strips(0, bufs[0]);
+    } else {
+        // every level's strips at once, each into its level's buffer: strips
+        // of one parity never overlap, and no level's rectangle, reads or
+        // panel reads touch a later level's strip, so the copies' latency is
+        // paid once per tile instead of once per level
+        for (int k = 0; k < h; ++k) load_strips(k, bufs[k & 1]);
+        async_wait();
+    }
     __syncthreads();
     for (int k = 0; k < h; ++k) {
         S *cur = bufs[k & 1];
@@ -638,14 +707,13 @@ __device__ __forceinline__ void bridge_tile(const Op &op, const Geom &G, const t
             }
         }
         if (k + 1 < h) {
-            load_strips(k + 1, nxt);   // disjoint from the rectangle computed below
+            if constexpr (STG) load_strips(k + 1, nxt);   // disjoint from the rectangle below
             const u64 g = g0 + k;
             const int u0 = k + 1, uw = n - 2 * k - 2, w0 = h - k - 1, ww = 2 * k + 2;
             if (xb)
                 compute_rect(op, (int)(g % Op::NST), g, cur, nxt, aux, P, w0, u0, ww, uw);
             else
                 compute_rect(op, (int)(g % Op::NST), g, cur, nxt, aux, P, u0, w0, uw, ww);
-            if constexpr (!STG) async_wait();
         }
         __syncthreads();
     }
@@ -724,17 +792,24 @@ __device__ __forceinline__ bool down_body(const Op &op, const Geom &G, unsigned 
         }
         if constexpr (!STG) async_commit();
     };
-    load_ring(0, buf0);
-    if constexpr (!STG) async_wait();
+    if constexpr (STG) {
+        load_ring(0, buf0);
+    } else {
+        // every level's ring at once, each into its level's buffer: rings of
+        // one parity never overlap and lie outside every earlier level's
+        // square and reads, so the copies' latency is paid once per tile
+        for (int k = 0; k < h; ++k) load_ring(k, (k & 1) ? buf1 : buf0);
+        async_wait();
+    }
     __syncthreads();
     for (int k = 0; k < h; ++k) {
         S *cur = (k & 1) ? buf1 : buf0;
         S *nxt = (k & 1) ? buf0 : buf1;
-        if (k + 1 < h) load_ring(k + 1, nxt);   // disjoint from the square computed below
+        if constexpr (STG)
+            if (k + 1 < h) load_ring(k + 1, nxt);   // disjoint from the square computed below
         const u64 g = g0 + k;
         compute_rect(op, (int)(g % Op::NST), g, cur, nxt, aux, P, h - k - 1, h - k - 1,
                      2 * k + 2, 2 * k + 2);
-        if constexpr (!STG) async_wait();
         __syncthreads();
     }
     return true;
@@ -812,9 +887,10 @@ __global__ void __launch_bounds__(256) down_kernel(Op op, Geom G, const typename
 // replaced by those waits. Items are taken in index order and every dependency
 // has a smaller index, so the lowest unfinished item can always run: no
 // deadlock, whatever number of blocks is resident. Panels written by one block
-// are read by another through TMA bulk copies (L2) after an acquire and a
-// generic-to-async proxy fence, so no stale L1 line is ever read. Waits are
-// bounded: on timeout the error word is set and the block stops.
+// are read by another after an acquire of the writer's release (and, for the
+// TMA bulk copies of the staged form, a generic-to-async proxy fence); the
+// unstaged form's element copies are ordinary reads after that acquire. Waits
+// are bounded: on timeout the error word is set and the block stops.
 // A dependency is at most one work item away (tens of microseconds); the
 // default bound (about a second of 64 ns naps and polls) only catches a block
 // that never finishes.
@@ -837,7 +913,7 @@ __device__ __forceinline__ void st_release(int *p, int v) {
 // `first` is the first work item taken (0; a positive value skips items, which
 // only the wait-timeout self-test does: the skipped items' phases are never
 // released, so every wait runs out).
-template <class Op>
+template <class Op, bool STG>
 __global__ void __launch_bounds__(256) persistent_kernel(Op op, Geom G, typename Op::S *state,
                                                          typename Op::S *upp, typename Op::S *br,
                                                          int *stage, int *queue, int H, u64 g0,
@@ -892,13 +968,13 @@ __global__ void __launch_bounds__(256) persistent_kernel(Op op, Geom G, typename
             const u64 gj = g0 + (u64)j * h;
             const int o = (j & 1) ? h : 0;
             if ((p & 1) == 0) {                     // bridges of half cycle j
-                bridge_tile<Op, true>(op, G, upp, br, gj, err, I, J, false);
+                bridge_tile<Op, STG>(op, G, upp, br, gj, err, I, J, false);
                 __syncthreads();
-                bridge_tile<Op, true>(op, G, upp, br, gj, err, I, J, true);
+                bridge_tile<Op, STG>(op, G, upp, br, gj, err, I, J, true);
             } else if (j + 1 < H) {
-                octahedron_tile<Op, true>(op, G, br, upp, o, gj, err, I, J);
+                octahedron_tile<Op, STG>(op, G, br, upp, o, gj, err, I, J);
             } else {
-                down_tile<Op, true>(op, G, br, state, o, gj, err, I, J);
+                down_tile<Op, STG>(op, G, br, state, o, gj, err, I, J);
             }
         }
         // make this item's panel (and state) stores visible, to the generic and

@@ -37,7 +37,7 @@ struct OpTable {
     // the whole swept part of an advance (H half cycles) as one persistent
     // launch; sched: T*Q phase counters followed by the queue counter, zeroed
     cudaError_t (*persistent)(const Geom &, const double *c, void *state, void *up, void *br,
-                              int *sched, int H, u64 g0, int *err, int threads, int first,
+                              int *sched, int H, u64 g0, int *err, const Tuning &, int first,
                               long long spin_limit, cudaStream_t);
 };
 
@@ -160,14 +160,15 @@ struct Launch {
         return tn.stage ? down_t<true>(G, c, br, state, o, g0, err, tn.threads, st)
                         : down_t<false>(G, c, br, state, o, g0, err, tn.threads, st);
     }
-    static cudaError_t persistent(const Geom &G, const double *c, void *state, void *upp,
-                                  void *br, int *sched, int H, u64 g0, int *err, int threads,
-                                  int first, long long spin_limit, cudaStream_t st) {
-        const size_t sm = down_smem<Op>(G.n, true);
-        cudaError_t e = allow_smem(persistent_kernel<Op>, sm);
+    template <bool STG>
+    static cudaError_t persistent_t(const Geom &G, const double *c, void *state, void *upp,
+                                    void *br, int *sched, int H, u64 g0, int *err, int threads,
+                                    int first, long long spin_limit, cudaStream_t st) {
+        const size_t sm = down_smem<Op>(G.n, STG);
+        cudaError_t e = allow_smem(persistent_kernel<Op, STG>, sm);
         if (e != cudaSuccess) return e;
         int per_sm = 0, dev = 0, nsm = 0;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel<Op>,
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel<Op, STG>,
                                                                threads, sm)) != cudaSuccess)
             return e;
         cudaGetDevice(&dev);
@@ -176,10 +177,20 @@ struct Launch {
         long long grid = (long long)(per_sm > 0 ? per_sm : 1) * nsm;
         if (grid > nitems) grid = nitems;
         const int NT = G.T * G.Q;
-        persistent_kernel<Op><<<(int)grid, threads, sm, st>>>(Op(c), G, (S *)state, (S *)upp,
-                                                              (S *)br, sched, sched + NT, H, g0,
-                                                              err, first, spin_limit);
+        persistent_kernel<Op, STG><<<(int)grid, threads, sm, st>>>(Op(c), G, (S *)state,
+                                                                   (S *)upp, (S *)br, sched,
+                                                                   sched + NT, H, g0, err, first,
+                                                                   spin_limit);
         return cudaGetLastError();
+    }
+    static cudaError_t persistent(const Geom &G, const double *c, void *state, void *upp,
+                                  void *br, int *sched, int H, u64 g0, int *err,
+                                  const Tuning &tn, int first, long long spin_limit,
+                                  cudaStream_t st) {
+        return tn.stage ? persistent_t<true>(G, c, state, upp, br, sched, H, g0, err, tn.threads,
+                                             first, spin_limit, st)
+                        : persistent_t<false>(G, c, state, upp, br, sched, H, g0, err, tn.threads,
+                                              first, spin_limit, st);
     }
     static const OpTable *table() {
         static const OpTable t = {Op::NV,      Op::NST,     (int)sizeof(S), &swept_smem_bytes<Op>,

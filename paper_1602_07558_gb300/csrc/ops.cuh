@@ -64,7 +64,9 @@ template <class SS>
 struct HeatKahanOp {
     typedef SS S;
     static constexpr int NV = 2, NST = 1, AUX = 0;
-    static constexpr bool STAGE = true;
+    // bfloat16 panels are staged by TMA (element copies of 2 bytes are slow);
+    // binary32 ones are copied straight into the level buffers (more blocks fit)
+    static constexpr bool STAGE = sizeof(SS) == 2;
     float r;
     __host__ __device__ explicit HeatKahanOp(const double *c) : r((float)c[0]) {}
     // the update from the centre (u, c) and the four edge neighbours' u

@@ -41,7 +41,7 @@ OP_SHAPE = {
 MODES = {"swept": 0, "naive": 1, "persistent": 0x200}
 GRAPH = 0x100
 Q = {"dt": 0, "wavespeed": 1, "substeps": 2, "launches": 3, "state_bytes": 4,
-     "panel_bytes": 5, "smem_bytes": 6, "cells": 7}
+     "panel_bytes": 5, "smem_bytes": 6, "cells": 7, "threads": 8, "stage": 9}
 KERNELS = {"naive": 0, "up": 1, "bridge": 2, "octahedron": 3, "down": 4, "reduce": 5}
 
 _lock = threading.Lock()

@@ -272,7 +272,8 @@ def test_euler_kahan_swept_equals_naive_and_oracle(oracle_lib, storage, nx, ny, 
 ])
 def test_persistent_form_gives_the_same_bits(oracle_lib, op, dtype, nx, ny, tile, nsteps):
     """One persistent launch per advance (work items with neighbourhood waits)
-    equals the naive path bit for bit, also through a captured graph."""
+    equals the naive path bit for bit, with panels staged by TMA and copied
+    element-wise, also through a captured graph."""
     rng = np.random.default_rng(nx + ny + tile)
     nv = {"hash": 1, "heat": 1, "heat_kahan": 2, "wide2": 5, "wave": 2, "euler_rk2": 8,
           "euler_kahan": 12}[op]
@@ -292,13 +293,19 @@ def test_persistent_form_gives_the_same_bits(oracle_lib, op, dtype, nx, ny, tile
         u0 = rng.random((nv, ny, nx))
     naive = run(op, u0, nsteps, tile, "naive", params, dtype=dtype)
     stream = torch.cuda.Stream()
-    with Swept2D(nx, ny, op=op, tile=tile, params=params, dtype=dtype, stream=stream) as s:
-        s.set_state(np.ascontiguousarray(u0))
-        s.advance(nsteps, mode="persistent")
-        assert np.array_equal(s.get_state(), naive)
-        s.set_state(np.ascontiguousarray(u0))
-        s.advance(nsteps, mode="persistent", graph=True)
-        assert np.array_equal(s.get_state(), naive)
+    from paper_1602_07558_gb300.swept2d import SweptError
+    for stage in (False, True):
+        with Swept2D(nx, ny, op=op, tile=tile, params=params, dtype=dtype, stream=stream) as s:
+            try:
+                s.set_tuning(128 if stage else 256, stage)
+            except SweptError:
+                continue                    # the staged panels do not fit at this tile
+            s.set_state(np.ascontiguousarray(u0))
+            s.advance(nsteps, mode="persistent")
+            assert np.array_equal(s.get_state(), naive), stage
+            s.set_state(np.ascontiguousarray(u0))
+            s.advance(nsteps, mode="persistent", graph=True)
+            assert np.array_equal(s.get_state(), naive), stage
 
 
 def test_persistent_wait_timeout_is_reported_and_the_context_stays_usable(oracle_lib):
