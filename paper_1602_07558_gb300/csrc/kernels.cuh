@@ -442,28 +442,25 @@ __device__ __forceinline__ void up_panel_xy(int side, int n, int k, int d, int p
 }
 
 // Write level k of the 4 up panels of the tile held in cur to slot `slot`.
+// The block's threads take the level's 4 sides x 2 lines x L elements in
+// order (element e: line e div L, position e mod L), so short lines at deep
+// levels or small tiles do not leave most lanes idle.
 template <class S, int NV>
 __device__ __forceinline__ void write_up_panels(const S *cur, int P, const Geom &G, int k,
                                                 S *up, int slot) {
     const int n = G.n, L = n - 2 * k, plane = P * P;
     const int off = 2 * k * (n - k + 1);
-    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int line = threadIdx.x >> 5; line < 8; line += nw) {   // 4 sides x 2 lines
-        const int side = line >> 1, d = line & 1;
-        S *dst = up + ((size_t)slot * 4 + side) * NV * G.PS + off + d * L;
-        // buffer index of element p: base + p * step (up_panel_xy, plus the halo)
-        int a0, b0, a1, b1;
-        up_panel_xy(side, n, k, d, 0, a0, b0);
-        up_panel_xy(side, n, k, d, 1, a1, b1);
-        const int base = (b0 + 1) * P + (a0 + 1), step = (b1 - b0) * P + (a1 - a0);
-        S *dv[NV];
+    const float rl = recip_small(L);
+    S *tile = up + (size_t)slot * 4 * NV * G.PS + off;
+    for (int e = threadIdx.x; e < 8 * L; e += blockDim.x) {
+        const int q = div_small(e, rl);          // side * 2 + line
+        const int p = e - q * L, side = q >> 1, d = q & 1;
+        int a, b;
+        up_panel_xy(side, n, k, d, p, a, b);
+        const S *src = cur + (b + 1) * P + (a + 1);
+        S *dst = tile + side * NV * G.PS + d * L + p;
 #pragma unroll
-        for (int v = 0; v < NV; ++v) dv[v] = dst + (size_t)v * G.PS;
-        for (int p = lane; p < L; p += 32) {
-            const S *src = cur + base + p * step;
-#pragma unroll
-            for (int v = 0; v < NV; ++v) dv[v][p] = src[v * plane];
-        }
+        for (int v = 0; v < NV; ++v) dst[v * G.PS] = src[v * plane];
     }
 }
 
@@ -650,26 +647,25 @@ __device__ __forceinline__ void bridge_tile(const Op &op, const Geom &G, const t
         if (threadIdx.x == 0) mbar_inval(bar);   // the block may stage again (persistent form)
         stg = st;
     }
-    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     auto load_strips = [&](int k, S *dst) {
         const int L = n - 2 * k;
         const int off = 2 * k * (n - k + 1);
-        for (int line = threadIdx.x >> 5; line < 4; line += nw) {   // 2 strips x 2 lines
-            const int which = line >> 1, d = line & 1;
+        const float rl = recip_small(L);
+        for (int e = threadIdx.x; e < 4 * L; e += blockDim.x) {   // 2 strips x 2 lines x L
+            const int q = div_small(e, rl);
+            const int p = e - q * L, which = q >> 1, d = q & 1;
             const int ww = which ? h + k + d : h - 1 - k - d;
-            for (int p = lane; p < L; p += 32) {
-                const int uu = k + p;
-                const int x = xb ? ww : uu, y = xb ? uu : ww;
-                S *dd = dst + (y + 1) * P + (x + 1);
-                if constexpr (STG) {
-                    const S *src = stg + which * NV * G.PS + off + d * L + p;
+            const int uu = k + p;
+            const int x = xb ? ww : uu, y = xb ? uu : ww;
+            S *dd = dst + (y + 1) * P + (x + 1);
+            if constexpr (STG) {
+                const S *src = stg + which * NV * G.PS + off + d * L + p;
 #pragma unroll
-                    for (int v = 0; v < NV; ++v) dd[v * plane] = src[v * G.PS];
-                } else {
-                    const S *src = seg[which] + off + d * L + p;
+                for (int v = 0; v < NV; ++v) dd[v * plane] = src[v * G.PS];
+            } else {
+                const S *src = seg[which] + off + d * L + p;
 #pragma unroll
-                    for (int v = 0; v < NV; ++v) async_copy(dd + v * plane, src + (size_t)v * G.PS);
-                }
+                for (int v = 0; v < NV; ++v) async_copy(dd + v * plane, src + (size_t)v * G.PS);
             }
         }
         if constexpr (!STG) async_commit();
@@ -688,22 +684,22 @@ __device__ __forceinline__ void bridge_tile(const Op &op, const Geom &G, const t
     for (int k = 0; k < h; ++k) {
         S *cur = bufs[k & 1];
         S *nxt = bufs[(k + 1) & 1];
-        // bridge panels of level k
+        // bridge panels of level k (2 sides x 2 lines x L, threads in order)
         {
             const int L = 2 * k + 2;
             const int off = 2 * k * (k + 1);
-            for (int line = threadIdx.x >> 5; line < 4; line += nw) {   // 2 sides x 2 lines
-                const int which = line >> 1, d = line & 1;
+            const float rl = recip_small(L);
+            for (int e = threadIdx.x; e < 4 * L; e += blockDim.x) {
+                const int q = div_small(e, rl);
+                const int p = e - q * L, which = q >> 1, d = q & 1;
                 const int uu = which ? n - 1 - k - d : k + d;
-                const int w0 = h - k + (which ? hi_w_shift : lo_w_shift);
-                S *dst = br + ((size_t)slot * 4 + (which ? out_hi : out_lo)) * NV * G.PS + off + d * L;
-                for (int p = lane; p < L; p += 32) {
-                    const int ww = w0 + p;
-                    const int x = xb ? ww : uu, y = xb ? uu : ww;
+                const int ww = h - k + (which ? hi_w_shift : lo_w_shift) + p;
+                const int x = xb ? ww : uu, y = xb ? uu : ww;
+                S *dst = br + ((size_t)slot * 4 + (which ? out_hi : out_lo)) * NV * G.PS + off +
+                         d * L + p;
+                const S *src = cur + (y + 1) * P + (x + 1);
 #pragma unroll
-                    for (int v = 0; v < NV; ++v)
-                        dst[(size_t)v * G.PS + p] = cur[v * plane + (y + 1) * P + (x + 1)];
-                }
+                for (int v = 0; v < NV; ++v) dst[(size_t)v * G.PS] = src[v * plane];
             }
         }
         if (k + 1 < h) {
@@ -761,12 +757,13 @@ __device__ __forceinline__ bool down_body(const Op &op, const Geom &G, unsigned 
         if (threadIdx.x == 0) mbar_inval(bar);
         stg = st;
     }
-    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     auto load_ring = [&](int k, S *dst) {
         const int L = 2 * k + 2;
         const int off = 2 * k * (k + 1);
-        for (int line = threadIdx.x >> 5; line < 8; line += nw) {   // 4 sides x 2 lines
-            const int side = line >> 1, d = line & 1;
+        const float rl = recip_small(L);
+        for (int e = threadIdx.x; e < 8 * L; e += blockDim.x) {   // 4 sides x 2 lines x L
+            const int q = div_small(e, rl);
+            const int p = e - q * L, side = q >> 1, d = q & 1;
             // (x, y) of element p: x = bx + p ax, y = by + p ay
             int bx, by, ax, ay;
             switch (side) {
@@ -775,19 +772,15 @@ __device__ __forceinline__ bool down_body(const Op &op, const Geom &G, unsigned 
                 case 2: bx = h - k; by = h - 1 - k - d; ax = 1; ay = 0; break;       // north
                 default: bx = h - k - 2; by = h + k + d; ax = 1; ay = 0; break;      // south
             }
-            S *dbase = dst + (by + 1) * P + (bx + 1);
-            const int step = ay * P + ax;
-            for (int p = lane; p < L; p += 32) {
-                S *dd = dbase + p * step;
-                if constexpr (STG) {
-                    const S *src = stg + side * NV * G.PS + off + d * L + p;
+            S *dd = dst + (by + 1 + p * ay) * P + (bx + 1 + p * ax);
+            if constexpr (STG) {
+                const S *src = stg + side * NV * G.PS + off + d * L + p;
 #pragma unroll
-                    for (int v = 0; v < NV; ++v) dd[v * plane] = src[v * G.PS];
-                } else {
-                    const S *src = seg[side] + off + d * L + p;
+                for (int v = 0; v < NV; ++v) dd[v * plane] = src[v * G.PS];
+            } else {
+                const S *src = seg[side] + off + d * L + p;
 #pragma unroll
-                    for (int v = 0; v < NV; ++v) async_copy(dd + v * plane, src + (size_t)v * G.PS);
-                }
+                for (int v = 0; v < NV; ++v) async_copy(dd + v * plane, src + (size_t)v * G.PS);
             }
         }
         if constexpr (!STG) async_commit();
