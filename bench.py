@@ -692,14 +692,15 @@ def run_batch(args, w, world, rank, local):
                         dtype=w.dtype) as sb:
             for tile_n, (thr, stg) in class_tuning.items():
                 sb.set_tuning(thr, stg, tile=tile_n)
-            ms_sw, launches = timed(sb, "swept", args.steps, max(1, args.warmup // 3))
+            sw_mode = "persistent" if args.persistent else "swept"
+            ms_sw, launches = timed(sb, sw_mode, args.steps, max(1, args.warmup // 3))
             out_sw = sb.get_state()
             h_in = torch.from_numpy(flat.copy()).pin_memory()
             h_out = torch.empty_like(h_in).pin_memory()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             sb.set_state(h_in)
-            sb.advance(nsteps, graph=True)
+            sb.advance(nsteps, mode=sw_mode, graph=True)
             sb.get_state(h_out)
             e2e_s = time.perf_counter() - t0
         naive_ms = None
@@ -762,7 +763,7 @@ def run_batch(args, w, world, rank, local):
             "warmup": max(1, args.warmup // 3), "ms_per_step": ms_sw, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": w.dtype, "data": "synthetic",
             "config": {"workload": w.describe, "grids": count, "cells": cells,
-                       "tiles_chosen": class_counts, "class_tuning (threads, stage)": stage,
+                       "tiles_chosen": class_counts, "persistent": bool(args.persistent), "class_tuning (threads, stage)": stage,
                        "autotune": tune_table,
                        "cuda_graph": True, "l2": "flushed (256 MB write) between timed steps"},
             "naive_batched": {"value": naive_value, "unit": UNIT, "ms_per_step": naive_ms,

@@ -235,7 +235,10 @@ int swept2d_measure_fp64_rate(void *stream, double *ops_per_s);
  *               HEAT_KAHAN (F32, BF16), HASH (U64)
  * State layout: the grids' states concatenated in grid order, each nvars planes
  * of ny[i] x nx[i]. Modes: SWEPT2D_SWEPT or SWEPT2D_NAIVE, optionally OR-ed with
- * SWEPT2D_GRAPH (not for HASH). Every call returns a status; messages through
+ * SWEPT2D_GRAPH (not for HASH); SWEPT2D_SWEPT may also be OR-ed with
+ * SWEPT2D_PERSISTENT (one persistent launch per tile class runs all of the
+ * class's half cycles, waiting per grid on each tile's 3 x 3 neighbourhood).
+ * Every call returns a status; messages through
  * swept2d_batch_last_error (NULL batch: the last failed create on this thread).
  */
 typedef struct swept2d_batch swept2d_batch_t;

@@ -64,6 +64,34 @@ __global__ void __launch_bounds__(256) batch_down_kernel(Op op, const GridDesc *
     down_tile<Op, STG>(op, gd.G, br + gd.panel_off, state + gd.state_off, o, g0, err, I, J);
 }
 
+// Persistent form over every tile of a class: the tile table lists each
+// grid's tiles consecutively, so a grid's phase counters start at the table
+// index of its tile 0.
+struct GridTiles {
+    const GridDesc *grids;
+    const int2 *tiles;
+    __device__ __forceinline__ TileAt operator()(int t) const {
+        const int2 e = tiles[t];
+        const GridDesc gd = grids[e.x];
+        TileAt w;
+        w.G = gd.G;
+        w.soff = gd.state_off;
+        w.poff = gd.panel_off;
+        w.J = e.y / gd.G.T;
+        w.I = e.y - w.J * gd.G.T;
+        w.base = t - e.y;
+        return w;
+    }
+};
+
+template <class Op, bool STG>
+__global__ void __launch_bounds__(256) batch_persistent_kernel(
+    Op op, const GridDesc *grids, const int2 *tile_grid, int ntiles, int n, typename Op::S *state,
+    typename Op::S *up, typename Op::S *br, int *stage, int *queue, int H, u64 g0, int *err) {
+    persistent_loop<Op, STG>(op, GridTiles{grids, tile_grid}, ntiles, n, state, up, br, stage,
+                             queue, H, g0, err, 0, kPersistSpinLimit);
+}
+
 // One sub-step of every grid in a block table: block b covers a 32 x 8 patch of
 // its grid (the same per-point update as the single-grid naive kernel).
 template <class Op>
@@ -106,6 +134,11 @@ struct BatchTable {
     cudaError_t (*down)(const GridDesc *, const int2 *tile_grid, int ntiles, int n,
                         const double *c, const void *br, void *state, int o, u64 g0, int *err,
                         const Tuning &, cudaStream_t);
+    // all H half cycles of a class as one persistent launch; sched: ntiles
+    // phase counters followed by the queue counter, zeroed
+    cudaError_t (*persistent)(const GridDesc *, const int2 *tile_grid, int ntiles, int n,
+                              const double *c, void *state, void *up, void *br, int *sched, int H,
+                              u64 g0, int *err, const Tuning &, cudaStream_t);
 };
 
 template <class Op>
@@ -176,10 +209,39 @@ struct BatchLaunch {
         return tn.stage ? down_t<true>(d, tg, ntiles, n, c, br, state, o, g0, err, tn.threads, st)
                         : down_t<false>(d, tg, ntiles, n, c, br, state, o, g0, err, tn.threads, st);
     }
+    template <bool STG>
+    static cudaError_t persistent_t(const GridDesc *d, const int2 *tg, int ntiles, int n,
+                                    const double *c, void *state, void *upp, void *br, int *sched,
+                                    int H, u64 g0, int *err, int threads, cudaStream_t st) {
+        const size_t sm = down_smem<Op>(n, STG);
+        cudaError_t e = allow_smem(batch_persistent_kernel<Op, STG>, sm);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0, dev = 0, nsm = 0;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                 &per_sm, batch_persistent_kernel<Op, STG>, threads, sm)) != cudaSuccess)
+            return e;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        const long long nitems = (long long)ntiles * (2 * H + 1);
+        long long grid = (long long)(per_sm > 0 ? per_sm : 1) * nsm;
+        if (grid > nitems) grid = nitems;
+        batch_persistent_kernel<Op, STG><<<(int)grid, threads, sm, st>>>(
+            Op(c), d, tg, ntiles, n, (S *)state, (S *)upp, (S *)br, sched, sched + ntiles, H, g0,
+            err);
+        return cudaGetLastError();
+    }
+    static cudaError_t persistent(const GridDesc *d, const int2 *tg, int ntiles, int n,
+                                  const double *c, void *state, void *upp, void *br, int *sched,
+                                  int H, u64 g0, int *err, const Tuning &tn, cudaStream_t st) {
+        return tn.stage ? persistent_t<true>(d, tg, ntiles, n, c, state, upp, br, sched, H, g0, err,
+                                             tn.threads, st)
+                        : persistent_t<false>(d, tg, ntiles, n, c, state, upp, br, sched, H, g0,
+                                              err, tn.threads, st);
+    }
     static const BatchTable *table() {
         static const BatchTable t = {Op::NV, Op::NST, (int)sizeof(S), Op::STAGE,
                                      &swept_smem_for<Op>, &naive, &up, &bridge, &octahedron,
-                                     &down};
+                                     &down, &persistent};
         return &t;
     }
 };

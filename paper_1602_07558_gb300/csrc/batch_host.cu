@@ -31,6 +31,7 @@ struct BatchClass {
     std::vector<int2> tiles;   // (grid, tile) for the swept launches
     std::vector<int2> blocks;  // (grid, 32x8 block) for the naive tail
     int2 *d_tiles = nullptr, *d_blocks = nullptr;
+    int *d_sched = nullptr;    // persistent form: phase counters + queue counter
 };
 
 struct BatchGraph {
@@ -90,6 +91,7 @@ void batch_free(swept2d_batch *b) {
     for (auto &c : b->classes) {
         if (c.d_tiles) cudaFree(c.d_tiles);
         if (c.d_blocks) cudaFree(c.d_blocks);
+        if (c.d_sched) cudaFree(c.d_sched);
     }
     for (void *p : {(void *)b->d_grids, (void *)b->d_all_blocks, b->state, b->state2, b->up, b->br,
                     (void *)b->errword})
@@ -124,6 +126,8 @@ int batch_naive(swept2d_batch *b, const int2 *d_blocks, int nblocks, long long c
 }
 
 int batch_run(swept2d_batch *b, long long total, int mode) {
+    const bool persistent = (mode & SWEPT2D_PERSISTENT) != 0;
+    mode &= ~SWEPT2D_PERSISTENT;
     const u64 g_start = (u64)b->substeps;
     if (mode == SWEPT2D_NAIVE) {
         void *cur = b->state, *other = b->state2;
@@ -143,7 +147,16 @@ int batch_run(swept2d_batch *b, long long total, int mode) {
             rem = total - H * half;
         }
         const int nt = (int)c.tiles.size();
-        if (H > 0) {
+        if (H > 0 && persistent) {
+            cudaError_t e = cudaMemsetAsync(c.d_sched, 0, ((size_t)nt + 1) * sizeof(int), b->stream);
+            if (e != cudaSuccess) return bcuda(b, e, "persistent schedule reset");
+            int rc = blaunch(b, "batched persistent kernel", [&] {
+                return b->bt->persistent(b->d_grids, c.d_tiles, nt, c.n, b->consts, b->state,
+                                         b->up, b->br, c.d_sched, (int)H, g_start, b->errword,
+                                         c.tune, b->stream);
+            });
+            if (rc) return rc;
+        } else if (H > 0) {
             const int half = c.n / 2;
             int rc = blaunch(b, "batched up kernel", [&] {
                 return b->bt->up(b->d_grids, c.d_tiles, nt, c.n, b->consts, b->state, b->up, 0,
@@ -370,8 +383,23 @@ int swept2d_batch_advance(swept2d_batch_t *b, long long nsteps, int mode) {
     if (nsteps < 0) return bfail(b, SWEPT2D_EINVAL, "advance: nsteps < 0");
     if (!b->has_state) return bfail(b, SWEPT2D_ESTATE, "advance: no state set");
     const bool graph = (mode & SWEPT2D_GRAPH) != 0;
-    mode &= ~SWEPT2D_GRAPH;
+    const int persistent = mode & SWEPT2D_PERSISTENT;
+    mode &= ~(SWEPT2D_GRAPH | SWEPT2D_PERSISTENT);
     if (mode != SWEPT2D_SWEPT && mode != SWEPT2D_NAIVE) return bfail(b, SWEPT2D_EINVAL, "advance: bad mode");
+    if (persistent) {
+        if (mode != SWEPT2D_SWEPT) return bfail(b, SWEPT2D_EINVAL, "advance: persistent needs the swept mode");
+        for (auto &c : b->classes) {
+            if (!c.n) continue;
+            const long long H = nsteps * b->bt->nst / (c.n / 2);
+            if ((long long)c.tiles.size() * (2 * H + 1) >= (1LL << 31))
+                return bfail(b, SWEPT2D_EINVAL, "advance: too many work items for one persistent launch");
+            if (!c.d_sched) {
+                cudaError_t e = cudaMalloc(&c.d_sched, (c.tiles.size() + 1) * sizeof(int));
+                if (e != cudaSuccess) return bcuda(b, e, "persistent schedule allocation");
+            }
+        }
+        mode |= persistent;
+    }
     if (graph) {
         if (!b->stream) return bfail(b, SWEPT2D_EINVAL, "advance: graph mode needs a created stream");
         if (b->op == SWEPT2D_OP_HASH)

@@ -903,16 +903,40 @@ __device__ __forceinline__ void st_release(int *p, int v) {
     asm volatile("st.release.gpu.global.s32 [%0], %1;\n" ::"l"(p), "r"(v) : "memory");
 }
 
-// `first` is the first work item taken (0; a positive value skips items, which
-// only the wait-timeout self-test does: the skipped items' phases are never
-// released, so every wait runs out).
-template <class Op, bool STG>
-__global__ void __launch_bounds__(256) persistent_kernel(Op op, Geom G, typename Op::S *state,
-                                                         typename Op::S *upp, typename Op::S *br,
-                                                         int *stage, int *queue, int H, u64 g0,
-                                                         int *err, int first, long long spin_limit) {
+// Where a work item's tile lives: its grid's geometry, the grid's offsets in
+// the (pooled) state and panel buffers, the tile's (I, J), and the index of the
+// grid's first tile among the launch's tiles (its phase counters start there).
+struct TileAt {
+    Geom G;
+    long long soff, poff;
+    int I, J, base;
+};
+
+// One grid: tile index t = J T + I.
+struct OneGrid {
+    Geom G;
+    __device__ __forceinline__ TileAt operator()(int t) const {
+        TileAt w;
+        w.G = G;
+        w.soff = w.poff = 0;
+        w.J = t / G.T;
+        w.I = t - w.J * G.T;
+        w.base = 0;
+        return w;
+    }
+};
+
+// The work loop of the persistent form over NT tiles (all of one tile side n)
+// located by `at`. `first` is the first work item taken (0; a positive value
+// skips items, which only the wait-timeout self-test does: the skipped items'
+// phases are never released, so every wait runs out).
+template <class Op, bool STG, class Loc>
+__device__ __forceinline__ void persistent_loop(const Op &op, const Loc &at, int NT, int n,
+                                                typename Op::S *state, typename Op::S *upp,
+                                                typename Op::S *br, int *stage, int *queue, int H,
+                                                u64 g0, int *err, int first, long long spin_limit) {
     __shared__ int s_item, s_fail;
-    const int NT = G.T * G.Q, h = G.n / 2;
+    const int h = n / 2;
     const int nitems = NT * (2 * H + 1);
     for (;;) {
         if (threadIdx.x == 0) {
@@ -924,7 +948,9 @@ __global__ void __launch_bounds__(256) persistent_kernel(Op op, Geom G, typename
         const int item = s_item;
         if (item >= nitems) return;
         const int p = item / NT + 1, t = item - (p - 1) * NT;
-        const int J = t / G.T, I = t - J * G.T;
+        const TileAt w = at(t);
+        const Geom &G = w.G;
+        const int I = w.I, J = w.J;
         if (p > 1 && threadIdx.x < 32) {
             // lanes 0..8 wait for one tile each of the periodic 3 x 3 neighbourhood
             bool bad = false;
@@ -932,7 +958,7 @@ __global__ void __launch_bounds__(256) persistent_kernel(Op op, Geom G, typename
                 const int dj = (int)threadIdx.x / 3 - 1, di = (int)threadIdx.x % 3 - 1;
                 const int jj = J + dj < 0 ? G.Q - 1 : (J + dj == G.Q ? 0 : J + dj);
                 const int ii = I + di < 0 ? G.T - 1 : (I + di == G.T ? 0 : I + di);
-                const int *flag = stage + jj * G.T + ii;
+                const int *flag = stage + w.base + jj * G.T + ii;
                 long long it = 0;
                 while (ld_acquire(flag) < p - 1) {
                     // give up after the bound, or at once when another block
@@ -954,20 +980,21 @@ __global__ void __launch_bounds__(256) persistent_kernel(Op op, Geom G, typename
         if (s_fail) return;
         // the acquired panels are read next by bulk copies (the async proxy)
         if (threadIdx.x == 0) asm volatile("fence.proxy.async.global;\n" ::: "memory");
+        typename Op::S *st = state + w.soff, *u = upp + w.poff, *b = br + w.poff;
         if (p == 1) {
-            up_tile(op, G, state, upp, 0, g0, I, J);
+            up_tile(op, G, st, u, 0, g0, I, J);
         } else {
             const int j = (p - 2) / 2;              // half cycle
             const u64 gj = g0 + (u64)j * h;
             const int o = (j & 1) ? h : 0;
             if ((p & 1) == 0) {                     // bridges of half cycle j
-                bridge_tile<Op, STG>(op, G, upp, br, gj, err, I, J, false);
+                bridge_tile<Op, STG>(op, G, u, b, gj, err, I, J, false);
                 __syncthreads();
-                bridge_tile<Op, STG>(op, G, upp, br, gj, err, I, J, true);
+                bridge_tile<Op, STG>(op, G, u, b, gj, err, I, J, true);
             } else if (j + 1 < H) {
-                octahedron_tile<Op, STG>(op, G, br, upp, o, gj, err, I, J);
+                octahedron_tile<Op, STG>(op, G, b, u, o, gj, err, I, J);
             } else {
-                down_tile<Op, STG>(op, G, br, state, o, gj, err, I, J);
+                down_tile<Op, STG>(op, G, b, st, o, gj, err, I, J);
             }
         }
         // make this item's panel (and state) stores visible, to the generic and
@@ -979,6 +1006,15 @@ __global__ void __launch_bounds__(256) persistent_kernel(Op op, Geom G, typename
         __syncthreads();
         if (threadIdx.x == 0) st_release(stage + t, p);
     }
+}
+
+template <class Op, bool STG>
+__global__ void __launch_bounds__(256) persistent_kernel(Op op, Geom G, typename Op::S *state,
+                                                         typename Op::S *upp, typename Op::S *br,
+                                                         int *stage, int *queue, int H, u64 g0,
+                                                         int *err, int first, long long spin_limit) {
+    persistent_loop<Op, STG>(op, OneGrid{G}, G.T * G.Q, G.n, state, upp, br, stage, queue, H, g0,
+                             err, first, spin_limit);
 }
 
 }  // namespace swept

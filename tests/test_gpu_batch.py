@@ -49,7 +49,7 @@ def _oracle(oracle_lib, op, dtype, s, nsteps):
 
 @pytest.mark.parametrize("op,dtype", [("heat", "f64"), ("hash", "u64"),
                                       ("heat_kahan", "f32"), ("heat_kahan", "bf16")])
-@pytest.mark.parametrize("mode", ["swept", "naive"])
+@pytest.mark.parametrize("mode", ["swept", "naive", "persistent"])
 def test_batch_equals_the_oracle_for_every_grid(oracle_lib, op, dtype, mode):
     nsteps = 37                           # odd tails for every class
     states = _states(op, dtype, seed=len(op) + len(mode))
@@ -77,6 +77,10 @@ def test_batch_graph_and_split_advances_match(op, dtype):
         for _ in range(3):
             b.advance(21, graph=True)
         got = b.split(b.get_state())
+        b.set_state(states)
+        for _ in range(3):
+            b.advance(21, mode="persistent", graph=True)
+        assert all(np.array_equal(x, y) for x, y in zip(got, b.split(b.get_state())))
     with SweptBatch([s[0] for s in SIZES], [s[1] for s in SIZES], [s[2] for s in SIZES],
                     **kw) as b:
         b.set_state(states)
@@ -94,10 +98,11 @@ def test_batch_tuning_gives_identical_bits():
     states = _states("heat_kahan", "f32", seed=3)
     outs = []
     for threads, stage in [(256, False), (128, True), (64, False)]:
-        with SweptBatch([s[0] for s in SIZES], [s[1] for s in SIZES], [s[2] for s in SIZES],
-                        op="heat_kahan", params=(0.2,), dtype="f32") as b:
-            b.set_tuning(threads, stage)
-            b.set_state(states)
-            b.advance(45)
-            outs.append(b.get_state())
+        for mode in ("swept", "persistent"):
+            with SweptBatch([s[0] for s in SIZES], [s[1] for s in SIZES], [s[2] for s in SIZES],
+                            op="heat_kahan", params=(0.2,), dtype="f32") as b:
+                b.set_tuning(threads, stage)
+                b.set_state(states)
+                b.advance(45, mode=mode)
+                outs.append(b.get_state())
     assert all(np.array_equal(outs[0], o) for o in outs[1:])
