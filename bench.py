@@ -321,6 +321,17 @@ def bridge_updates(n):
     return 2 * sum((n - 2 * k - 2) * (2 * k + 2) for k in range(h - 1))
 
 
+# DRAM traffic (read + write bytes) per tile of one octahedron launch, from one
+# ncu capture of the same kernel on a 2048 x 2048 grid (4096 tiles), scaled to a
+# launch by its number of tiles (reads equal the algorithmic panel bytes there;
+# part of the writes is still in L2 when the kernel ends). Kernels without a
+# capture of their current version report None.
+OCT_TRAFFIC_PER_TILE = {
+    ("heat", "f64", 32): (71.499264e6 + 29.265152e6) / 4096,
+    ("euler_kahan", "f32", 32): (427.88352e6 + 380.93696e6) / 4096,
+}
+
+
 def roofline(w: Workload, kern, fp64_rate, esize, nvars):
     """Roofline of the dominant swept kernel (the octahedron): the slower of the
     FP64-pipe bound and the HBM bound on its algorithmic work per launch."""
@@ -331,9 +342,14 @@ def roofline(w: Workload, kern, fp64_rate, esize, nvars):
     upd = octahedron_updates(n) * tiles            # point updates (sub-steps) per launch
     hbm_bytes = 2 * 4 * (n * n // 2 + n) * nvars * esize * tiles
     total_ms = sum(v[1] for v in kern.values())
+    per_tile = OCT_TRAFFIC_PER_TILE.get((w.op, w.dtype, n))
     out = {"kernel": "octahedron", "avg_launch_ms": avg_ms, "updates_per_launch": upd,
            "hbm_bytes_per_launch": hbm_bytes,
-           "share_of_kernel_time": ms / total_ms if total_ms else None, "traffic": None}
+           "share_of_kernel_time": ms / total_ms if total_ms else None,
+           "traffic": per_tile * tiles if per_tile else None,
+           "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the same "
+                              "kernel at 2048x2048 (4096 tiles), scaled by tiles")
+           if per_tile else None}
     t_hbm = hbm_bytes / (HBM_PEAK_GBPS * 1e9)
     if w.fp64_ops:
         t_alu = w.fp64_ops * upd / fp64_rate

@@ -194,11 +194,13 @@ const char *swept2d_last_error(const swept2d_t *h);
 int swept2d_query(const swept2d_t *h, int what, double *out);
 
 /* Launch shape of the swept kernels of a handle (a tuning knob, not a change
- * of results: every setting gives the same bits). threads: 64, 128 or 256 per
- * block (default 256). stage: 1 = the bridge and downward-pyramid blocks bring
- * their whole input panel set into shared memory with TMA bulk copies at block
- * start; 0 = they prefetch each level's strip with cp.async (default: 1 for
- * HEAT_KAHAN, 0 otherwise, and 0 wherever the staged panels do not fit).
+ * of results: every setting gives the same bits). threads: 64, 128, 256 or 512
+ * per block (default 256; the persistent form takes at most 256). stage: 1 =
+ * the bridge and downward-pyramid blocks bring their whole input panel set
+ * into shared memory with TMA bulk copies at block start; 0 = they copy every
+ * level's strip or ring from device memory straight into its level buffer with
+ * cp.async at block start (default: 1 for HEAT_KAHAN with BF16 storage, 0
+ * otherwise, and 0 wherever the staged panels do not fit).
  * Errors: EINVAL (bad value, naive-only handle, does not fit). */
 int swept2d_set_tuning(swept2d_t *h, int threads, int stage);
 

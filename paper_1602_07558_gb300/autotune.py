@@ -17,7 +17,7 @@ from __future__ import annotations
 from .swept2d import Swept2D, SweptError
 
 
-def candidates(nx, ny, tiles=(16, 32, 64), threads=(64, 128, 256), stages=(False, True)):
+def candidates(nx, ny, tiles=(16, 32, 64), threads=(64, 128, 256, 512), stages=(False, True)):
     for n in tiles:
         if nx % n == 0 and ny % n == 0:
             for t in threads:
@@ -26,7 +26,7 @@ def candidates(nx, ny, tiles=(16, 32, 64), threads=(64, 128, 256), stages=(False
 
 
 def autotune(nx, ny, op, params, dtype=None, state=None, stream=None, probe_steps=None,
-             tiles=(16, 32, 64), threads=(64, 128, 256), stages=(False, True)):
+             tiles=(16, 32, 64), threads=(64, 128, 256, 512), stages=(False, True)):
     """Returns ((tile, threads, stage), table) with table a list of
     {"tile", "threads", "stage", "ms", "gcell_per_s"} for every candidate that ran."""
     import torch

@@ -18,7 +18,7 @@ struct GridDesc {
 // Tile and block tables hold (grid index, tile or block index within the grid).
 
 template <class Op>
-__global__ void __launch_bounds__(256) batch_up_kernel(Op op, const GridDesc *grids,
+__global__ void __launch_bounds__(kMaxSweptThreads) batch_up_kernel(Op op, const GridDesc *grids,
                                                        const int2 *tile_grid,
                                                        const typename Op::S *state,
                                                        typename Op::S *up, int o, u64 g0) {
@@ -29,7 +29,7 @@ __global__ void __launch_bounds__(256) batch_up_kernel(Op op, const GridDesc *gr
 }
 
 template <class Op, bool STG>
-__global__ void __launch_bounds__(256) batch_bridge_kernel(Op op, const GridDesc *grids,
+__global__ void __launch_bounds__(kMaxSweptThreads) batch_bridge_kernel(Op op, const GridDesc *grids,
                                                            const int2 *tile_grid,
                                                            const typename Op::S *up,
                                                            typename Op::S *br, u64 g0, int *err) {
@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(256) batch_bridge_kernel(Op op, const GridDesc
 }
 
 template <class Op, bool STG>
-__global__ void __launch_bounds__(256) batch_octahedron_kernel(Op op, const GridDesc *grids,
+__global__ void __launch_bounds__(kMaxSweptThreads) batch_octahedron_kernel(Op op, const GridDesc *grids,
                                                                const int2 *tile_grid,
                                                                const typename Op::S *br,
                                                                typename Op::S *up, int o, u64 g0,
@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(256) batch_octahedron_kernel(Op op, const Grid
 }
 
 template <class Op, bool STG>
-__global__ void __launch_bounds__(256) batch_down_kernel(Op op, const GridDesc *grids,
+__global__ void __launch_bounds__(kMaxSweptThreads) batch_down_kernel(Op op, const GridDesc *grids,
                                                          const int2 *tile_grid,
                                                          const typename Op::S *br,
                                                          typename Op::S *state, int o, u64 g0,

@@ -390,6 +390,8 @@ int swept2d_batch_advance(swept2d_batch_t *b, long long nsteps, int mode) {
         if (mode != SWEPT2D_SWEPT) return bfail(b, SWEPT2D_EINVAL, "advance: persistent needs the swept mode");
         for (auto &c : b->classes) {
             if (!c.n) continue;
+            if (c.tune.threads > 256)
+                return bfail(b, SWEPT2D_EINVAL, "advance: the persistent form takes at most 256 threads");
             const long long H = nsteps * b->bt->nst / (c.n / 2);
             if ((long long)c.tiles.size() * (2 * H + 1) >= (1LL << 31))
                 return bfail(b, SWEPT2D_EINVAL, "advance: too many work items for one persistent launch");
@@ -427,8 +429,8 @@ int swept2d_batch_get_state(swept2d_batch_t *b, void *dst, int dst_is_device) {
 
 int swept2d_batch_set_tuning(swept2d_batch_t *b, int threads, int stage) {
     if (!b) return SWEPT2D_EINVAL;
-    if (threads != 64 && threads != 128 && threads != 256)
-        return bfail(b, SWEPT2D_EINVAL, "set_tuning: threads must be 64, 128 or 256");
+    if (threads != 64 && threads != 128 && threads != 256 && threads != 512)
+        return bfail(b, SWEPT2D_EINVAL, "set_tuning: threads must be 64, 128, 256 or 512");
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
@@ -444,8 +446,8 @@ int swept2d_batch_set_tuning(swept2d_batch_t *b, int threads, int stage) {
 
 int swept2d_batch_set_class_tuning(swept2d_batch_t *b, int tile, int threads, int stage) {
     if (!b) return SWEPT2D_EINVAL;
-    if (threads != 64 && threads != 128 && threads != 256)
-        return bfail(b, SWEPT2D_EINVAL, "set_class_tuning: threads must be 64, 128 or 256");
+    if (threads != 64 && threads != 128 && threads != 256 && threads != 512)
+        return bfail(b, SWEPT2D_EINVAL, "set_class_tuning: threads must be 64, 128, 256 or 512");
     for (auto &c : b->classes) {
         if (c.n != tile || tile == 0) continue;
         int dev = 0, optin = 0;

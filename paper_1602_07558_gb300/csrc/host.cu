@@ -481,6 +481,8 @@ int swept2d_selftest_wait_timeout(swept2d_t *h, long long spin_limit) {
     if (!h) return SWEPT2D_EINVAL;
     if (h->n == 0) return fail(h, SWEPT2D_EINVAL, "selftest: needs a handle created with a tile");
     if (spin_limit < 1) return fail(h, SWEPT2D_EINVAL, "selftest: spin_limit < 1");
+    if (h->tune.threads > 256)
+        return fail(h, SWEPT2D_EINVAL, "selftest: the persistent form takes at most 256 threads");
     int rc = persistent_prepare(h, 1);
     if (rc) return rc;
     const int NT = h->G.T * h->G.Q;
@@ -517,6 +519,8 @@ int swept2d_advance(swept2d_t *h, long long nsteps, int mode) {
         return fail(h, SWEPT2D_EINVAL, "advance: swept mode needs a tile (created with tile 0)");
     if (persistent) {
         if (mode != SWEPT2D_SWEPT) return fail(h, SWEPT2D_EINVAL, "advance: persistent needs the swept mode");
+        if (h->tune.threads > 256)
+            return fail(h, SWEPT2D_EINVAL, "advance: the persistent form takes at most 256 threads");
         const int rc = persistent_prepare(h, nsteps * h->nst / (h->n / 2));
         if (rc) return rc;
         mode |= persistent;
@@ -579,8 +583,8 @@ int swept2d_query(const swept2d_t *h, int what, double *out) {
 
 int swept2d_set_tuning(swept2d_t *h, int threads, int stage) {
     if (!h) return SWEPT2D_EINVAL;
-    if (threads != 64 && threads != 128 && threads != 256)
-        return fail(h, SWEPT2D_EINVAL, "set_tuning: threads must be 64, 128 or 256");
+    if (threads != 64 && threads != 128 && threads != 256 && threads != 512)
+        return fail(h, SWEPT2D_EINVAL, "set_tuning: threads must be 64, 128, 256 or 512");
     if (h->n == 0) return fail(h, SWEPT2D_EINVAL, "set_tuning: naive-only handle");
     const size_t sm = h->ops->smem_for(h->n, stage != 0);
     int dev = 0, optin = 0;

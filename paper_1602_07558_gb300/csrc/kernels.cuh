@@ -97,6 +97,11 @@ __device__ __forceinline__ void async_wait() {
 // the error word (if any) and gives up instead of hanging.
 constexpr long long kSpinLimit = 1LL << 22;
 
+// Largest block of the launch-per-phase swept kernels (their register use stays
+// far below the 128 a 512-thread block leaves each thread); the naive and the
+// persistent kernels take at most 256.
+constexpr int kMaxSweptThreads = 512;
+
 __device__ __forceinline__ unsigned smem_u32(const void *p) {
     return (unsigned)__cvta_generic_to_shared(p);
 }
@@ -591,7 +596,7 @@ __device__ __forceinline__ void up_tile(const Op &op, const Geom &G, const typen
 }
 
 template <class Op>
-__global__ void __launch_bounds__(256) up_kernel(Op op, Geom G, const typename Op::S *state,
+__global__ void __launch_bounds__(kMaxSweptThreads) up_kernel(Op op, Geom G, const typename Op::S *state,
                                                  typename Op::S *up, int o, u64 g0) {
     up_tile(op, G, state, up, o, g0, blockIdx.x, blockIdx.y);
 }
@@ -716,7 +721,7 @@ __device__ __forceinline__ void bridge_tile(const Op &op, const Geom &G, const t
 }
 
 template <class Op, bool STG>
-__global__ void __launch_bounds__(256) bridge_kernel(Op op, Geom G, const typename Op::S *up,
+__global__ void __launch_bounds__(kMaxSweptThreads) bridge_kernel(Op op, Geom G, const typename Op::S *up,
                                                      typename Op::S *br, u64 g0, int *err) {
     bridge_tile<Op, STG>(op, G, up, br, g0, err, blockIdx.x, blockIdx.y, blockIdx.z == 1);
 }
@@ -831,7 +836,7 @@ __device__ __forceinline__ void octahedron_tile(const Op &op, const Geom &G,
 }
 
 template <class Op, bool STG>
-__global__ void __launch_bounds__(256) octahedron_kernel(Op op, Geom G, const typename Op::S *br,
+__global__ void __launch_bounds__(kMaxSweptThreads) octahedron_kernel(Op op, Geom G, const typename Op::S *br,
                                                          typename Op::S *up, int o, u64 g0,
                                                          int *err) {
     octahedron_tile<Op, STG>(op, G, br, up, o, g0, err, blockIdx.x, blockIdx.y);
@@ -863,7 +868,7 @@ __device__ __forceinline__ void down_tile(const Op &op, const Geom &G, const typ
 }
 
 template <class Op, bool STG>
-__global__ void __launch_bounds__(256) down_kernel(Op op, Geom G, const typename Op::S *br,
+__global__ void __launch_bounds__(kMaxSweptThreads) down_kernel(Op op, Geom G, const typename Op::S *br,
                                                    typename Op::S *state, int o, u64 g0, int *err) {
     down_tile<Op, STG>(op, G, br, state, o, g0, err, blockIdx.x, blockIdx.y);
 }

@@ -185,16 +185,19 @@ def test_heat_kahan_2048_full_grid_matches_oracle(oracle_lib, storage):
 
 @pytest.mark.parametrize("op,dtype,params", [
     ("heat", "f64", (0.2,)), ("heat_kahan", "f32", (0.2,)), ("heat_kahan", "bf16", (0.2,)),
-    ("hash", "u64", ()), ("wide2", "u64", ()),
+    ("hash", "u64", ()), ("wide2", "u64", ()), ("euler_kahan", "f32", (GAMMA, CFL, KAPPA)),
 ])
-@pytest.mark.parametrize("threads,stage", [(64, False), (128, True), (256, True), (256, False)])
+@pytest.mark.parametrize("threads,stage", [(64, False), (128, True), (256, True), (256, False),
+                                           (512, False), (512, True)])
 def test_tuning_gives_identical_bits(op, dtype, params, threads, stage):
     """Threads per block and TMA panel staging change the schedule, never the
     result: every setting equals the naive path bit for bit."""
     nx, ny, tile, nsteps = 64, 48, 16, 37
     rng = np.random.default_rng(threads + stage)
-    shape = {"heat": 1, "heat_kahan": 2, "hash": 1, "wide2": 5}[op]
-    if dtype == "f64":
+    shape = {"heat": 1, "heat_kahan": 2, "hash": 1, "wide2": 5, "euler_kahan": 12}[op]
+    if op == "euler_kahan":
+        u0 = _euler_kahan_state(nx, ny, dtype, seed=threads + stage)
+    elif dtype == "f64":
         u0 = rng.random((shape, ny, nx))
     elif dtype == "f32":
         u0 = np.stack([rng.random((ny, nx)), np.zeros((ny, nx))]).astype(np.float32)
