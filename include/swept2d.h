@@ -234,7 +234,10 @@ int swept2d_measure_fp64_rate(void *stream, double *ops_per_s);
  *   tile[i]     tile side of grid i (even, >= 4, dividing nx[i] and ny[i]), or 0
  *               for a grid that only takes naive steps
  *   op, params, dtype, stream   as for swept2d_create; supported: HEAT (F64),
- *               HEAT_KAHAN (F32, BF16), HASH (U64)
+ *               HEAT_KAHAN (F32, BF16), HASH (U64), EULER_RK2 (F64), EULER_KAHAN
+ *               (F32, BF16); for the Euler updates each grid's wave speed a and
+ *               time step dt come from its own state at set_state, its spacing
+ *               is lx / nx[i], ly / ny[i]
  * State layout: the grids' states concatenated in grid order, each nvars planes
  * of ny[i] x nx[i]. Modes: SWEPT2D_SWEPT or SWEPT2D_NAIVE, optionally OR-ed with
  * SWEPT2D_GRAPH (not for HASH); SWEPT2D_SWEPT may also be OR-ed with
@@ -257,6 +260,10 @@ int swept2d_batch_set_class_tuning(swept2d_batch_t *b, int tile, int threads, in
 int swept2d_batch_destroy(swept2d_batch_t *b);
 const char *swept2d_batch_last_error(const swept2d_batch_t *b);
 int swept2d_batch_query(const swept2d_batch_t *b, int what, double *out);
+/* Per-grid values: SWEPT2D_Q_DT and SWEPT2D_Q_WAVESPEED (Euler updates, fixed at
+ * set_state; 0 otherwise) and SWEPT2D_Q_CELLS of grid `grid` (0-based).
+ * Errors: EINVAL (bad handle, grid or query). */
+int swept2d_batch_query_grid(const swept2d_batch_t *b, int grid, int what, double *out);
 
 /*
  * Allocation-free swept advance of the heat equation (FP64). The paper has no

@@ -14,54 +14,56 @@ struct GridDesc {
     Geom G;                 // the grid's geometry (tile side n of its class)
     long long state_off;    // first element of the grid's state in the pooled state
     long long panel_off;    // first element of the grid's panel slots in each pool
+    double c[8];            // the point update's constants for this grid (Euler's
+                            // depend on the grid's own state and spacing)
 };
 // Tile and block tables hold (grid index, tile or block index within the grid).
 
 template <class Op>
-__global__ void __launch_bounds__(kMaxSweptThreads) batch_up_kernel(Op op, const GridDesc *grids,
-                                                       const int2 *tile_grid,
-                                                       const typename Op::S *state,
-                                                       typename Op::S *up, int o, u64 g0) {
+__global__ void __launch_bounds__(kMaxSweptThreads) batch_up_kernel(const GridDesc *grids,
+                                                                    const int2 *tile_grid,
+                                                                    const typename Op::S *state,
+                                                                    typename Op::S *up, int o,
+                                                                    u64 g0) {
     const int2 e = tile_grid[blockIdx.x];
     const GridDesc gd = grids[e.x];
     const int J = e.y / gd.G.T, I = e.y - J * gd.G.T;
-    up_tile(op, gd.G, state + gd.state_off, up + gd.panel_off, o, g0, I, J);
+    up_tile(Op(gd.c), gd.G, state + gd.state_off, up + gd.panel_off, o, g0, I, J);
 }
 
 template <class Op, bool STG>
-__global__ void __launch_bounds__(kMaxSweptThreads) batch_bridge_kernel(Op op, const GridDesc *grids,
-                                                           const int2 *tile_grid,
-                                                           const typename Op::S *up,
-                                                           typename Op::S *br, u64 g0, int *err) {
+__global__ void __launch_bounds__(kMaxSweptThreads) batch_bridge_kernel(const GridDesc *grids,
+                                                                        const int2 *tile_grid,
+                                                                        const typename Op::S *up,
+                                                                        typename Op::S *br, u64 g0,
+                                                                        int *err) {
     const int2 e = tile_grid[blockIdx.x];
     const GridDesc gd = grids[e.x];
     const int J = e.y / gd.G.T, I = e.y - J * gd.G.T;
-    bridge_tile<Op, STG>(op, gd.G, up + gd.panel_off, br + gd.panel_off, g0, err, I, J,
+    bridge_tile<Op, STG>(Op(gd.c), gd.G, up + gd.panel_off, br + gd.panel_off, g0, err, I, J,
                          blockIdx.y == 1);
 }
 
 template <class Op, bool STG>
-__global__ void __launch_bounds__(kMaxSweptThreads) batch_octahedron_kernel(Op op, const GridDesc *grids,
-                                                               const int2 *tile_grid,
-                                                               const typename Op::S *br,
-                                                               typename Op::S *up, int o, u64 g0,
-                                                               int *err) {
+__global__ void __launch_bounds__(kMaxSweptThreads) batch_octahedron_kernel(
+    const GridDesc *grids, const int2 *tile_grid, const typename Op::S *br, typename Op::S *up,
+    int o, u64 g0, int *err) {
     const int2 e = tile_grid[blockIdx.x];
     const GridDesc gd = grids[e.x];
     const int J = e.y / gd.G.T, I = e.y - J * gd.G.T;
-    octahedron_tile<Op, STG>(op, gd.G, br + gd.panel_off, up + gd.panel_off, o, g0, err, I, J);
+    octahedron_tile<Op, STG>(Op(gd.c), gd.G, br + gd.panel_off, up + gd.panel_off, o, g0, err, I,
+                             J);
 }
 
 template <class Op, bool STG>
-__global__ void __launch_bounds__(kMaxSweptThreads) batch_down_kernel(Op op, const GridDesc *grids,
-                                                         const int2 *tile_grid,
-                                                         const typename Op::S *br,
-                                                         typename Op::S *state, int o, u64 g0,
-                                                         int *err) {
+__global__ void __launch_bounds__(kMaxSweptThreads) batch_down_kernel(
+    const GridDesc *grids, const int2 *tile_grid, const typename Op::S *br, typename Op::S *state,
+    int o, u64 g0, int *err) {
     const int2 e = tile_grid[blockIdx.x];
     const GridDesc gd = grids[e.x];
     const int J = e.y / gd.G.T, I = e.y - J * gd.G.T;
-    down_tile<Op, STG>(op, gd.G, br + gd.panel_off, state + gd.state_off, o, g0, err, I, J);
+    down_tile<Op, STG>(Op(gd.c), gd.G, br + gd.panel_off, state + gd.state_off, o, g0, err, I,
+                       J);
 }
 
 // Persistent form over every tile of a class: the tile table lists each
@@ -80,28 +82,31 @@ struct GridTiles {
         w.J = e.y / gd.G.T;
         w.I = e.y - w.J * gd.G.T;
         w.base = t - e.y;
+        w.c = grids[e.x].c;
         return w;
     }
 };
 
 template <class Op, bool STG>
 __global__ void __launch_bounds__(256) batch_persistent_kernel(
-    Op op, const GridDesc *grids, const int2 *tile_grid, int ntiles, int n, typename Op::S *state,
+    const GridDesc *grids, const int2 *tile_grid, int ntiles, int n, typename Op::S *state,
     typename Op::S *up, typename Op::S *br, int *stage, int *queue, int H, u64 g0, int *err) {
-    persistent_loop<Op, STG>(op, GridTiles{grids, tile_grid}, ntiles, n, state, up, br, stage,
-                             queue, H, g0, err, 0, kPersistSpinLimit);
+    // the update's constants come from each item's grid (TileAt::c)
+    persistent_loop<Op, STG>(Op(grids[0].c), GridTiles{grids, tile_grid}, ntiles, n, state, up,
+                             br, stage, queue, H, g0, err, 0, kPersistSpinLimit);
 }
 
 // One sub-step of every grid in a block table: block b covers a 32 x 8 patch of
 // its grid (the same per-point update as the single-grid naive kernel).
 template <class Op>
-__global__ void __launch_bounds__(256) batch_naive_kernel(Op op, const GridDesc *grids,
+__global__ void __launch_bounds__(256) batch_naive_kernel(const GridDesc *grids,
                                                           const int2 *block_grid,
                                                           const typename Op::S *in,
                                                           typename Op::S *out, u64 g) {
     typedef typename Op::S S;
     const int2 e = block_grid[blockIdx.x];
     const GridDesc gd = grids[e.x];
+    const Op op(gd.c);
     const int nbx = (gd.G.nx + 31) / 32;
     const int by = e.y / nbx, bx = e.y - by * nbx;
     const int x = bx * 32 + (threadIdx.x & 31);
@@ -121,98 +126,96 @@ struct BatchTable {
     int nv, nst, esize;
     bool default_stage;
     size_t (*smem_for)(int n, bool stage);
-    cudaError_t (*naive)(const GridDesc *, const int2 *block_grid, int nblocks, const double *c,
-                         const void *in, void *out, u64 g, cudaStream_t);
-    cudaError_t (*up)(const GridDesc *, const int2 *tile_grid, int ntiles, int n, const double *c,
+    // (every kernel takes its grid's constants from the grid table)
+    cudaError_t (*naive)(const GridDesc *, const int2 *block_grid, int nblocks, const void *in,
+                         void *out, u64 g, cudaStream_t);
+    cudaError_t (*up)(const GridDesc *, const int2 *tile_grid, int ntiles, int n,
                       const void *state, void *up, int o, u64 g0, cudaStream_t);
     cudaError_t (*bridge)(const GridDesc *, const int2 *tile_grid, int ntiles, int n,
-                          const double *c, const void *up, void *br, u64 g0, int *err,
-                          const Tuning &, cudaStream_t);
+                          const void *up, void *br, u64 g0, int *err, const Tuning &,
+                          cudaStream_t);
     cudaError_t (*octahedron)(const GridDesc *, const int2 *tile_grid, int ntiles, int n,
-                              const double *c, const void *br, void *up, int o, u64 g0, int *err,
-                              const Tuning &, cudaStream_t);
+                              const void *br, void *up, int o, u64 g0, int *err, const Tuning &,
+                              cudaStream_t);
     cudaError_t (*down)(const GridDesc *, const int2 *tile_grid, int ntiles, int n,
-                        const double *c, const void *br, void *state, int o, u64 g0, int *err,
-                        const Tuning &, cudaStream_t);
+                        const void *br, void *state, int o, u64 g0, int *err, const Tuning &,
+                        cudaStream_t);
     // all H half cycles of a class as one persistent launch; sched: ntiles
     // phase counters followed by the queue counter, zeroed
     cudaError_t (*persistent)(const GridDesc *, const int2 *tile_grid, int ntiles, int n,
-                              const double *c, void *state, void *up, void *br, int *sched, int H,
-                              u64 g0, int *err, const Tuning &, cudaStream_t);
+                              void *state, void *up, void *br, int *sched, int H, u64 g0,
+                              int *err, const Tuning &, cudaStream_t);
 };
 
 template <class Op>
 struct BatchLaunch {
     typedef typename Op::S S;
-    static cudaError_t naive(const GridDesc *d, const int2 *bg, int nblocks, const double *c,
-                             const void *in, void *out, u64 g, cudaStream_t st) {
-        batch_naive_kernel<Op><<<nblocks, kBlock, 0, st>>>(Op(c), d, bg, (const S *)in, (S *)out, g);
+    static cudaError_t naive(const GridDesc *d, const int2 *bg, int nblocks, const void *in,
+                             void *out, u64 g, cudaStream_t st) {
+        batch_naive_kernel<Op><<<nblocks, kBlock, 0, st>>>(d, bg, (const S *)in, (S *)out, g);
         return cudaGetLastError();
     }
-    static cudaError_t up(const GridDesc *d, const int2 *tg, int ntiles, int n, const double *c,
-                          const void *state, void *upp, int o, u64 g0, cudaStream_t st) {
+    static cudaError_t up(const GridDesc *d, const int2 *tg, int ntiles, int n, const void *state,
+                          void *upp, int o, u64 g0, cudaStream_t st) {
         const size_t sm = up_smem<Op>(n);
         cudaError_t e = allow_smem(batch_up_kernel<Op>, sm);
         if (e != cudaSuccess) return e;
-        batch_up_kernel<Op><<<ntiles, kBlock, sm, st>>>(Op(c), d, tg, (const S *)state, (S *)upp, o, g0);
+        batch_up_kernel<Op><<<ntiles, kBlock, sm, st>>>(d, tg, (const S *)state, (S *)upp, o, g0);
         return cudaGetLastError();
     }
     template <bool STG>
     static cudaError_t bridge_t(const GridDesc *d, const int2 *tg, int ntiles, int n,
-                                const double *c, const void *upp, void *br, u64 g0, int *err,
-                                int threads, cudaStream_t st) {
+                                const void *upp, void *br, u64 g0, int *err, int threads,
+                                cudaStream_t st) {
         const size_t sm = bridge_smem<Op>(n, STG);
         cudaError_t e = allow_smem(batch_bridge_kernel<Op, STG>, sm);
         if (e != cudaSuccess) return e;
-        batch_bridge_kernel<Op, STG><<<dim3(ntiles, 2), threads, sm, st>>>(Op(c), d, tg,
-                                                                           (const S *)upp, (S *)br,
-                                                                           g0, err);
+        batch_bridge_kernel<Op, STG><<<dim3(ntiles, 2), threads, sm, st>>>(d, tg, (const S *)upp,
+                                                                           (S *)br, g0, err);
         return cudaGetLastError();
     }
-    static cudaError_t bridge(const GridDesc *d, const int2 *tg, int ntiles, int n, const double *c,
+    static cudaError_t bridge(const GridDesc *d, const int2 *tg, int ntiles, int n,
                               const void *upp, void *br, u64 g0, int *err, const Tuning &tn,
                               cudaStream_t st) {
-        return tn.stage ? bridge_t<true>(d, tg, ntiles, n, c, upp, br, g0, err, tn.threads, st)
-                        : bridge_t<false>(d, tg, ntiles, n, c, upp, br, g0, err, tn.threads, st);
+        return tn.stage ? bridge_t<true>(d, tg, ntiles, n, upp, br, g0, err, tn.threads, st)
+                        : bridge_t<false>(d, tg, ntiles, n, upp, br, g0, err, tn.threads, st);
     }
     template <bool STG>
-    static cudaError_t oct_t(const GridDesc *d, const int2 *tg, int ntiles, int n, const double *c,
-                             const void *br, void *upp, int o, u64 g0, int *err, int threads,
-                             cudaStream_t st) {
+    static cudaError_t oct_t(const GridDesc *d, const int2 *tg, int ntiles, int n, const void *br,
+                             void *upp, int o, u64 g0, int *err, int threads, cudaStream_t st) {
         const size_t sm = down_smem<Op>(n, STG);
         cudaError_t e = allow_smem(batch_octahedron_kernel<Op, STG>, sm);
         if (e != cudaSuccess) return e;
-        batch_octahedron_kernel<Op, STG><<<ntiles, threads, sm, st>>>(Op(c), d, tg, (const S *)br,
+        batch_octahedron_kernel<Op, STG><<<ntiles, threads, sm, st>>>(d, tg, (const S *)br,
                                                                       (S *)upp, o, g0, err);
         return cudaGetLastError();
     }
     static cudaError_t octahedron(const GridDesc *d, const int2 *tg, int ntiles, int n,
-                                  const double *c, const void *br, void *upp, int o, u64 g0,
-                                  int *err, const Tuning &tn, cudaStream_t st) {
-        return tn.stage ? oct_t<true>(d, tg, ntiles, n, c, br, upp, o, g0, err, tn.threads, st)
-                        : oct_t<false>(d, tg, ntiles, n, c, br, upp, o, g0, err, tn.threads, st);
+                                  const void *br, void *upp, int o, u64 g0, int *err,
+                                  const Tuning &tn, cudaStream_t st) {
+        return tn.stage ? oct_t<true>(d, tg, ntiles, n, br, upp, o, g0, err, tn.threads, st)
+                        : oct_t<false>(d, tg, ntiles, n, br, upp, o, g0, err, tn.threads, st);
     }
     template <bool STG>
-    static cudaError_t down_t(const GridDesc *d, const int2 *tg, int ntiles, int n,
-                              const double *c, const void *br, void *state, int o, u64 g0,
-                              int *err, int threads, cudaStream_t st) {
+    static cudaError_t down_t(const GridDesc *d, const int2 *tg, int ntiles, int n, const void *br,
+                              void *state, int o, u64 g0, int *err, int threads, cudaStream_t st) {
         const size_t sm = down_smem<Op>(n, STG);
         cudaError_t e = allow_smem(batch_down_kernel<Op, STG>, sm);
         if (e != cudaSuccess) return e;
-        batch_down_kernel<Op, STG><<<ntiles, threads, sm, st>>>(Op(c), d, tg, (const S *)br,
+        batch_down_kernel<Op, STG><<<ntiles, threads, sm, st>>>(d, tg, (const S *)br,
                                                                 (S *)state, o, g0, err);
         return cudaGetLastError();
     }
-    static cudaError_t down(const GridDesc *d, const int2 *tg, int ntiles, int n, const double *c,
-                            const void *br, void *state, int o, u64 g0, int *err,
-                            const Tuning &tn, cudaStream_t st) {
-        return tn.stage ? down_t<true>(d, tg, ntiles, n, c, br, state, o, g0, err, tn.threads, st)
-                        : down_t<false>(d, tg, ntiles, n, c, br, state, o, g0, err, tn.threads, st);
+    static cudaError_t down(const GridDesc *d, const int2 *tg, int ntiles, int n, const void *br,
+                            void *state, int o, u64 g0, int *err, const Tuning &tn,
+                            cudaStream_t st) {
+        return tn.stage ? down_t<true>(d, tg, ntiles, n, br, state, o, g0, err, tn.threads, st)
+                        : down_t<false>(d, tg, ntiles, n, br, state, o, g0, err, tn.threads, st);
     }
     template <bool STG>
     static cudaError_t persistent_t(const GridDesc *d, const int2 *tg, int ntiles, int n,
-                                    const double *c, void *state, void *upp, void *br, int *sched,
-                                    int H, u64 g0, int *err, int threads, cudaStream_t st) {
+                                    void *state, void *upp, void *br, int *sched, int H, u64 g0,
+                                    int *err, int threads, cudaStream_t st) {
         const size_t sm = down_smem<Op>(n, STG);
         cudaError_t e = allow_smem(batch_persistent_kernel<Op, STG>, sm);
         if (e != cudaSuccess) return e;
@@ -226,16 +229,15 @@ struct BatchLaunch {
         long long grid = (long long)(per_sm > 0 ? per_sm : 1) * nsm;
         if (grid > nitems) grid = nitems;
         batch_persistent_kernel<Op, STG><<<(int)grid, threads, sm, st>>>(
-            Op(c), d, tg, ntiles, n, (S *)state, (S *)upp, (S *)br, sched, sched + ntiles, H, g0,
-            err);
+            d, tg, ntiles, n, (S *)state, (S *)upp, (S *)br, sched, sched + ntiles, H, g0, err);
         return cudaGetLastError();
     }
     static cudaError_t persistent(const GridDesc *d, const int2 *tg, int ntiles, int n,
-                                  const double *c, void *state, void *upp, void *br, int *sched,
-                                  int H, u64 g0, int *err, const Tuning &tn, cudaStream_t st) {
-        return tn.stage ? persistent_t<true>(d, tg, ntiles, n, c, state, upp, br, sched, H, g0, err,
+                                  void *state, void *upp, void *br, int *sched, int H, u64 g0,
+                                  int *err, const Tuning &tn, cudaStream_t st) {
+        return tn.stage ? persistent_t<true>(d, tg, ntiles, n, state, upp, br, sched, H, g0, err,
                                              tn.threads, st)
-                        : persistent_t<false>(d, tg, ntiles, n, c, state, upp, br, sched, H, g0,
+                        : persistent_t<false>(d, tg, ntiles, n, state, upp, br, sched, H, g0,
                                               err, tn.threads, st);
     }
     static const BatchTable *table() {
@@ -250,5 +252,14 @@ const BatchTable *batchtable_heat();
 const BatchTable *batchtable_heat_kahan_f32();
 const BatchTable *batchtable_heat_kahan_bf16();
 const BatchTable *batchtable_hash();
+const BatchTable *batchtable_euler();
+const BatchTable *batchtable_euler_kahan_f32();
+const BatchTable *batchtable_euler_kahan_bf16();
+
+// Maximum wave speed of planes 0-3 of every grid of a pooled state whose
+// elements are esize bytes, into d_out[grid] (bit patterns of positive doubles).
+cudaError_t batch_euler_wavespeed(const GridDesc *d_grids, int count, const void *state,
+                                  int esize, double gamma, unsigned long long *d_out,
+                                  cudaStream_t st);
 
 }  // namespace swept

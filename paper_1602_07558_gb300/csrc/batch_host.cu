@@ -62,6 +62,10 @@ struct swept2d_batch {
     long long cells = 0;
     int *errword = nullptr;
     double consts[8] = {0};
+    double params[8] = {0};
+    int nparams = 0;
+    std::vector<double> wavespeed, dt;          // Euler: per grid, fixed at set_state
+    unsigned long long *d_amax = nullptr;       // Euler: per-grid wave-speed scratch
     long long substeps = 0, launches = 0;
     bool has_state = false;
     swept::Tuning tune;
@@ -84,6 +88,10 @@ const BatchTable *batch_table(int op, int dtype) {
     if (op == SWEPT2D_OP_HEAT_KAHAN && dtype == SWEPT2D_F32) return swept::batchtable_heat_kahan_f32();
     if (op == SWEPT2D_OP_HEAT_KAHAN && dtype == SWEPT2D_BF16) return swept::batchtable_heat_kahan_bf16();
     if (op == SWEPT2D_OP_HASH && dtype == SWEPT2D_U64) return swept::batchtable_hash();
+    if (op == SWEPT2D_OP_EULER_RK2 && dtype == SWEPT2D_F64) return swept::batchtable_euler();
+    if (op == SWEPT2D_OP_EULER_KAHAN && dtype == SWEPT2D_F32) return swept::batchtable_euler_kahan_f32();
+    if (op == SWEPT2D_OP_EULER_KAHAN && dtype == SWEPT2D_BF16)
+        return swept::batchtable_euler_kahan_bf16();
     return nullptr;
 }
 
@@ -94,7 +102,7 @@ void batch_free(swept2d_batch *b) {
         if (c.d_sched) cudaFree(c.d_sched);
     }
     for (void *p : {(void *)b->d_grids, (void *)b->d_all_blocks, b->state, b->state2, b->up, b->br,
-                    (void *)b->errword})
+                    (void *)b->errword, (void *)b->d_amax})
         if (p) cudaFree(p);
     for (auto &g : b->graphs) {
         cudaGraphExecDestroy(g.exec);
@@ -117,7 +125,7 @@ int batch_naive(swept2d_batch *b, const int2 *d_blocks, int nblocks, long long c
     for (long long s = 0; s < count; ++s) {
         void *in = *cur, *out = *other;
         int rc = blaunch(b, "batched naive kernel", [&] {
-            return b->bt->naive(b->d_grids, d_blocks, nblocks, b->consts, in, out, g + s, b->stream);
+            return b->bt->naive(b->d_grids, d_blocks, nblocks, in, out, g + s, b->stream);
         });
         if (rc) return rc;
         std::swap(*cur, *other);
@@ -151,35 +159,35 @@ int batch_run(swept2d_batch *b, long long total, int mode) {
             cudaError_t e = cudaMemsetAsync(c.d_sched, 0, ((size_t)nt + 1) * sizeof(int), b->stream);
             if (e != cudaSuccess) return bcuda(b, e, "persistent schedule reset");
             int rc = blaunch(b, "batched persistent kernel", [&] {
-                return b->bt->persistent(b->d_grids, c.d_tiles, nt, c.n, b->consts, b->state,
-                                         b->up, b->br, c.d_sched, (int)H, g_start, b->errword,
-                                         c.tune, b->stream);
+                return b->bt->persistent(b->d_grids, c.d_tiles, nt, c.n, b->state, b->up, b->br,
+                                         c.d_sched, (int)H, g_start, b->errword, c.tune,
+                                         b->stream);
             });
             if (rc) return rc;
         } else if (H > 0) {
             const int half = c.n / 2;
             int rc = blaunch(b, "batched up kernel", [&] {
-                return b->bt->up(b->d_grids, c.d_tiles, nt, c.n, b->consts, b->state, b->up, 0,
-                                 g_start, b->stream);
+                return b->bt->up(b->d_grids, c.d_tiles, nt, c.n, b->state, b->up, 0, g_start,
+                                 b->stream);
             });
             if (rc) return rc;
             for (long long j = 0; j < H; ++j) {
                 const u64 g0 = g_start + (u64)j * half;
                 const int o = (j & 1) ? half : 0;
                 rc = blaunch(b, "batched bridge kernel", [&] {
-                    return b->bt->bridge(b->d_grids, c.d_tiles, nt, c.n, b->consts, b->up, b->br,
-                                         g0, b->errword, c.tune, b->stream);
+                    return b->bt->bridge(b->d_grids, c.d_tiles, nt, c.n, b->up, b->br, g0,
+                                         b->errword, c.tune, b->stream);
                 });
                 if (rc) return rc;
                 if (j + 1 < H)
                     rc = blaunch(b, "batched octahedron kernel", [&] {
-                        return b->bt->octahedron(b->d_grids, c.d_tiles, nt, c.n, b->consts, b->br,
-                                                 b->up, o, g0, b->errword, c.tune, b->stream);
+                        return b->bt->octahedron(b->d_grids, c.d_tiles, nt, c.n, b->br, b->up, o,
+                                                 g0, b->errword, c.tune, b->stream);
                     });
                 else
                     rc = blaunch(b, "batched down kernel", [&] {
-                        return b->bt->down(b->d_grids, c.d_tiles, nt, c.n, b->consts, b->br,
-                                           b->state, o, g0, b->errword, c.tune, b->stream);
+                        return b->bt->down(b->d_grids, c.d_tiles, nt, c.n, b->br, b->state, o, g0,
+                                           b->errword, c.tune, b->stream);
                     });
                 if (rc) return rc;
             }
@@ -268,9 +276,15 @@ int swept2d_batch_create(swept2d_batch_t **out, int count, const int *nx, const 
     };
     if (count < 1 || !nx || !ny || !tile) return reject("need count >= 1 and nx, ny, tile arrays");
     const BatchTable *bt = batch_table(op, dtype);
-    if (!bt) return reject("op/dtype not supported by the batch (heat F64, heat_kahan F32/BF16, hash U64)");
+    if (!bt)
+        return reject("op/dtype not supported by the batch (heat F64, heat_kahan F32/BF16, hash "
+                      "U64, euler_rk2 F64, euler_kahan F32/BF16)");
     if ((op == SWEPT2D_OP_HEAT || op == SWEPT2D_OP_HEAT_KAHAN) && (nparams < 1 || !params))
         return reject("heat needs params {r}");
+    const bool euler = op == SWEPT2D_OP_EULER_RK2 || op == SWEPT2D_OP_EULER_KAHAN;
+    if (euler && (nparams < 3 || nparams == 4 || nparams > 5 || !params))
+        return reject("euler needs params {gamma, cfl, kappa[, lx, ly]}");
+    if (nparams > 8) return reject("at most 8 params");
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
@@ -292,7 +306,13 @@ int swept2d_batch_create(swept2d_batch_t **out, int count, const int *nx, const 
     b->stream = (cudaStream_t)stream;
     b->tune.threads = 256;
     b->tune.stage = bt->default_stage;
-    if (nparams > 0) b->consts[0] = params[0];
+    if (nparams > 0 && !euler) b->consts[0] = params[0];
+    b->nparams = nparams;
+    for (int i = 0; i < nparams; ++i) b->params[i] = params[i];
+    if (euler) {
+        b->wavespeed.assign(count, 0.0);
+        b->dt.assign(count, 0.0);
+    }
     // grids, classes (by tile side), pooled offsets
     long long soff = 0, poff = 0;
     for (int i = 0; i < count; ++i) {
@@ -306,6 +326,7 @@ int swept2d_batch_create(swept2d_batch_t **out, int count, const int *nx, const 
         gd.G.PS = n ? swept::panel_stride(n) : 0;
         gd.state_off = soff;
         gd.panel_off = poff;
+        for (int k = 0; k < 8; ++k) gd.c[k] = b->consts[k];   // Euler's: at set_state
         soff += (long long)bt->nv * nx[i] * ny[i];
         poff += (long long)gd.G.T * gd.G.Q * 4 * bt->nv * gd.G.PS;
         b->cells += (long long)nx[i] * ny[i];
@@ -344,6 +365,9 @@ int swept2d_batch_create(swept2d_batch_t **out, int count, const int *nx, const 
         if ((e = dev_copy(&c.d_tiles, c.tiles)) != cudaSuccess ||
             (e = dev_copy(&c.d_blocks, c.blocks)) != cudaSuccess)
             goto fail;
+    if (euler && (e = cudaMalloc(&b->d_amax, (size_t)count * sizeof(unsigned long long))) !=
+                     cudaSuccess)
+        goto fail;
     if ((e = cudaMalloc(&b->state, b->state_bytes)) != cudaSuccess ||
         (e = cudaMalloc(&b->state2, b->state_bytes)) != cudaSuccess ||
         (e = cudaMalloc(&b->errword, sizeof(int))) != cudaSuccess ||
@@ -374,6 +398,42 @@ int swept2d_batch_set_state(swept2d_batch_t *b, const void *src, int src_is_devi
     if (!src_is_device && (e = cudaStreamSynchronize(b->stream)) != cudaSuccess)
         return bcuda(b, e, "set_state sync");
     b->substeps = 0;
+    if (b->op == SWEPT2D_OP_EULER_RK2 || b->op == SWEPT2D_OP_EULER_KAHAN) {
+        // each grid's a and dt from its own state, and its constants (formed in
+        // binary64 as for a single grid), into the grid table
+        const double gamma = b->params[0], cfl = b->params[1], kappa = b->params[2];
+        const double lx = b->nparams >= 5 ? b->params[3] : 1.0;
+        const double ly = b->nparams >= 5 ? b->params[4] : 1.0;
+        if ((e = swept::batch_euler_wavespeed(b->d_grids, b->count, b->state, b->bt->esize, gamma,
+                                              b->d_amax, b->stream)) != cudaSuccess)
+            return bcuda(b, e, "wave speed");
+        b->launches += 1;
+        std::vector<unsigned long long> bits(b->count);
+        if ((e = cudaMemcpyAsync(bits.data(), b->d_amax, bits.size() * sizeof(bits[0]),
+                                 cudaMemcpyDeviceToHost, b->stream)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(b->stream)) != cudaSuccess)
+            return bcuda(b, e, "wave speed copy");
+        for (int i = 0; i < b->count; ++i) {
+            GridDesc &gd = b->grids[i];
+            double a;
+            std::memcpy(&a, &bits[i], sizeof a);
+            const double dx = lx / gd.G.nx, dy = ly / gd.G.ny;
+            const double hmin = dx < dy ? dx : dy;
+            b->wavespeed[i] = a;
+            b->dt[i] = (cfl * hmin) / a;
+            gd.c[0] = gamma - 1.0;
+            gd.c[1] = 0.5 / dx;
+            gd.c[2] = 0.5 / dy;
+            gd.c[3] = (kappa * a) / dx;
+            gd.c[4] = (kappa * a) / dy;
+            gd.c[5] = 0.5 * b->dt[i];
+            gd.c[6] = b->dt[i];
+        }
+        if ((e = cudaMemcpyAsync(b->d_grids, b->grids.data(), b->grids.size() * sizeof(GridDesc),
+                                 cudaMemcpyHostToDevice, b->stream)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(b->stream)) != cudaSuccess)
+            return bcuda(b, e, "grid table copy");
+    }
     b->has_state = true;
     return SWEPT2D_OK;
 }
@@ -474,6 +534,18 @@ int swept2d_batch_destroy(swept2d_batch_t *b) {
 const char *swept2d_batch_last_error(const swept2d_batch_t *b) {
     if (!b) return g_batch_create_err.empty() ? "invalid batch (NULL)" : g_batch_create_err.c_str();
     return b->err.c_str();
+}
+
+int swept2d_batch_query_grid(const swept2d_batch_t *b, int grid, int what, double *out) {
+    if (!b || !out || grid < 0 || grid >= b->count) return SWEPT2D_EINVAL;
+    const GridDesc &gd = b->grids[grid];
+    switch (what) {
+        case SWEPT2D_Q_DT: *out = b->dt.empty() ? 0.0 : b->dt[grid]; break;
+        case SWEPT2D_Q_WAVESPEED: *out = b->wavespeed.empty() ? 0.0 : b->wavespeed[grid]; break;
+        case SWEPT2D_Q_CELLS: *out = (double)gd.G.nx * gd.G.ny; break;
+        default: return SWEPT2D_EINVAL;
+    }
+    return SWEPT2D_OK;
 }
 
 int swept2d_batch_query(const swept2d_batch_t *b, int what, double *out) {

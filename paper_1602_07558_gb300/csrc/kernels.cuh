@@ -915,6 +915,7 @@ struct TileAt {
     Geom G;
     long long soff, poff;
     int I, J, base;
+    const double *c;        // the grid's own update constants (nullptr: the launch's)
 };
 
 // One grid: tile index t = J T + I.
@@ -927,6 +928,7 @@ struct OneGrid {
         w.J = t / G.T;
         w.I = t - w.J * G.T;
         w.base = 0;
+        w.c = nullptr;
         return w;
     }
 };
@@ -956,6 +958,7 @@ __device__ __forceinline__ void persistent_loop(const Op &op, const Loc &at, int
         const TileAt w = at(t);
         const Geom &G = w.G;
         const int I = w.I, J = w.J;
+        const Op opi = w.c ? Op(w.c) : op;
         if (p > 1 && threadIdx.x < 32) {
             // lanes 0..8 wait for one tile each of the periodic 3 x 3 neighbourhood
             bool bad = false;
@@ -987,19 +990,19 @@ __device__ __forceinline__ void persistent_loop(const Op &op, const Loc &at, int
         if (threadIdx.x == 0) asm volatile("fence.proxy.async.global;\n" ::: "memory");
         typename Op::S *st = state + w.soff, *u = upp + w.poff, *b = br + w.poff;
         if (p == 1) {
-            up_tile(op, G, st, u, 0, g0, I, J);
+            up_tile(opi, G, st, u, 0, g0, I, J);
         } else {
             const int j = (p - 2) / 2;              // half cycle
             const u64 gj = g0 + (u64)j * h;
             const int o = (j & 1) ? h : 0;
             if ((p & 1) == 0) {                     // bridges of half cycle j
-                bridge_tile<Op, STG>(op, G, u, b, gj, err, I, J, false);
+                bridge_tile<Op, STG>(opi, G, u, b, gj, err, I, J, false);
                 __syncthreads();
-                bridge_tile<Op, STG>(op, G, u, b, gj, err, I, J, true);
+                bridge_tile<Op, STG>(opi, G, u, b, gj, err, I, J, true);
             } else if (j + 1 < H) {
-                octahedron_tile<Op, STG>(op, G, b, u, o, gj, err, I, J);
+                octahedron_tile<Op, STG>(opi, G, b, u, o, gj, err, I, J);
             } else {
-                down_tile<Op, STG>(op, G, b, st, o, gj, err, I, J);
+                down_tile<Op, STG>(opi, G, b, st, o, gj, err, I, J);
             }
         }
         // make this item's panel (and state) stores visible, to the generic and

@@ -294,10 +294,11 @@ class SweptBatch:
         L.swept2d_batch_last_error.argtypes = [vp]
         L.swept2d_batch_last_error.restype = ctypes.c_char_p
         L.swept2d_batch_query.argtypes = [vp, i, ctypes.POINTER(d)]
+        L.swept2d_batch_query_grid.argtypes = [vp, i, i, ctypes.POINTER(d)]
         for name in ("swept2d_batch_create", "swept2d_batch_set_state", "swept2d_batch_advance",
                      "swept2d_batch_get_state", "swept2d_batch_set_tuning",
                      "swept2d_batch_set_class_tuning",
-                     "swept2d_batch_destroy", "swept2d_batch_query"):
+                     "swept2d_batch_destroy", "swept2d_batch_query", "swept2d_batch_query_grid"):
             getattr(L, name).restype = i
         L._batch_ready = True
 
@@ -347,6 +348,12 @@ class SweptBatch:
     def query(self, what):
         v = ctypes.c_double()
         self._check(lib().swept2d_batch_query(self._h, Q[what], ctypes.byref(v)))
+        return v.value
+
+    def query_grid(self, grid, what):
+        """Per-grid "dt", "wavespeed" (Euler updates) or "cells"."""
+        v = ctypes.c_double()
+        self._check(lib().swept2d_batch_query_grid(self._h, int(grid), Q[what], ctypes.byref(v)))
         return v.value
 
     def close(self):

@@ -94,6 +94,57 @@ def test_batch_graph_and_split_advances_match(op, dtype):
             assert np.array_equal(g, h.get_state())
 
 
+GAMMA, CFL, KAPPA = 1.4, 0.3, 0.5
+
+
+# the Euler point state does not fit a 64-wide tile's level buffers
+EULER_SIZES = [(nx, ny, min(n, 32)) for nx, ny, n in SIZES]
+
+
+def _euler_states(dtype, seed):
+    out = []
+    for i, (nx, ny, _) in enumerate(EULER_SIZES):
+        U = inputs.euler_pulse(nx, ny, seed + i, gamma=GAMMA)
+        if dtype == "f64":
+            out.append(np.concatenate([U, U]))
+        else:
+            U = U.astype(np.float32)
+            U = U if dtype == "f32" else _bf16(U)
+            out.append(np.concatenate([U, U, np.zeros_like(U)]))
+    return out
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("mode", ["swept", "naive", "persistent"])
+def test_batch_euler_every_grid_has_its_own_time_step(oracle_lib, dtype, mode):
+    """Euler grids of uneven sizes in one batch: each grid's wave speed and
+    time step come from its own state and spacing (exactly the oracle's), and
+    every grid equals the oracle bit for bit (FP64: U; binary32 / bfloat16:
+    all 12 planes)."""
+    nsteps = 13
+    op = "euler_rk2" if dtype == "f64" else "euler_kahan"
+    states = _euler_states(dtype, seed=40)
+    S = EULER_SIZES
+    with SweptBatch([s[0] for s in S], [s[1] for s in S], [s[2] for s in S],
+                    op=op, params=(GAMMA, CFL, KAPPA), dtype=dtype) as b:
+        b.set_state(states)
+        consts = [(b.query_grid(i, "wavespeed"), b.query_grid(i, "dt")) for i in range(len(S))]
+        b.advance(nsteps, mode=mode)
+        got = b.split(b.get_state())
+    for s, g, (a_gpu, dt_gpu) in zip(states, got, consts):
+        if dtype == "f64":
+            a, dt = oracle_lib.euler_setup(s[:4], GAMMA, CFL)
+            ref = oracle_lib.euler_rk2(s[:4], GAMMA, dt, KAPPA, a, nsteps)
+            gv = g[:4]
+        else:
+            Uf = (oracle_lib.bf16_bits_to_f32(s[:4]) if dtype == "bf16" else s[:4]).astype(np.float64)
+            a, dt = oracle_lib.euler_setup(Uf, GAMMA, CFL)
+            ref = oracle_lib.euler_kahan(s, GAMMA, dt, KAPPA, a, nsteps, dtype)
+            gv = g
+        assert (a_gpu, dt_gpu) == (a, dt)
+        assert np.array_equal(gv, ref)
+
+
 def test_batch_tuning_gives_identical_bits():
     states = _states("heat_kahan", "f32", seed=3)
     outs = []

@@ -84,5 +84,8 @@ def test_batch_create_rejects_bad_tiles(tiles, needle):
 
 def test_batch_create_rejects_unsupported_ops():
     with pytest.raises(swept2d.SweptError) as ei:
-        swept2d.SweptBatch([32], [32], [16], op="euler_rk2", params=(1.4, 0.3, 0.5))
+        swept2d.SweptBatch([32], [32], [16], op="wave", params=(0.3,))
     assert "not supported" in str(ei.value)
+    with pytest.raises(swept2d.SweptError) as ei:
+        swept2d.SweptBatch([32], [32], [16], op="euler_kahan", params=(1.4, 0.3), dtype="f32")
+    assert "euler needs params" in str(ei.value)
