@@ -487,6 +487,19 @@ int swept2d_batch_get_state(swept2d_batch_t *b, void *dst, int dst_is_device) {
     return SWEPT2D_OK;
 }
 
+// Captured graphs hold the launch shapes they were captured with: drop them
+// when a class's tuning changes.
+static int drop_graphs(swept2d_batch *b) {
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bcuda(b, e, "tuning sync");
+    for (auto &g : b->graphs) {
+        cudaGraphExecDestroy(g.exec);
+        cudaGraphDestroy(g.graph);
+    }
+    b->graphs.clear();
+    return SWEPT2D_OK;
+}
+
 int swept2d_batch_set_tuning(swept2d_batch_t *b, int threads, int stage) {
     if (!b) return SWEPT2D_EINVAL;
     if (threads != 64 && threads != 128 && threads != 256 && threads != 512)
@@ -498,6 +511,8 @@ int swept2d_batch_set_tuning(swept2d_batch_t *b, int threads, int stage) {
     for (auto &c : b->classes)
         if (c.n && b->bt->smem_for(c.n, stage != 0) > (size_t)optin)
             return bfail(b, SWEPT2D_EINVAL, "set_tuning: staged panels do not fit");
+    const int rc = drop_graphs(b);
+    if (rc) return rc;
     b->tune.threads = threads;
     b->tune.stage = stage != 0;
     for (auto &c : b->classes) c.tune = b->tune;
@@ -516,6 +531,8 @@ int swept2d_batch_set_class_tuning(swept2d_batch_t *b, int tile, int threads, in
             optin = 227 * 1024;
         if (b->bt->smem_for(c.n, stage != 0) > (size_t)optin)
             return bfail(b, SWEPT2D_EINVAL, "set_class_tuning: staged panels do not fit");
+        const int rc = drop_graphs(b);
+        if (rc) return rc;
         c.tune.threads = threads;
         c.tune.stage = stage != 0;
         return SWEPT2D_OK;

@@ -592,6 +592,16 @@ int swept2d_set_tuning(swept2d_t *h, int threads, int stage) {
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
         optin = 227 * 1024;
     if (sm > (size_t)optin) return fail(h, SWEPT2D_EINVAL, "set_tuning: staged panels do not fit");
+    if (h->tune.threads != threads || h->tune.stage != (stage != 0)) {
+        // captured graphs hold the old launch shape: drop them
+        cudaError_t e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "set_tuning sync");
+        for (auto &g : h->graphs) {
+            cudaGraphExecDestroy(g.exec);
+            cudaGraphDestroy(g.graph);
+        }
+        h->graphs.clear();
+    }
     h->tune.threads = threads;
     h->tune.stage = stage != 0;
     h->smem_bytes = sm;
