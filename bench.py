@@ -489,7 +489,8 @@ def main():
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             sw.set_state(h_in)
-            sw.advance(w.nsteps)
+            sw.advance(w.nsteps, mode="persistent" if args.persistent else "swept",
+                       graph=args.graph)
             sw.get_state(h_out)
             dt = time.perf_counter() - t0
             if i >= 1:
