@@ -182,7 +182,11 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        # the raw samples go to $SWEPT2D_CLOCKS_DIR (default: the system's
+        # temporary directory); their summary goes into the JSON line
+        import tempfile
+        out_dir = os.environ.get("SWEPT2D_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out_dir, f"clocks_rank{gpu_index}.csv")
 
     def __enter__(self):
         try:
