@@ -332,7 +332,6 @@ def bridge_updates(n):
 # capture of their current version report None.
 OCT_TRAFFIC_PER_TILE = {
     ("heat", "f64", 32): (71.499264e6 + 29.265152e6) / 4096,
-    ("euler_kahan", "f32", 32): (427.88352e6 + 380.93696e6) / 4096,
 }
 
 

@@ -59,7 +59,7 @@ template <class Op>
 __host__ __device__ inline SmemPlan smem_plan(int n, int stage_segments, bool staged) {
     typedef typename Op::S S;
     const size_t P = (size_t)n + 2;
-    const size_t levels = (size_t)(2 * Op::NV + Op::AUX) * P * P * sizeof(S);
+    const size_t levels = (size_t)((Op::INPLACE ? 1 : 2) * Op::NV + Op::AUX) * P * P * sizeof(S);
     SmemPlan pl;
     pl.stage_off = (levels + 15) & ~(size_t)15;
     const size_t stage = staged ? (size_t)stage_segments * Op::NV * panel_stride(n) * sizeof(S) : 0;
@@ -354,12 +354,13 @@ __device__ __forceinline__ void compute_rect(const EulerOp &op, int stage, u64, 
             double res;
             op.combine(stage, c, Wc[0], Wc[1], Wc[-1], Wc[P], Wc[-P], __dsub_rn(F[1], F[-1]),
                        __dsub_rn(G[P], G[-P]), src[c * plane + off], res);
+            // (in place, src == dst: the passed-through plane is already there)
             if (stage == 0) {
-                dst[c * plane + off] = src[c * plane + off];
+                if (src != dst) dst[c * plane + off] = src[c * plane + off];
                 dst[(4 + c) * plane + off] = res;
             } else {
                 dst[c * plane + off] = res;
-                dst[(4 + c) * plane + off] = src[(4 + c) * plane + off];
+                if (src != dst) dst[(4 + c) * plane + off] = src[(4 + c) * plane + off];
             }
         }
     }
@@ -397,14 +398,17 @@ __device__ __forceinline__ void compute_rect(const EulerKahanOp<SS> &op, int sta
             const float L = op.rate(St::ld(Wc[0]), St::ld(Wc[1]), St::ld(Wc[-1]), St::ld(Wc[P]),
                                     St::ld(Wc[-P]), __fsub_rn(F[1], F[-1]),
                                     __fsub_rn(G[P], G[-P]));
+            // (in place, src == dst: the passed-through planes are already there)
             if (stage == 0) {
-                dst[c * plane + off] = src[c * plane + off];
                 dst[(4 + c) * plane + off] = op.midpoint(L, St::ld(src[c * plane + off]));
-                dst[(8 + c) * plane + off] = src[(8 + c) * plane + off];
+                if (src != dst) {
+                    dst[c * plane + off] = src[c * plane + off];
+                    dst[(8 + c) * plane + off] = src[(8 + c) * plane + off];
+                }
             } else {
-                op.accumulate(L, St::ld(src[c * plane + off]), St::ld(src[(8 + c) * plane + off]),
-                              dst[c * plane + off], dst[(8 + c) * plane + off]);
-                dst[(4 + c) * plane + off] = src[(4 + c) * plane + off];
+                const float u = St::ld(src[c * plane + off]), cc = St::ld(src[(8 + c) * plane + off]);
+                op.accumulate(L, u, cc, dst[c * plane + off], dst[(8 + c) * plane + off]);
+                if (src != dst) dst[(4 + c) * plane + off] = src[(4 + c) * plane + off];
             }
         }
     }
@@ -562,6 +566,7 @@ __device__ __forceinline__ void up_body(const Op &op, const Geom &G, typename Op
         const S *cur = par ? buf1 : buf0;
         S *nxt = par ? buf0 : buf1;
         write_up_panels<S, Op::NV>(cur, P, G, k, up, slot);
+        if constexpr (Op::INPLACE) __syncthreads();   // panels read before the level is overwritten
         if (k + 1 < h) {
             const u64 g = g0 + k;
             compute_rect(op, (int)(g % Op::NST), g, cur, nxt, aux, P, k + 1, k + 1,
@@ -579,7 +584,7 @@ __device__ __forceinline__ void up_tile(const Op &op, const Geom &G, const typen
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = G.n, P = n + 2, plane = P * P;
     S *buf0 = reinterpret_cast<S *>(smem_raw);
-    S *buf1 = buf0 + Op::NV * plane;
+    S *buf1 = Op::INPLACE ? buf0 : buf0 + Op::NV * plane;   // one buffer for in-place levels
     S *aux = buf1 + Op::NV * plane;
     const size_t gplane = (size_t)G.nx * G.ny;
     const int x0 = o + I * n, y0 = o + J * n;
@@ -617,7 +622,7 @@ __device__ __forceinline__ void bridge_tile(const Op &op, const Geom &G, const t
     const int n = G.n, h = n / 2, P = n + 2, plane = P * P;
     S *bufs[2];
     bufs[0] = reinterpret_cast<S *>(smem_raw);
-    bufs[1] = bufs[0] + NV * plane;
+    bufs[1] = Op::INPLACE ? bufs[0] : bufs[0] + NV * plane;   // one buffer for in-place levels
     S *aux = bufs[1] + NV * plane;
     const int slot = J * G.T + I;
     // low tile: Up(I,J); high tile: Up(I,J+1) or Up(I+1,J)
@@ -675,16 +680,18 @@ __device__ __forceinline__ void bridge_tile(const Op &op, const Geom &G, const t
         }
         if constexpr (!STG) async_commit();
     };
-    if constexpr (STG) {
+    // strips copied level by level (staged panels; in-place levels, whose one
+    // buffer cannot hold two levels' strips), or all at once before the first
+    // level: strips of one parity never overlap, and no level's rectangle,
+    // reads or panel reads touch a later level's strip, so the copies' latency
+    // is paid once per tile instead of once per level
+    constexpr bool per_level = STG || Op::INPLACE;
+    if constexpr (per_level) {
         load_strips(0, bufs[0]);
     } else {
-        // every level's strips at once, each into its level's buffer: strips
-        // of one parity never overlap, and no level's rectangle, reads or
-        // panel reads touch a later level's strip, so the copies' latency is
-        // paid once per tile instead of once per level
         for (int k = 0; k < h; ++k) load_strips(k, bufs[k & 1]);
-        async_wait();
     }
+    if constexpr (!STG) async_wait();
     __syncthreads();
     for (int k = 0; k < h; ++k) {
         S *cur = bufs[k & 1];
@@ -707,14 +714,19 @@ __device__ __forceinline__ void bridge_tile(const Op &op, const Geom &G, const t
                 for (int v = 0; v < NV; ++v) dst[(size_t)v * G.PS] = src[v * plane];
             }
         }
+        if constexpr (Op::INPLACE) __syncthreads();   // panels read before the strip copy below
         if (k + 1 < h) {
-            if constexpr (STG) load_strips(k + 1, nxt);   // disjoint from the rectangle below
+            // the next strip lies outside the rectangle below; for in-place
+            // levels it overlaps the rectangle's outermost neighbours, whose
+            // planes read at neighbours keep their values between the levels
+            if constexpr (per_level) load_strips(k + 1, nxt);
             const u64 g = g0 + k;
             const int u0 = k + 1, uw = n - 2 * k - 2, w0 = h - k - 1, ww = 2 * k + 2;
             if (xb)
                 compute_rect(op, (int)(g % Op::NST), g, cur, nxt, aux, P, w0, u0, ww, uw);
             else
                 compute_rect(op, (int)(g % Op::NST), g, cur, nxt, aux, P, u0, w0, uw, ww);
+            if constexpr (per_level && !STG) async_wait();
         }
         __syncthreads();
     }
@@ -790,24 +802,30 @@ __device__ __forceinline__ bool down_body(const Op &op, const Geom &G, unsigned 
         }
         if constexpr (!STG) async_commit();
     };
-    if constexpr (STG) {
+    // rings copied level by level (staged panels; in-place levels), or all at
+    // once before the first level: rings of one parity never overlap and lie
+    // outside every earlier level's square and reads, so the copies' latency
+    // is paid once per tile
+    constexpr bool per_level = STG || Op::INPLACE;
+    if constexpr (per_level) {
         load_ring(0, buf0);
     } else {
-        // every level's ring at once, each into its level's buffer: rings of
-        // one parity never overlap and lie outside every earlier level's
-        // square and reads, so the copies' latency is paid once per tile
         for (int k = 0; k < h; ++k) load_ring(k, (k & 1) ? buf1 : buf0);
-        async_wait();
     }
+    if constexpr (!STG) async_wait();
     __syncthreads();
     for (int k = 0; k < h; ++k) {
         S *cur = (k & 1) ? buf1 : buf0;
         S *nxt = (k & 1) ? buf0 : buf1;
-        if constexpr (STG)
-            if (k + 1 < h) load_ring(k + 1, nxt);   // disjoint from the square computed below
+        // the next ring lies outside the square below; for in-place levels it
+        // overlaps the square's outermost neighbours, whose planes read at
+        // neighbours keep their values between the levels
+        if constexpr (per_level)
+            if (k + 1 < h) load_ring(k + 1, nxt);
         const u64 g = g0 + k;
         compute_rect(op, (int)(g % Op::NST), g, cur, nxt, aux, P, h - k - 1, h - k - 1,
                      2 * k + 2, 2 * k + 2);
+        if constexpr (per_level && !STG) async_wait();
         __syncthreads();
     }
     return true;
@@ -823,7 +841,7 @@ __device__ __forceinline__ void octahedron_tile(const Op &op, const Geom &G,
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = G.n, h = n / 2, P = n + 2, plane = P * P;
     S *buf0 = reinterpret_cast<S *>(smem_raw);
-    S *buf1 = buf0 + Op::NV * plane;
+    S *buf1 = Op::INPLACE ? buf0 : buf0 + Op::NV * plane;   // one buffer for in-place levels
     S *aux = buf1 + Op::NV * plane;
     if (!down_body<Op, STG>(op, G, smem_raw, buf0, buf1, aux, P, br, g0, err, I, J)) return;
     // Down(I,J) in frame o+h is Up(I,J) of frame h when o = 0, and Up(I+1,J+1)
@@ -851,7 +869,7 @@ __device__ __forceinline__ void down_tile(const Op &op, const Geom &G, const typ
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = G.n, h = n / 2, P = n + 2, plane = P * P;
     S *buf0 = reinterpret_cast<S *>(smem_raw);
-    S *buf1 = buf0 + Op::NV * plane;
+    S *buf1 = Op::INPLACE ? buf0 : buf0 + Op::NV * plane;   // one buffer for in-place levels
     S *aux = buf1 + Op::NV * plane;
     if (!down_body<Op, STG>(op, G, smem_raw, buf0, buf1, aux, P, br, g0, err, I, J)) return;
     const S *fin = (h & 1) ? buf1 : buf0;

@@ -6,6 +6,9 @@
 //   NST      sub-steps (stages) per time step
 //   AUX      extra shared-memory planes the update's level computation uses
 //   STAGE    stage the block's input panels in shared memory by TMA
+//   INPLACE  every stage writes only planes that it reads at the centre point
+//            alone (never at a neighbour), so a level may be computed in place
+//            in a single level buffer
 //   operator()(stage, g, a, out): a(dx, dy, v) reads value v of the neighbour at
 //            offset (dx, dy) in {-1,0,1}^2 at the level below; out[0..NV) is the
 //            new point state; g is the global sub-step index.
@@ -29,6 +32,7 @@ struct HeatOp {
     typedef double S;
     static constexpr int NV = 1, NST = 1, AUX = 1;
     static constexpr bool STAGE = false;
+    static constexpr bool INPLACE = false;
     double r;
     __host__ __device__ explicit HeatOp(const double *c) : r(c[0]) {}
     template <class A>
@@ -67,6 +71,7 @@ struct HeatKahanOp {
     // bfloat16 panels are staged by TMA (element copies of 2 bytes are slow);
     // binary32 ones are copied straight into the level buffers (more blocks fit)
     static constexpr bool STAGE = sizeof(SS) == 2;
+    static constexpr bool INPLACE = false;
     float r;
     __host__ __device__ explicit HeatKahanOp(const double *c) : r((float)c[0]) {}
     // the update from the centre (u, c) and the four edge neighbours' u
@@ -101,6 +106,9 @@ struct EulerKahanOp {
     // aux: the 8 binary32 flux planes of a level, counted in SS elements
     static constexpr int NV = 12, NST = 2, AUX = 8 * (int)(sizeof(float) / sizeof(SS));
     static constexpr bool STAGE = false;
+    // each stage writes only planes it reads at the centre alone, so a
+    // level can be computed in place in one level buffer
+    static constexpr bool INPLACE = true;
     float gm1, cx, cy, kax, kay, tau0, tau1;
     __host__ __device__ explicit EulerKahanOp(const double *c)
         : gm1((float)c[0]), cx((float)c[1]), cy((float)c[2]), kax((float)c[3]),
@@ -182,6 +190,7 @@ struct WaveOp {
     typedef double S;
     static constexpr int NV = 2, NST = 1, AUX = 1;   // aux: pair sums of a level
     static constexpr bool STAGE = false;
+    static constexpr bool INPLACE = false;
     double C2;
     __host__ __device__ explicit WaveOp(const double *c) : C2(c[0]) {}
     template <class A>
@@ -200,6 +209,7 @@ struct IncrementOp {
     typedef double S;
     static constexpr int NV = 1, NST = 1, AUX = 0;
     static constexpr bool STAGE = false;
+    static constexpr bool INPLACE = false;
     __host__ __device__ explicit IncrementOp(const double *) {}
     template <class A>
     __device__ __forceinline__ void operator()(int, u64, const A &a, S *out) const {
@@ -212,6 +222,7 @@ struct LevelTagOp {
     typedef double S;
     static constexpr int NV = 1, NST = 1, AUX = 0;
     static constexpr bool STAGE = false;
+    static constexpr bool INPLACE = false;
     __host__ __device__ explicit LevelTagOp(const double *) {}
     template <class A>
     __device__ __forceinline__ void operator()(int, u64, const A &a, S *out) const {
@@ -238,6 +249,7 @@ struct HashOp {
     typedef u64 S;
     static constexpr int NV = 1, NST = 1, AUX = 0;
     static constexpr bool STAGE = false;
+    static constexpr bool INPLACE = false;
     __host__ __device__ explicit HashOp(const double *) {}
     template <class A>
     __device__ __forceinline__ void operator()(int, u64 g, const A &a, S *out) const {
@@ -257,6 +269,7 @@ struct Wide2Op {
     typedef u64 S;
     static constexpr int NV = 5, NST = 2, AUX = 0;
     static constexpr bool STAGE = false;
+    static constexpr bool INPLACE = false;
     __host__ __device__ explicit Wide2Op(const double *) {}
     template <class A>
     __device__ __forceinline__ void operator()(int stage, u64, const A &a, S *out) const {
@@ -286,6 +299,9 @@ struct EulerOp {
     typedef double S;
     static constexpr int NV = 8, NST = 2, AUX = 8;   // aux: F and G of a level
     static constexpr bool STAGE = false;
+    // each stage writes only planes it reads at the centre alone, so a
+    // level can be computed in place in one level buffer
+    static constexpr bool INPLACE = true;
     double gm1, cx, cy, kax, kay, tau0, tau1;
     __host__ __device__ explicit EulerOp(const double *c)
         : gm1(c[0]), cx(c[1]), cy(c[2]), kax(c[3]), kay(c[4]), tau0(c[5]), tau1(c[6]) {}
