@@ -105,7 +105,8 @@ struct EulerKahanOp {
     typedef SS S;
     // aux: the 8 binary32 flux planes of a level, counted in SS elements
     static constexpr int NV = 12, NST = 2, AUX = 8 * (int)(sizeof(float) / sizeof(SS));
-    static constexpr bool STAGE = false;
+    // bfloat16 panels are staged by TMA (element copies of 2 bytes are slow)
+    static constexpr bool STAGE = sizeof(SS) == 2;
     // each stage writes only planes it reads at the centre alone, so a
     // level can be computed in place in one level buffer
     static constexpr bool INPLACE = true;
