@@ -191,6 +191,25 @@ struct LinearWalk {
     }
 };
 
+// Visit every point (xx, yy) of a W x H rectangle (W even), threads taking
+// consecutive points. Tall rectangles narrower than a warp are taken in
+// column-pair order (x = 2p + (q & 1), y = q >> 1 for the q-th point of pair
+// p): with a row pitch whose half is odd (P = n + 2, n a multiple of 4) the 32
+// consecutive points of a pair fall on 32 different banks, where row order maps
+// several short rows onto the same banks. Other rectangles are taken in row
+// order. (The shape rule is where a bank-count model of both orders at the
+// stencil's five offsets favours column pairs for 4-byte elements; 8- and
+// 2-byte elements measured no faster, and take row order: PAIRS = false.)
+template <bool PAIRS, class F>
+__device__ __forceinline__ void for_each_point(int W, int H, F &&f) {
+    if (PAIRS && W < 32 && (H >= 14 || (W <= 10 && H >= 6))) {
+        for (LinearWalk w(2 * H); w.yy < (W >> 1); w.next(2 * H))
+            f(2 * w.yy + (w.xx & 1), w.xx >> 1);
+    } else {
+        for (LinearWalk w(W); w.yy < H; w.next(W)) f(w.xx, w.yy);
+    }
+}
+
 // Neighbourhood accessor into a shared-memory level buffer; p points at the
 // centre point in plane 0.
 template <class S>
@@ -333,8 +352,8 @@ __device__ __forceinline__ void compute_rect(const EulerOp &op, int stage, u64, 
                                              int W, int H) {
     const int plane = P * P, w0 = stage == 0 ? 0 : 4;
     if (W <= 0 || H <= 0) return;
-    for (LinearWalk w(W + 2); w.yy < H + 2; w.next(W + 2)) {
-        const int off = (y0 + w.yy) * P + (x0 + w.xx);     // point (x0-1+xx, y0-1+yy)
+    for_each_point<false>(W + 2, H + 2, [&](int xx, int yy) {
+        const int off = (y0 + yy) * P + (x0 + xx);     // point (x0-1+xx, y0-1+yy)
         double F[4], G[4];
         op.fluxes(src[w0 * plane + off], src[(w0 + 1) * plane + off],
                   src[(w0 + 2) * plane + off], src[(w0 + 3) * plane + off], F, G);
@@ -343,10 +362,10 @@ __device__ __forceinline__ void compute_rect(const EulerOp &op, int stage, u64, 
             aux[c * plane + off] = F[c];
             aux[(4 + c) * plane + off] = G[c];
         }
-    }
+    });
     __syncthreads();
-    for (LinearWalk w(W); w.yy < H; w.next(W)) {
-        const int off = (y0 + w.yy + 1) * P + (x0 + w.xx + 1);
+    for_each_point<false>(W, H, [&](int xx, int yy) {
+        const int off = (y0 + yy + 1) * P + (x0 + xx + 1);
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             const double *Wc = src + (w0 + c) * plane + off;
@@ -363,7 +382,7 @@ __device__ __forceinline__ void compute_rect(const EulerOp &op, int stage, u64, 
                 if (src != dst) dst[(4 + c) * plane + off] = src[(4 + c) * plane + off];
             }
         }
-    }
+    });
 }
 
 // Euler in binary32 with reduced-precision storage: the same two passes as
@@ -377,8 +396,8 @@ __device__ __forceinline__ void compute_rect(const EulerKahanOp<SS> &op, int sta
     float *aux = reinterpret_cast<float *>(aux_s);
     const int plane = P * P, w0 = stage == 0 ? 0 : 4;
     if (W <= 0 || H <= 0) return;
-    for (LinearWalk w(W + 2); w.yy < H + 2; w.next(W + 2)) {
-        const int off = (y0 + w.yy) * P + (x0 + w.xx);     // point (x0-1+xx, y0-1+yy)
+    for_each_point<sizeof(SS) == 4>(W + 2, H + 2, [&](int xx, int yy) {
+        const int off = (y0 + yy) * P + (x0 + xx);     // point (x0-1+xx, y0-1+yy)
         float F[4], G[4];
         op.fluxes(St::ld(src[w0 * plane + off]), St::ld(src[(w0 + 1) * plane + off]),
                   St::ld(src[(w0 + 2) * plane + off]), St::ld(src[(w0 + 3) * plane + off]), F, G);
@@ -387,10 +406,10 @@ __device__ __forceinline__ void compute_rect(const EulerKahanOp<SS> &op, int sta
             aux[c * plane + off] = F[c];
             aux[(4 + c) * plane + off] = G[c];
         }
-    }
+    });
     __syncthreads();
-    for (LinearWalk w(W); w.yy < H; w.next(W)) {
-        const int off = (y0 + w.yy + 1) * P + (x0 + w.xx + 1);
+    for_each_point<sizeof(SS) == 4>(W, H, [&](int xx, int yy) {
+        const int off = (y0 + yy + 1) * P + (x0 + xx + 1);
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             const SS *Wc = src + (w0 + c) * plane + off;
@@ -411,7 +430,7 @@ __device__ __forceinline__ void compute_rect(const EulerKahanOp<SS> &op, int sta
                 if (src != dst) dst[(4 + c) * plane + off] = src[(4 + c) * plane + off];
             }
         }
-    }
+    });
 }
 
 // Wave: the same pair-sum sharing as the heat update (pass 1 forms the
