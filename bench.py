@@ -3,7 +3,8 @@ path beside it), printing one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload heat4096|heat64|heat2048_f32|heat2048_bf16|euler2048|
-                              euler2048_f32|euler2048_bf16|wave1024|batch1024]
+                              euler2048_f32|euler2048_bf16|wave1024|batch1024|
+                              batch1024_euler]
 
 The default workload is the headline one: 2D heat, periodic 4096 x 4096 FP64,
 r = 0.2, 10,000 steps, smooth 32-mode initial field, tile 32. One bench step =
@@ -20,7 +21,9 @@ bfloat16 storage, error against the FP64 solution reported); wave1024 (the paper
 equation, leapfrog, Courant number 0.3, source at the centre, 1024 x 1024);
 batch1024 (1,024 independent grids of uneven sizes, binary32 storage, one
 graph-captured swept launch sequence for all of them, tile autotuned per size
-class, against the batched naive path and against looping single-grid runs).
+class, against the batched naive path and against looping single-grid runs);
+batch1024_euler (the same 1,024 grid sizes with the binary32 Euler form, each
+grid's own time step, 2,000 steps).
 
 With N > 1 (torchrun, one process per GPU) every rank advances its own
 independent grid ("replicas only"), the timed region is bracketed by a barrier,
@@ -98,6 +101,11 @@ WORKLOADS = {
                           "1024 independent periodic grids, nx and ny uniform in {32,48,...,512} "
                           "(seed 3), heat with binary32 storage and Kahan-compensated update, "
                           "r=0.2, 20000 steps"),
+    "batch1024_euler": Workload("euler_kahan", "f32", 0, 2_000, 0, (GAMMA, CFL, KAPPA), "batch",
+                                3, "1024 independent periodic grids, nx and ny uniform in "
+                                "{32,48,...,512} (seed 3), Euler with binary32 storage and "
+                                "arithmetic, Kahan-compensated update, each grid's own CFL 0.3 "
+                                "time step, 2000 steps"),
     "wave1024": Workload("wave", "f64", 1024, 10_000, 32, (0.3,), "source", 0,
                          "wave 1024x1024 FP64 leapfrog, Courant 0.3, Gaussian source at the "
                          "centre, 10000 steps", 6),
@@ -630,23 +638,39 @@ def batch_sizes(seed, count=1024):
         [int(v) for v in rng.choice(vals, size=count)]
 
 
-def batch_states(nx, ny, seed, dtype):
+def batch_states(nx, ny, seed, dtype, op="heat_kahan"):
+    """Per grid: heat (u, c = 0) from U[0,1) (seed 100000 seed + i), or Euler
+    (U, U* = U, C = 0) from the pressure pulse (seed 100000 seed + i)."""
     from paper_1602_07558_gb300 import inputs
     parts = []
     for i, (a, b) in enumerate(zip(nx, ny)):
-        u = inputs.uniform(a, b, seed * 100_000 + i).astype(np.float32)
-        if dtype == "bf16":
-            import torch
-            u = torch.from_numpy(u).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
+        if op == "euler_kahan":
+            U = to_storage(inputs.euler_pulse(a, b, seed * 100_000 + i, gamma=GAMMA)
+                           .astype(np.float32), dtype)
+            parts.append(np.concatenate([U, U, np.zeros_like(U)]).reshape(-1))
+            continue
+        u = to_storage(inputs.uniform(a, b, seed * 100_000 + i).astype(np.float32), dtype)
         parts.append(np.stack([u, np.zeros_like(u)]).reshape(-1))
     return parts
+
+
+def batch_oracle(w, part, a, b, nsteps):
+    """The oracle on one grid of the batch (same layout as the grid's slice)."""
+    import oracle
+    if w.op == "euler_kahan":
+        S = part.reshape(12, b, a)
+        av, dt = oracle.euler_setup(storage_to_f64(S[:4], w.dtype), GAMMA, CFL)
+        return oracle.euler_kahan(S, GAMMA, dt, KAPPA, av, nsteps, storage=w.dtype)
+    st = part.reshape(2, b, a)
+    return np.stack(oracle.heat_kahan(st[0], st[1], w.params[0], nsteps, storage=w.dtype))
 
 
 def run_batch(args, w, world, rank, local):
     nx, ny = batch_sizes(w.seed + rank)
     count = len(nx)
     cells = sum(a * b for a, b in zip(nx, ny))
-    parts = batch_states(nx, ny, w.seed + rank, w.dtype)
+    parts = batch_states(nx, ny, w.seed + rank, w.dtype, w.op)
+    nv = 12 if w.op == "euler_kahan" else 2
     flat = np.concatenate(parts)
     if args.impl == "reference":
         if rank != 0:
@@ -659,8 +683,7 @@ def run_batch(args, w, world, rank, local):
         t0 = time.perf_counter()
         done = 0
         for i in sample:
-            st = parts[i].reshape(2, ny[i], nx[i])
-            oracle.heat_kahan(st[0], st[1], w.params[0], nsteps, storage=w.dtype)
+            batch_oracle(w, parts[i], nx[i], ny[i], nsteps)
             done += nx[i] * ny[i] * nsteps
         dt = time.perf_counter() - t0
         value = done / dt / 1e9
@@ -752,29 +775,34 @@ def run_batch(args, w, world, rank, local):
     value = world * cells * nsteps / (ms_sw * 1e-3) / 1e9
     naive_value = world * cells * nsteps / (naive_ms * 1e-3) / 1e9 if naive_ms else None
     loop_value = loop_cells * nsteps / (loop_ms * 1e-3) / 1e9
-    # error against FP64 on four sample grids (GPU FP64 heat, bitwise the oracle)
+    # error against FP64 on four sample grids (the GPU FP64 path of the same
+    # update from the same values, bitwise the oracle in the parity tests)
     split, off = [], 0
     for a, b in zip(nx, ny):
-        split.append(out_sw[off:off + 2 * a * b].reshape(2, b, a))
-        off += 2 * a * b
+        split.append(out_sw[off:off + nv * a * b].reshape(nv, b, a))
+        off += nv * a * b
     errs = []
     for i in sample[:4]:
-        u0 = storage_to_f64(parts[i].reshape(2, ny[i], nx[i])[0], w.dtype)
-        with Swept2D(nx[i], ny[i], op="heat", tile=16, params=w.params, stream=stream) as f64:
-            f64.set_state(np.ascontiguousarray(u0[None]))
+        v0 = storage_to_f64(parts[i].reshape(nv, ny[i], nx[i]), w.dtype)
+        if w.op == "euler_kahan":
+            f64 = Swept2D(nx[i], ny[i], op="euler_rk2", tile=16, params=w.params, stream=stream)
+            init = np.concatenate([v0[:4], v0[:4]])
+        else:
+            f64 = Swept2D(nx[i], ny[i], op="heat", tile=16, params=w.params, stream=stream)
+            init = v0[:1]
+        with f64:
+            f64.set_state(np.ascontiguousarray(init))
             f64.advance(nsteps)
-            ref = f64.get_state()[0]
-        u = storage_to_f64(split[i][0], w.dtype)
-        errs.append(float(np.max(np.abs(u - ref)) / max(np.max(np.abs(ref)), np.max(np.abs(u0)))))
+            ref = f64.get_state()[:4 if w.op == "euler_kahan" else 1]
+        got = storage_to_f64(split[i][:ref.shape[0]], w.dtype)
+        denom = max(np.max(np.abs(ref)), np.max(np.abs(init)))
+        errs.append(float(np.max(np.abs(got - ref)) / denom))
     # parity of the two smallest grids against the oracle (every point)
     import oracle
     oracle.build()
     smallest = sorted(range(count), key=lambda i: nx[i] * ny[i])[:2]
-    par = []
-    for i in smallest:
-        st = parts[i].reshape(2, ny[i], nx[i])
-        ru, rc = oracle.heat_kahan(st[0], st[1], w.params[0], nsteps, storage=w.dtype)
-        par.append(bool(np.array_equal(split[i][0], ru) and np.array_equal(split[i][1], rc)))
+    par = [bool(np.array_equal(split[i], batch_oracle(w, parts[i], nx[i], ny[i], nsteps)))
+           for i in smallest]
     class_counts = {}
     for t in tiles:
         class_counts[str(t)] = class_counts.get(str(t), 0) + 1
@@ -796,8 +824,9 @@ def run_batch(args, w, world, rank, local):
             "speedup_vs_looped": value / loop_value,
             "swept_equals_naive_bitwise": same if not args.no_naive else None,
             "oracle_parity_two_smallest_grids": par,
-            "error_vs_fp64": {"u_max_rel_4_sample_grids": errs,
-                              "fp64_reference": "GPU FP64 heat path from the same initial field"},
+            "error_vs_fp64": {"max_rel_4_sample_grids": errs,
+                              "fp64_reference": "GPU FP64 path of the same update from the same "
+                                                "initial values"},
             "e2e": {"value": cells * nsteps / e2e_s / 1e9, "unit": UNIT,
                     "h2d_bytes_per_step": int(flat.nbytes), "d2h_bytes_per_step": int(flat.nbytes)},
             "gpu_launches": launches, "clocks": clocks.summary(),
