@@ -11,9 +11,11 @@
  * "network" is a panel buffer in device memory plus a kernel boundary. The
  * downward pyramid of one half cycle and the upward pyramid of the next act on
  * the same tile in the same frame, so they run fused in one kernel (the
- * "octahedron"): two launches per n/2 sub-steps. A plain one-kernel-per-sub-step
- * path (mode SWEPT2D_NAIVE) uses the same point-update code and gives bitwise
- * identical results.
+ * "octahedron"): two launches per n/2 sub-steps, or one persistent launch per
+ * advance (SWEPT2D_PERSISTENT). A plain one-kernel-per-sub-step path (mode
+ * SWEPT2D_NAIVE) uses the same point-update code and gives bitwise identical
+ * results. Many independent grids of uneven sizes share launches through the
+ * swept2d_batch_* calls.
  *
  * Conventions.
  *  - State: nvars planes of ny x nx elements, row-major, x fastest. Plane v,
@@ -48,7 +50,9 @@ typedef struct swept2d swept2d_t;
 #define SWEPT2D_EINVAL   (-1)   /* invalid argument (message says which) */
 #define SWEPT2D_ECUDA    (-2)   /* a CUDA call or kernel launch failed */
 #define SWEPT2D_ENOMEM   (-3)   /* device or host allocation failed */
-#define SWEPT2D_ETIMEOUT (-4)   /* a bounded wait gave up (reserved) */
+#define SWEPT2D_ETIMEOUT (-4)   /* a kernel's bounded wait gave up (TMA panel copies or
+                                   the persistent form's neighbourhood waits); the
+                                   state is unspecified until the next set_state */
 #define SWEPT2D_ESTATE   (-5)   /* call out of order (e.g. advance before set_state) */
 
 /* Point updates (the paper's St_k; Section 2, Section 5).
@@ -112,7 +116,8 @@ typedef struct swept2d swept2d_t;
  * The first advance with a given (nsteps, mode) and state buffer is captured
  * (stream capture on the handle's stream, which must not be the legacy default
  * stream) and cached (up to 8 per handle); later ones replay it with one graph
- * launch. Results are the same bits as without the flag. */
+ * launch. Results are the same bits as without the flag. Changing the launch
+ * shape (swept2d_set_tuning) drops the cached graphs. */
 #define SWEPT2D_GRAPH 0x100
 /* Flag OR-ed into SWEPT2D_SWEPT: run all half cycles of the advance as one
  * persistent launch (resident blocks take tile work items in phase order and
