@@ -340,7 +340,7 @@ def bridge_updates(n):
 # capture of their current version report None.
 OCT_TRAFFIC_PER_TILE = {
     ("heat", "f64", 32): (71.499264e6 + 29.265152e6) / 4096,
-    ("euler_kahan", "f32", 32): (428.338688e6 + 380.551424e6) / 4096,
+    ("euler_kahan", "f32", 32): (427.939072e6 + 380.31488e6) / 4096,
 }
 
 
