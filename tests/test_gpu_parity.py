@@ -372,6 +372,42 @@ def test_heat_4096_tile_32_full_grid_matches_oracle(oracle_lib):
     assert abs(long.sum() - u0.sum()) <= 640 * u0.size * 4 * np.finfo(float).eps * np.abs(u0).max()
 
 
+def test_euler_2048_tile_32_full_grid_matches_oracle(oracle_lib):
+    """The Euler benchmark's grid and tile (2048 x 2048, n = 32), FP64: three
+    half cycles (in-place levels) and a tail, every point against the oracle,
+    and the persistent form the same bits."""
+    nsteps = 27                        # 54 sub-steps = 3 half cycles + 6
+    u0, U = _euler_u0(2048, 2048, seed=2)
+    a, dt = oracle_lib.euler_setup(U, GAMMA, CFL)
+    ref = oracle_lib.euler_rk2(U, GAMMA, dt, KAPPA, a, nsteps)
+    got = run("euler_rk2", u0, nsteps, 32, "swept", (GAMMA, CFL, KAPPA))
+    assert np.array_equal(got[:4], ref)
+    assert np.array_equal(run("euler_rk2", u0, nsteps, 32, "persistent", (GAMMA, CFL, KAPPA)), got)
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_euler_kahan_2048_tile_32_full_grid_matches_oracle(oracle_lib, storage):
+    """The precision-form Euler benchmark's grid, tile and default launch
+    shape (binary32: unstaged; bfloat16: staged), all 12 planes against the
+    oracle after three half cycles and a tail."""
+    nsteps = 27
+    S = _euler_kahan_state(2048, 2048, storage, seed=2)
+    Uf = (oracle_lib.bf16_bits_to_f32(S[:4]) if storage == "bf16" else S[:4]).astype(np.float64)
+    a, dt = oracle_lib.euler_setup(Uf, GAMMA, CFL)
+    ref = oracle_lib.euler_kahan(S, GAMMA, dt, KAPPA, a, nsteps, storage)
+    got = run("euler_kahan", S, nsteps, 32, "swept", (GAMMA, CFL, KAPPA), dtype=storage)
+    assert np.array_equal(got, ref)
+
+
+def test_wave_1024_tile_32_full_grid_matches_oracle(oracle_lib):
+    """The wave benchmark's grid and tile: 53 steps (three half cycles and a
+    tail) against the oracle on every point."""
+    u0 = inputs.wave_source(1024, 1024)
+    ru, ro = oracle_lib.wave(u0[0], u0[1], 0.3 * 0.3, 53)
+    got = run("wave", u0, 53, 32, "swept", (0.3,))
+    assert np.array_equal(got[0], ru) and np.array_equal(got[1], ro)
+
+
 def test_device_tensors_in_and_out():
     u0 = torch.rand(1, 64, 64, dtype=torch.float64, device="cuda")
     with Swept2D(64, 64, op="heat", tile=16, params=(0.2,),
