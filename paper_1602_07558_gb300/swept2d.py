@@ -8,7 +8,7 @@ The names follow the C ABI in ``include/swept2d.h``::
 
     s = Swept2D(nx, ny, op="heat", tile=32, params=(0.2,), stream=torch_stream)
     s.set_state(u0)               # numpy array or torch tensor, (nvars, ny, nx)
-    s.advance(10_000)             # mode="swept" (default) or "naive"
+    s.advance(10_000)             # mode="swept" (default), "persistent" or "naive"
     u = s.get_state()             # numpy array (or fills a given tensor/array)
 """
 from __future__ import annotations
