@@ -437,7 +437,8 @@ def main():
             for s in filter(None, (sw, nv)):
                 s.set_state(state_dev)
                 s.advance(4 * w.tile // (2 if two_stage else 1),
-                          mode="swept" if s is sw else "naive")
+                          mode=("persistent" if args.persistent else "swept") if s is sw
+                          else "naive")
         torch.cuda.synchronize()
         print(json.dumps({"profile_case": True, "workload": w.describe, "grid": N,
                           "tile": w.tile}), flush=True)
