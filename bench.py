@@ -702,6 +702,10 @@ def run_batch(args, w, world, rank, local):
 
     import torch
     torch.cuda.set_device(local)
+    dist = None
+    if world > 1:                       # replicas: one batch per rank, max time over ranks
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
     from paper_1602_07558_gb300.autotune import autotune_batch
     from paper_1602_07558_gb300.swept2d import Swept2D, SweptBatch
     stream = torch.cuda.Stream()
@@ -719,6 +723,8 @@ def run_batch(args, w, world, rank, local):
         times, l0 = [], 0
         for i in range(wu + k):
             if i == wu:
+                if dist is not None:
+                    dist.barrier()
                 torch.cuda.synchronize()
                 l0 = b.query("launches")
             with torch.cuda.stream(stream):
@@ -730,6 +736,8 @@ def run_batch(args, w, world, rank, local):
             ev1.synchronize()
             if i >= wu:
                 times.append(ev0.elapsed_time(ev1))
+        if dist is not None:
+            dist.barrier()
         return statistics.mean(times), int(b.query("launches") - l0)
 
     with ClockSampler(local) as clocks:
@@ -773,8 +781,10 @@ def run_batch(args, w, world, rank, local):
                     ev1.synchronize()
                 loop_ms += ev0.elapsed_time(ev1)
                 loop_cells += nx[i] * ny[i]
-    value = world * cells * nsteps / (ms_sw * 1e-3) / 1e9
-    naive_value = world * cells * nsteps / (naive_ms * 1e-3) / 1e9 if naive_ms else None
+    ms_sw, value = aggregate_over_ranks(ms_sw, cells, nsteps, dist, "cuda")
+    naive_value = None
+    if naive_ms:
+        naive_ms, naive_value = aggregate_over_ranks(naive_ms, cells, nsteps, dist, "cuda")
     loop_value = loop_cells * nsteps / (loop_ms * 1e-3) / 1e9
     # error against FP64 on four sample grids (the GPU FP64 path of the same
     # update from the same values, bitwise the oracle in the parity tests)
@@ -832,6 +842,9 @@ def run_batch(args, w, world, rank, local):
                     "h2d_bytes_per_step": int(flat.nbytes), "d2h_bytes_per_step": int(flat.nbytes)},
             "gpu_launches": launches, "clocks": clocks.summary(),
         }), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
 
 
 if __name__ == "__main__":
