@@ -514,6 +514,11 @@ def main():
             rate, nsteps_cpu, secs, cores = cpu_oracle_rate(w, state_host, args.cpu_seconds)
             cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                    "sample": f"{N}x{N}, {nsteps_cpu} of {w.nsteps} steps ({secs:.1f} s)"}
+            if N <= 64:                  # the small grid: the single-core oracle too
+                import oracle
+                oracle.set_threads(1)
+                cpu["value_1core"] = cpu_oracle_rate(w, state_host, args.cpu_seconds / 4)[0]
+                oracle.set_threads(cores)
         naive_rf = None
         if nv is not None:
             nk = naive_kernel_ms(nv, state_dev, stream, w)

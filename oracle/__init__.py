@@ -88,6 +88,13 @@ def num_threads() -> int:
     return int(_load().oracle_num_threads())
 
 
+def set_threads(n: int) -> None:
+    """OpenMP threads of the following oracle calls (results do not change)."""
+    L = _load()
+    L.oracle_set_threads.argtypes = [ctypes.c_int]
+    L.oracle_set_threads(int(n))
+
+
 def _grid(u, dtype):
     a = np.ascontiguousarray(np.array(u, dtype=dtype, copy=True))
     if a.ndim != 2:

@@ -65,6 +65,16 @@ int oracle_num_threads(void) {
 #endif
 }
 
+/* OpenMP threads for the following calls (no result depends on it: every
+ * output point is written once from the previous sweep). */
+void oracle_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 /* ------------------------------------------------------------------------ heat
  * u_t = laplace(u), forward Euler with diffusion number r on the 5-point stencil:
  *     s = (u_E + u_S) + (u_W + u_N)
