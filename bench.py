@@ -270,9 +270,16 @@ def cpu_oracle_rate(w: Workload, state, seconds):
     workload's own step count; a workload shorter than that is repeated).
     Returns (Gcell-updates/s, steps per run, runs, seconds, threads)."""
     import oracle
-    t0 = time.perf_counter()
-    oracle_advance(w, state, 1)
-    t1 = max(time.perf_counter() - t0, 1e-6)
+    oracle_advance(w, state, 1)                # first call: library load, page faults
+    k = 1                                      # calibration: double until ~5% of the budget
+    while True:
+        t0 = time.perf_counter()
+        oracle_advance(w, state, k)
+        dt = time.perf_counter() - t0
+        if dt >= 0.05 * seconds or k >= w.nsteps:
+            break
+        k *= 2
+    t1 = max(dt / k, 1e-9)
     nsteps = max(1, min(w.nsteps, int(seconds / t1)))
     runs = max(1, int(seconds / (t1 * nsteps))) if nsteps == w.nsteps else 1
     t0 = time.perf_counter()
