@@ -1,0 +1,114 @@
+"""Model check of the persistent form's dependency rule (no GPU): an item of
+phase p on tile (I, J) starts once every tile of its periodic 3 x 3
+neighbourhood has finished phase p-1. Random interleavings of concurrent
+items (each a start event, reads at any time while it runs, and an end event
+that writes and releases) must never let an item read a panel slot that is not
+the version it needs, nor let a writer overwrite a slot that a running item
+still reads.
+
+Items (the launch-per-phase schedule of Algorithm 4 on one GPU, as work items):
+  phase 1            Up(I, J), frame 0: reads the state, writes up slot (I, J)
+  phase 2 + 2j       bridges of half cycle j: read up slots (I, J), (I, J+1),
+                     (I+1, J); write bridge slot (I, J)
+  phase 3 + 2j       octahedron (j < H-1) or final Down (j = H-1): read bridge
+                     slots (I, J), (I+1, J), (I, J+1); the octahedron writes up
+                     slot (I, J) for even j and (I+1, J+1) for odd j (its Up is
+                     in the shifted frame); the final Down writes the state of
+                     the four tiles its shifted tile overlaps (the first Ups
+                     read the state of their own tile).
+"""
+import random
+
+import pytest
+
+
+def items_of(T, Q, H):
+    out = []
+    wrap = lambda i, j: ((i % T), (j % Q))
+    for p in range(1, 2 * H + 2):
+        for J in range(Q):
+            for I in range(T):
+                reads, writes = [], []
+                if p == 1:
+                    reads.append(("st",) + wrap(I, J))
+                    writes.append(("up",) + wrap(I, J))
+                elif p % 2 == 0:
+                    j = (p - 2) // 2
+                    reads += [("up",) + wrap(I, J), ("up",) + wrap(I, J + 1), ("up",) + wrap(I + 1, J)]
+                    writes.append(("br",) + wrap(I, J))
+                else:
+                    j = (p - 3) // 2
+                    reads += [("br",) + wrap(I, J), ("br",) + wrap(I + 1, J), ("br",) + wrap(I, J + 1)]
+                    if j + 1 < H:
+                        writes.append(("up",) + (wrap(I, J) if j % 2 == 0 else wrap(I + 1, J + 1)))
+                    else:   # the final Down writes the state of the tile shifted by (h, h)
+                        writes += [("st",) + wrap(I + a, J + b) for a in (0, 1) for b in (0, 1)]
+                out.append((p, I, J, reads, writes))
+    return out
+
+
+def needed_version(p, kind):
+    """The phase whose write an item of phase p must read in a slot of `kind`
+    (the first Up reads the state as set, which no item has written)."""
+    return None if kind == "st" else p - 1
+
+
+def run_model(T, Q, H, rng):
+    items = items_of(T, Q, H)
+    done = {(I, J): 0 for J in range(Q) for I in range(T)}   # last finished phase per tile
+    version = {}                                               # slot -> phase of last write
+    pending = list(range(len(items)))
+    running = []
+    while pending or running:
+        ready = []
+        for k in pending:
+            p, I, J, _, _ = items[k]
+            if all(done[((I + di) % T, (J + dj) % Q)] >= p - 1
+                   for di in (-1, 0, 1) for dj in (-1, 0, 1)):
+                ready.append(k)
+        choices = [("start", k) for k in ready] + [("end", k) for k in running]
+        assert choices, "deadlock"
+        what, k = rng.choice(choices)
+        p, I, J, reads, writes = items[k]
+        if what == "start":
+            for slot in reads:
+                assert version.get(slot) == needed_version(p, slot[0]), (p, I, J, slot, version.get(slot))
+            pending.remove(k)
+            running.append(k)
+        else:
+            for slot in writes:
+                for r in running:
+                    if r != k:
+                        assert slot not in items[r][3], ("overwrite while read", items[k][:3], items[r][:3], slot)
+                version[slot] = p
+            running.remove(k)
+            done[(I, J)] = p
+
+
+@pytest.mark.parametrize("T,Q", [(1, 1), (2, 1), (2, 2), (3, 2), (4, 3), (5, 5)])
+@pytest.mark.parametrize("H", [1, 2, 3, 4])
+def test_neighbourhood_waits_order_every_panel_exchange(T, Q, H):
+    rng = random.Random(1000 * T + 10 * Q + H)
+    for _ in range(40):
+        run_model(T, Q, H, rng)
+
+
+def test_a_smaller_neighbourhood_is_not_enough():
+    """Waiting only for the tile itself (not its neighbours) lets an item read a
+    slot before its producer wrote it: the model detects it."""
+    rng = random.Random(7)
+    T, Q, H = 3, 3, 2
+    items = items_of(T, Q, H)
+    done = {(I, J): 0 for J in range(Q) for I in range(T)}
+    version, pending, failures = {}, list(range(len(items))), 0
+    while pending:
+        ready = [k for k in pending if done[(items[k][1], items[k][2])] >= items[k][0] - 1]
+        k = rng.choice(ready)
+        p, I, J, reads, writes = items[k]
+        if any(version.get(s) != needed_version(p, s[0]) for s in reads):
+            failures += 1
+        for s in writes:
+            version[s] = p
+        done[(I, J)] = p
+        pending.remove(k)
+    assert failures > 0
