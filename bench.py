@@ -424,7 +424,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
 
-    from paper_1602_07558_gb300.swept2d import Swept2D, measure_fp64_rate
+    from paper_1602_07558_gb300.swept2d import Swept2D, measure_peaks
 
     N = w.grid
     cells = N * N
@@ -503,7 +503,8 @@ def main():
     same = bool(np.array_equal(out_sw, nv.get_state())) if nv is not None else None
 
     # per-kernel CUDA-event timing on one more pass (not the headline timing)
-    fp64_rate = measure_fp64_rate(stream)
+    peaks = measure_peaks(stream)
+    fp64_rate = peaks["fp64_ops_per_s"]
     sw.set_timing(True)
     with torch.cuda.stream(stream):
         sw.set_state(state_dev)
@@ -571,6 +572,7 @@ def main():
             "swept_equals_naive_bitwise": same,
             "error_vs_fp64": errors,
             "roofline": rf,
+            "measured_rates": peaks,
             "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in kern.items()},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT,

@@ -200,7 +200,7 @@ int swept2d_query(const swept2d_t *h, int what, double *out);
 
 /* Launch shape of the swept kernels of a handle (a tuning knob, not a change
  * of results: every setting gives the same bits). threads: 64, 128, 256 or 512
- * per block (default 256; the persistent form takes at most 256). stage: 1 =
+ * per block (default 256; the persistent form also takes up to 512). stage: 1 =
  * the bridge and downward-pyramid blocks bring their whole input panel set
  * into shared memory with TMA bulk copies at block start; 0 = they copy every
  * level's strip or ring from device memory straight into its level buffer with
@@ -223,9 +223,22 @@ int swept2d_set_tuning(swept2d_t *h, int threads, int stage);
 int swept2d_set_timing(swept2d_t *h, int on);
 int swept2d_kernel_stats(swept2d_t *h, int kind, long long *launches, double *total_ms);
 
-/* Measured FP64 issue rate of this GPU: a kernel of independent fused
- * multiply-add chains on `stream`; writes lane-operations per second (one FMA
- * = one operation) to *ops_per_s. Used to state the FP64-pipe roofline. */
+/* Measured rates of this GPU for the roofline, each timed with CUDA events on
+ * `stream` (best of five launches after a warm-up), written to out[0..nout):
+ *   out[0]  FP64 lane-operations per second: the maximum over fused
+ *           multiply-add chains (4, 8 and 16 per thread) and add chains (8),
+ *           each at 2, 4 and 8 blocks of 256 threads per SM (one FMA = one
+ *           operation);
+ *   out[1]  FP32 lane-operations per second (16 fused multiply-add chains per
+ *           thread, 8 blocks of 256 threads per SM);
+ *   out[2]  shared-memory wavefronts per second: warp loads of 32 consecutive
+ *           4-byte words (one wavefront each, no bank conflict).
+ * nout >= 1; entries beyond 3 are left alone. Allocates a small device buffer
+ * for the kernels' results (freed before returning).
+ * Errors: EINVAL (out NULL or nout < 1), ENOMEM, ECUDA. */
+int swept2d_measure_peaks(void *stream, double *out, int nout);
+
+/* out[0] of swept2d_measure_peaks alone: the FP64 lane-operation rate. */
 int swept2d_measure_fp64_rate(void *stream, double *ops_per_s);
 
 /*
@@ -295,9 +308,11 @@ int swept2d_batch_query_grid(const swept2d_batch_t *b, int grid, int what, doubl
  * rounded up to 256 bytes; larger grids are rejected with SWEPT2D_EINVAL and a
  * message. Nothing in the scratch needs to start at zero.
  *
- * Set-up. The first call on each device looks up the device address of the
- * scratch array (cudaGetSymbolAddress, with that device current) and caches it;
- * make that first call before any stream capture begins.
+ * Set-up. Every call looks up the device address of the scratch array on the
+ * current device (cudaGetSymbolAddress; nothing is cached, so a device reset or
+ * another context on the same device is harmless). The first call on a device
+ * is also where the runtime loads this library's device code there; make that
+ * first call before any stream capture begins.
  *
  * Concurrency. All calls on a device share the one scratch array, and it keeps
  * the contents of the last call: calls whose work overlaps on the GPU (other

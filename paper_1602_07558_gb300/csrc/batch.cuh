@@ -225,7 +225,7 @@ struct BatchLaunch {
             return e;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        const long long nitems = (long long)ntiles * (2 * H + 1);
+        const long long nitems = persistent_items(ntiles, H);
         long long grid = (long long)(per_sm > 0 ? per_sm : 1) * nsm;
         if (grid > nitems) grid = nitems;
         batch_persistent_kernel<Op, STG><<<(int)grid, threads, sm, st>>>(

@@ -453,7 +453,7 @@ int swept2d_batch_advance(swept2d_batch_t *b, long long nsteps, int mode) {
             if (c.tune.threads > 256)
                 return bfail(b, SWEPT2D_EINVAL, "advance: the persistent form takes at most 256 threads");
             const long long H = nsteps * b->bt->nst / (c.n / 2);
-            if ((long long)c.tiles.size() * (2 * H + 1) >= (1LL << 31))
+            if (swept::persistent_items((long long)c.tiles.size(), H) >= (1LL << 31))
                 return bfail(b, SWEPT2D_EINVAL, "advance: too many work items for one persistent launch");
             if (!c.d_sched) {
                 cudaError_t e = cudaMalloc(&c.d_sched, (c.tiles.size() + 1) * sizeof(int));

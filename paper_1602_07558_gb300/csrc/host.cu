@@ -468,7 +468,7 @@ static int persistent_prepare(swept2d *h, long long H) {
         optin = 227 * 1024;
     if (h->ops->smem_for(h->n, h->tune.stage) > (size_t)optin)
         return fail(h, SWEPT2D_EINVAL, "advance: the persistent form's shared memory does not fit");
-    if ((long long)h->G.T * h->G.Q * (2 * H + 1) >= (1LL << 31))
+    if (swept::persistent_items((long long)h->G.T * h->G.Q, H) >= (1LL << 31))
         return fail(h, SWEPT2D_EINVAL, "advance: too many work items for one persistent launch");
     if (!h->sched) {
         cudaError_t e = cudaMalloc(&h->sched, ((size_t)h->G.T * h->G.Q + 1) * sizeof(int));
@@ -481,8 +481,8 @@ int swept2d_selftest_wait_timeout(swept2d_t *h, long long spin_limit) {
     if (!h) return SWEPT2D_EINVAL;
     if (h->n == 0) return fail(h, SWEPT2D_EINVAL, "selftest: needs a handle created with a tile");
     if (spin_limit < 1) return fail(h, SWEPT2D_EINVAL, "selftest: spin_limit < 1");
-    if (h->tune.threads > 256)
-        return fail(h, SWEPT2D_EINVAL, "selftest: the persistent form takes at most 256 threads");
+    if (h->tune.threads > h->ops->max_persistent_threads)
+        return fail(h, SWEPT2D_EINVAL, "selftest: the persistent form takes at most 512 threads per block");
     int rc = persistent_prepare(h, 1);
     if (rc) return rc;
     const int NT = h->G.T * h->G.Q;
@@ -519,8 +519,8 @@ int swept2d_advance(swept2d_t *h, long long nsteps, int mode) {
         return fail(h, SWEPT2D_EINVAL, "advance: swept mode needs a tile (created with tile 0)");
     if (persistent) {
         if (mode != SWEPT2D_SWEPT) return fail(h, SWEPT2D_EINVAL, "advance: persistent needs the swept mode");
-        if (h->tune.threads > 256)
-            return fail(h, SWEPT2D_EINVAL, "advance: the persistent form takes at most 256 threads");
+        if (h->tune.threads > h->ops->max_persistent_threads)
+            return fail(h, SWEPT2D_EINVAL, "advance: the persistent form takes at most 512 threads per block");
         const int rc = persistent_prepare(h, nsteps * h->nst / (h->n / 2));
         if (rc) return rc;
         mode |= persistent;

@@ -50,6 +50,10 @@ struct Geom {
 
 __host__ __device__ inline int panel_stride(int n) { return ((n * n / 2 + n) + 7) & ~7; }
 
+// Updates whose levels are computed in place in one level buffer.
+template <class Op>
+__host__ __device__ constexpr bool one_buffer() { return Op::INPLACE || Op::INPLACE_AFTER_AUX; }
+
 // Dynamic shared memory of a swept block: level buffers (+ aux planes), then
 // (when staged) the block's input panels, then an mbarrier.
 struct SmemPlan {
@@ -59,7 +63,7 @@ template <class Op>
 __host__ __device__ inline SmemPlan smem_plan(int n, int stage_segments, bool staged) {
     typedef typename Op::S S;
     const size_t P = (size_t)n + 2;
-    const size_t levels = (size_t)((Op::INPLACE ? 1 : 2) * Op::NV + Op::AUX) * P * P * sizeof(S);
+    const size_t levels = (size_t)((one_buffer<Op>() ? 1 : 2) * Op::NV + Op::AUX) * P * P * sizeof(S);
     SmemPlan pl;
     pl.stage_off = (levels + 15) & ~(size_t)15;
     const size_t stage = staged ? (size_t)stage_segments * Op::NV * panel_stride(n) * sizeof(S) : 0;
@@ -101,6 +105,10 @@ constexpr long long kSpinLimit = 1LL << 22;
 // far below the 128 a 512-thread block leaves each thread); the naive and the
 // persistent kernels take at most 256.
 constexpr int kMaxSweptThreads = 512;
+
+// Largest block of the persistent kernel (it needs no more registers a thread
+// than the launch-per-phase kernels).
+constexpr int kMaxPersistentThreads = 512;
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) {
     return (unsigned)__cvta_generic_to_shared(p);
@@ -270,9 +278,13 @@ __device__ __forceinline__ void compute_rect(const Op &op, int stage, u64 g,
 // and each point then needs s = Pr(x, y) + Pr(x-1, y-1) and two fused
 // multiply-adds (pass 2): about 4.1 FP64 operations per point instead of 5,
 // with the same roundings as HeatOp::operator() (the pair sums commute).
-__device__ __forceinline__ void compute_rect(const HeatOp &op, int, u64, const double *src,
-                                             double *dst, double *aux, int P, int x0, int y0,
-                                             int W, int H) {
+// Pass 2 reads only the centre and the pair sums, so it may write the level in
+// place (src == dst); `mid` runs after the barrier between the passes, when
+// no neighbour value of the level is read any more.
+template <class Mid>
+__device__ __forceinline__ void compute_rect_mid(const HeatOp &op, int, u64, const double *src,
+                                                 double *dst, double *aux, int P, int x0, int y0,
+                                                 int W, int H, Mid &&mid) {
     // (FP64-pipe bound: the per-point decode by reciprocal keeps independent
     // points per thread visible to the scheduler better than a carried walk)
     const int W1 = W + 1, cnt1 = W1 * (H + 1);
@@ -283,6 +295,7 @@ __device__ __forceinline__ void compute_rect(const HeatOp &op, int, u64, const d
         aux[off] = __dadd_rn(src[off + 1], src[off + P]);
     }
     __syncthreads();
+    mid();
     const int cnt = W * H;
     for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
         const int yy = div_small(e, rw), xx = e - yy * W;
@@ -435,10 +448,13 @@ __device__ __forceinline__ void compute_rect(const EulerKahanOp<SS> &op, int sta
 
 // Wave: the same pair-sum sharing as the heat update (pass 1 forms the
 // east+south pair sums of the rectangle grown by one into the aux plane), then
-// u' = (2u - u_old) + C^2 d, u_old' = u.
-__device__ __forceinline__ void compute_rect(const WaveOp &op, int, u64, const double *src,
-                                             double *dst, double *aux, int P, int x0, int y0,
-                                             int W, int H) {
+// u' = (2u - u_old) + C^2 d, u_old' = u. Pass 2 reads only the centre's two
+// values and the pair sums, so it may write the level in place; `mid` runs
+// between the passes.
+template <class Mid>
+__device__ __forceinline__ void compute_rect_mid(const WaveOp &op, int, u64, const double *src,
+                                                 double *dst, double *aux, int P, int x0, int y0,
+                                                 int W, int H, Mid &&mid) {
     const int plane = P * P;
     const int W1 = W + 1, cnt1 = W1 * (H + 1);
     const float rw1 = recip_small(W1), rw = recip_small(W);
@@ -448,14 +464,33 @@ __device__ __forceinline__ void compute_rect(const WaveOp &op, int, u64, const d
         aux[off] = __dadd_rn(src[off + 1], src[off + P]);
     }
     __syncthreads();
+    mid();
     const int cnt = W * H;
     for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
         const int yy = div_small(e, rw), xx = e - yy * W;
         const int off = (y0 + yy + 1) * P + (x0 + xx + 1);
-        const double c = src[off];
+        const double c = src[off], old = src[plane + off];
         const double d = __fma_rn(-4.0, c, __dadd_rn(aux[off], aux[off - P - 1]));
-        dst[off] = __fma_rn(op.C2, d, __dsub_rn(__dmul_rn(2.0, c), src[plane + off]));
+        dst[off] = __fma_rn(op.C2, d, __dsub_rn(__dmul_rn(2.0, c), old));
         dst[plane + off] = c;
+    }
+}
+
+// One level of a rectangle: level k+1 on [x0, x0+W) x [y0, y0+H) from level k
+// in `cur`, into `nxt` (the same buffer for in-place updates). `next` copies
+// the next level's ring or strip into `nxt`: for INPLACE_AFTER_AUX updates
+// after the level's first pass (it overwrites neighbour values that pass
+// reads), otherwise before the computation (the caller's prefetch).
+template <class Op, class Next>
+__device__ __forceinline__ void level_step(const Op &op, int stage, u64 g,
+                                           const typename Op::S *cur, typename Op::S *nxt,
+                                           typename Op::S *aux, int P,
+                                           int x0, int y0, int W, int H, Next &&next) {
+    if constexpr (Op::INPLACE_AFTER_AUX) {
+        compute_rect_mid(op, stage, g, cur, nxt, aux, P, x0, y0, W, H, next);
+    } else {
+        next();
+        compute_rect(op, stage, g, cur, nxt, aux, P, x0, y0, W, H);
     }
 }
 
@@ -585,11 +620,13 @@ __device__ __forceinline__ void up_body(const Op &op, const Geom &G, typename Op
         const S *cur = par ? buf1 : buf0;
         S *nxt = par ? buf0 : buf1;
         write_up_panels<S, Op::NV>(cur, P, G, k, up, slot);
-        if constexpr (Op::INPLACE) __syncthreads();   // panels read before the level is overwritten
+        // panels read before the level is overwritten (INPLACE_AFTER_AUX updates
+        // overwrite it only after the barrier between their two passes)
+        if constexpr (Op::INPLACE) __syncthreads();
         if (k + 1 < h) {
             const u64 g = g0 + k;
-            compute_rect(op, (int)(g % Op::NST), g, cur, nxt, aux, P, k + 1, k + 1,
-                         n - 2 * k - 2, n - 2 * k - 2);
+            level_step(op, (int)(g % Op::NST), g, cur, nxt, aux, P, k + 1, k + 1, n - 2 * k - 2,
+                       n - 2 * k - 2, [] {});
         }
         __syncthreads();
     }
@@ -603,7 +640,7 @@ __device__ __forceinline__ void up_tile(const Op &op, const Geom &G, const typen
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = G.n, P = n + 2, plane = P * P;
     S *buf0 = reinterpret_cast<S *>(smem_raw);
-    S *buf1 = Op::INPLACE ? buf0 : buf0 + Op::NV * plane;   // one buffer for in-place levels
+    S *buf1 = one_buffer<Op>() ? buf0 : buf0 + Op::NV * plane;   // one buffer for in-place levels
     S *aux = buf1 + Op::NV * plane;
     const size_t gplane = (size_t)G.nx * G.ny;
     const int x0 = o + I * n, y0 = o + J * n;
@@ -620,7 +657,8 @@ __device__ __forceinline__ void up_tile(const Op &op, const Geom &G, const typen
 }
 
 template <class Op>
-__global__ void __launch_bounds__(kMaxSweptThreads) up_kernel(Op op, Geom G, const typename Op::S *state,
+__global__ void __launch_bounds__(kMaxSweptThreads)
+up_kernel(Op op, Geom G, const typename Op::S *state,
                                                  typename Op::S *up, int o, u64 g0) {
     up_tile(op, G, state, up, o, g0, blockIdx.x, blockIdx.y);
 }
@@ -641,7 +679,7 @@ __device__ __forceinline__ void bridge_tile(const Op &op, const Geom &G, const t
     const int n = G.n, h = n / 2, P = n + 2, plane = P * P;
     S *bufs[2];
     bufs[0] = reinterpret_cast<S *>(smem_raw);
-    bufs[1] = Op::INPLACE ? bufs[0] : bufs[0] + NV * plane;   // one buffer for in-place levels
+    bufs[1] = one_buffer<Op>() ? bufs[0] : bufs[0] + NV * plane;   // one buffer for in-place levels
     S *aux = bufs[1] + NV * plane;
     const int slot = J * G.T + I;
     // low tile: Up(I,J); high tile: Up(I,J+1) or Up(I+1,J)
@@ -704,7 +742,7 @@ __device__ __forceinline__ void bridge_tile(const Op &op, const Geom &G, const t
     // level: strips of one parity never overlap, and no level's rectangle,
     // reads or panel reads touch a later level's strip, so the copies' latency
     // is paid once per tile instead of once per level
-    constexpr bool per_level = STG || Op::INPLACE;
+    constexpr bool per_level = STG || one_buffer<Op>();
     if constexpr (per_level) {
         load_strips(0, bufs[0]);
     } else {
@@ -733,18 +771,23 @@ __device__ __forceinline__ void bridge_tile(const Op &op, const Geom &G, const t
                 for (int v = 0; v < NV; ++v) dst[(size_t)v * G.PS] = src[v * plane];
             }
         }
-        if constexpr (Op::INPLACE) __syncthreads();   // panels read before the strip copy below
+        // panels read before the strip copy below (INPLACE_AFTER_AUX updates
+        // copy it only after the barrier between their two passes)
+        if constexpr (Op::INPLACE) __syncthreads();
         if (k + 1 < h) {
-            // the next strip lies outside the rectangle below; for in-place
-            // levels it overlaps the rectangle's outermost neighbours, whose
-            // planes read at neighbours keep their values between the levels
-            if constexpr (per_level) load_strips(k + 1, nxt);
+            // the next strip lies outside the rectangle below; it overlaps the
+            // rectangle's outermost neighbours: INPLACE updates keep the planes
+            // read there unchanged between the levels, INPLACE_AFTER_AUX ones
+            // copy the strip once those neighbours are read
+            auto next = [&] {
+                if constexpr (per_level) load_strips(k + 1, nxt);
+            };
             const u64 g = g0 + k;
             const int u0 = k + 1, uw = n - 2 * k - 2, w0 = h - k - 1, ww = 2 * k + 2;
             if (xb)
-                compute_rect(op, (int)(g % Op::NST), g, cur, nxt, aux, P, w0, u0, ww, uw);
+                level_step(op, (int)(g % Op::NST), g, cur, nxt, aux, P, w0, u0, ww, uw, next);
             else
-                compute_rect(op, (int)(g % Op::NST), g, cur, nxt, aux, P, u0, w0, uw, ww);
+                level_step(op, (int)(g % Op::NST), g, cur, nxt, aux, P, u0, w0, uw, ww, next);
             if constexpr (per_level && !STG) async_wait();
         }
         __syncthreads();
@@ -752,7 +795,8 @@ __device__ __forceinline__ void bridge_tile(const Op &op, const Geom &G, const t
 }
 
 template <class Op, bool STG>
-__global__ void __launch_bounds__(kMaxSweptThreads) bridge_kernel(Op op, Geom G, const typename Op::S *up,
+__global__ void __launch_bounds__(kMaxSweptThreads)
+bridge_kernel(Op op, Geom G, const typename Op::S *up,
                                                      typename Op::S *br, u64 g0, int *err) {
     bridge_tile<Op, STG>(op, G, up, br, g0, err, blockIdx.x, blockIdx.y, blockIdx.z == 1);
 }
@@ -825,7 +869,7 @@ __device__ __forceinline__ bool down_body(const Op &op, const Geom &G, unsigned 
     // once before the first level: rings of one parity never overlap and lie
     // outside every earlier level's square and reads, so the copies' latency
     // is paid once per tile
-    constexpr bool per_level = STG || Op::INPLACE;
+    constexpr bool per_level = STG || one_buffer<Op>();
     if constexpr (per_level) {
         load_ring(0, buf0);
     } else {
@@ -836,14 +880,17 @@ __device__ __forceinline__ bool down_body(const Op &op, const Geom &G, unsigned 
     for (int k = 0; k < h; ++k) {
         S *cur = (k & 1) ? buf1 : buf0;
         S *nxt = (k & 1) ? buf0 : buf1;
-        // the next ring lies outside the square below; for in-place levels it
-        // overlaps the square's outermost neighbours, whose planes read at
-        // neighbours keep their values between the levels
-        if constexpr (per_level)
-            if (k + 1 < h) load_ring(k + 1, nxt);
+        // the next ring lies outside the square below; it overlaps the square's
+        // outermost neighbours: INPLACE updates keep the planes read there
+        // unchanged between the levels, INPLACE_AFTER_AUX ones copy the ring
+        // once those neighbours are read
+        auto next = [&] {
+            if constexpr (per_level)
+                if (k + 1 < h) load_ring(k + 1, nxt);
+        };
         const u64 g = g0 + k;
-        compute_rect(op, (int)(g % Op::NST), g, cur, nxt, aux, P, h - k - 1, h - k - 1,
-                     2 * k + 2, 2 * k + 2);
+        level_step(op, (int)(g % Op::NST), g, cur, nxt, aux, P, h - k - 1, h - k - 1, 2 * k + 2,
+                   2 * k + 2, next);
         if constexpr (per_level && !STG) async_wait();
         __syncthreads();
     }
@@ -860,7 +907,7 @@ __device__ __forceinline__ void octahedron_tile(const Op &op, const Geom &G,
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = G.n, h = n / 2, P = n + 2, plane = P * P;
     S *buf0 = reinterpret_cast<S *>(smem_raw);
-    S *buf1 = Op::INPLACE ? buf0 : buf0 + Op::NV * plane;   // one buffer for in-place levels
+    S *buf1 = one_buffer<Op>() ? buf0 : buf0 + Op::NV * plane;   // one buffer for in-place levels
     S *aux = buf1 + Op::NV * plane;
     if (!down_body<Op, STG>(op, G, smem_raw, buf0, buf1, aux, P, br, g0, err, I, J)) return;
     // Down(I,J) in frame o+h is Up(I,J) of frame h when o = 0, and Up(I+1,J+1)
@@ -873,7 +920,8 @@ __device__ __forceinline__ void octahedron_tile(const Op &op, const Geom &G,
 }
 
 template <class Op, bool STG>
-__global__ void __launch_bounds__(kMaxSweptThreads) octahedron_kernel(Op op, Geom G, const typename Op::S *br,
+__global__ void __launch_bounds__(kMaxSweptThreads)
+octahedron_kernel(Op op, Geom G, const typename Op::S *br,
                                                          typename Op::S *up, int o, u64 g0,
                                                          int *err) {
     octahedron_tile<Op, STG>(op, G, br, up, o, g0, err, blockIdx.x, blockIdx.y);
@@ -888,7 +936,7 @@ __device__ __forceinline__ void down_tile(const Op &op, const Geom &G, const typ
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = G.n, h = n / 2, P = n + 2, plane = P * P;
     S *buf0 = reinterpret_cast<S *>(smem_raw);
-    S *buf1 = Op::INPLACE ? buf0 : buf0 + Op::NV * plane;   // one buffer for in-place levels
+    S *buf1 = one_buffer<Op>() ? buf0 : buf0 + Op::NV * plane;   // one buffer for in-place levels
     S *aux = buf1 + Op::NV * plane;
     if (!down_body<Op, STG>(op, G, smem_raw, buf0, buf1, aux, P, br, g0, err, I, J)) return;
     const S *fin = (h & 1) ? buf1 : buf0;
@@ -905,7 +953,8 @@ __device__ __forceinline__ void down_tile(const Op &op, const Geom &G, const typ
 }
 
 template <class Op, bool STG>
-__global__ void __launch_bounds__(kMaxSweptThreads) down_kernel(Op op, Geom G, const typename Op::S *br,
+__global__ void __launch_bounds__(kMaxSweptThreads)
+down_kernel(Op op, Geom G, const typename Op::S *br,
                                                    typename Op::S *state, int o, u64 g0, int *err) {
     down_tile<Op, STG>(op, G, br, state, o, g0, err, blockIdx.x, blockIdx.y);
 }
@@ -913,19 +962,22 @@ __global__ void __launch_bounds__(kMaxSweptThreads) down_kernel(Op op, Geom G, c
 // ------------------------------------------------------- persistent form
 // One launch runs a whole swept advance: resident blocks take work items from
 // an atomic queue in phase order (phase 1: every tile's first Up; then per half
-// cycle j a bridge item (both bridges of a slot) and an octahedron item per
-// tile, or the final Down items), and an item of phase p on tile t starts once
-// every tile of t's periodic 3 x 3 neighbourhood has finished phase p-1. That
-// neighbourhood holds every producer of the item's inputs and every reader of
-// the panels it overwrites (the frame shift moves a tile's panels by at most
-// one slot), so the kernel boundaries of the launch-per-phase schedule are
-// replaced by those waits. Items are taken in index order and every dependency
-// has a smaller index, so the lowest unfinished item can always run: no
-// deadlock, whatever number of blocks is resident. Panels written by one block
-// are read by another after an acquire of the writer's release (and, for the
-// TMA bulk copies of the staged form, a generic-to-async proxy fence); the
-// unstaged form's element copies are ordinary reads after that acquire. Waits
-// are bounded: on timeout the error word is set and the block stops.
+// cycle j the y- and x-bridge items of every tile, two items per tile, then an
+// octahedron item per tile, or the final Down items). Each tile has a counter
+// of its finished items, and an item of half cycle j on tile t starts once
+// every tile of t's periodic 3 x 3 neighbourhood has finished all its items of
+// the previous phase (count >= 1 + 3j for a bridge, 3 + 3j for an octahedron
+// or Down). That neighbourhood holds every producer of the item's inputs and
+// every reader of the panels it overwrites (the frame shift moves a tile's
+// panels by at most one slot), so the kernel boundaries of the
+// launch-per-phase schedule are replaced by those waits. Items are taken in
+// index order and every dependency has a smaller index, so the lowest
+// unfinished item can always run: no deadlock, whatever number of blocks is
+// resident. Panels written by one block are read by another after an acquire
+// of the writer's release (and, for the TMA bulk copies of the staged form, a
+// generic-to-async proxy fence); the unstaged form's element copies are
+// ordinary reads after that acquire. Waits are bounded: on timeout the error
+// word is set and the block stops.
 // A dependency is at most one work item away (tens of microseconds); the
 // default bound (about a second of 64 ns naps and polls) only catches a block
 // that never finishes.
@@ -941,8 +993,8 @@ __device__ __forceinline__ int ld_relaxed(const int *p) {
     asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ __forceinline__ void st_release(int *p, int v) {
-    asm volatile("st.release.gpu.global.s32 [%0], %1;\n" ::"l"(p), "r"(v) : "memory");
+__device__ __forceinline__ void add_release(int *p, int v) {
+    asm volatile("red.release.gpu.global.add.s32 [%0], %1;\n" ::"l"(p), "r"(v) : "memory");
 }
 
 // Where a work item's tile lives: its grid's geometry, the grid's offsets in
@@ -970,10 +1022,17 @@ struct OneGrid {
     }
 };
 
+// Work items of the persistent form for NT tiles and H half cycles: NT first
+// Ups, then per half cycle 2 NT bridge items (tile t, y- then x-bridge) and NT
+// octahedron or final Down items.
+__host__ __device__ inline long long persistent_items(long long NT, long long H) {
+    return NT * (1 + 3 * H);
+}
+
 // The work loop of the persistent form over NT tiles (all of one tile side n)
 // located by `at`. `first` is the first work item taken (0; a positive value
-// skips items, which only the wait-timeout self-test does: the skipped items'
-// phases are never released, so every wait runs out).
+// skips items, which only the wait-timeout self-test does: the skipped items
+// are never counted, so every wait runs out).
 template <class Op, bool STG, class Loc>
 __device__ __forceinline__ void persistent_loop(const Op &op, const Loc &at, int NT, int n,
                                                 typename Op::S *state, typename Op::S *upp,
@@ -981,7 +1040,7 @@ __device__ __forceinline__ void persistent_loop(const Op &op, const Loc &at, int
                                                 u64 g0, int *err, int first, long long spin_limit) {
     __shared__ int s_item, s_fail;
     const int h = n / 2;
-    const int nitems = NT * (2 * H + 1);
+    const int nitems = (int)persistent_items(NT, H);
     for (;;) {
         if (threadIdx.x == 0) {
             const int it = atomicAdd(queue, 1) + first;
@@ -991,12 +1050,32 @@ __device__ __forceinline__ void persistent_loop(const Op &op, const Loc &at, int
         __syncthreads();
         const int item = s_item;
         if (item >= nitems) return;
-        const int p = item / NT + 1, t = item - (p - 1) * NT;
+        // decode: kind 0 first Up, 1 bridge (xb: x-bridge), 2 octahedron or Down
+        int kind, t, j = 0, need = 0;
+        bool xb = false;
+        if (item < NT) {
+            kind = 0;
+            t = item;
+        } else {
+            const int r = item - NT;
+            j = r / (3 * NT);
+            const int q = r - j * 3 * NT;
+            if (q < 2 * NT) {
+                kind = 1;
+                t = q >> 1;
+                xb = (q & 1) != 0;
+                need = 1 + 3 * j;
+            } else {
+                kind = 2;
+                t = q - 2 * NT;
+                need = 3 + 3 * j;
+            }
+        }
         const TileAt w = at(t);
         const Geom &G = w.G;
         const int I = w.I, J = w.J;
         const Op opi = w.c ? Op(w.c) : op;
-        if (p > 1 && threadIdx.x < 32) {
+        if (kind != 0 && threadIdx.x < 32) {
             // lanes 0..8 wait for one tile each of the periodic 3 x 3 neighbourhood
             bool bad = false;
             if (threadIdx.x < 9) {
@@ -1005,7 +1084,7 @@ __device__ __forceinline__ void persistent_loop(const Op &op, const Loc &at, int
                 const int ii = I + di < 0 ? G.T - 1 : (I + di == G.T ? 0 : I + di);
                 const int *flag = stage + w.base + jj * G.T + ii;
                 long long it = 0;
-                while (ld_acquire(flag) < p - 1) {
+                while (ld_acquire(flag) < need) {
                     // give up after the bound, or at once when another block
                     // has already recorded a failure
                     if (++it > spin_limit || ((it & 255) == 0 && ld_relaxed(err) != 0)) {
@@ -1026,35 +1105,30 @@ __device__ __forceinline__ void persistent_loop(const Op &op, const Loc &at, int
         // the acquired panels are read next by bulk copies (the async proxy)
         if (threadIdx.x == 0) asm volatile("fence.proxy.async.global;\n" ::: "memory");
         typename Op::S *st = state + w.soff, *u = upp + w.poff, *b = br + w.poff;
-        if (p == 1) {
+        const u64 gj = g0 + (u64)j * h;
+        const int o = (j & 1) ? h : 0;
+        if (kind == 0) {
             up_tile(opi, G, st, u, 0, g0, I, J);
+        } else if (kind == 1) {                     // one bridge of half cycle j
+            bridge_tile<Op, STG>(opi, G, u, b, gj, err, I, J, xb);
+        } else if (j + 1 < H) {
+            octahedron_tile<Op, STG>(opi, G, b, u, o, gj, err, I, J);
         } else {
-            const int j = (p - 2) / 2;              // half cycle
-            const u64 gj = g0 + (u64)j * h;
-            const int o = (j & 1) ? h : 0;
-            if ((p & 1) == 0) {                     // bridges of half cycle j
-                bridge_tile<Op, STG>(opi, G, u, b, gj, err, I, J, false);
-                __syncthreads();
-                bridge_tile<Op, STG>(opi, G, u, b, gj, err, I, J, true);
-            } else if (j + 1 < H) {
-                octahedron_tile<Op, STG>(opi, G, b, u, o, gj, err, I, J);
-            } else {
-                down_tile<Op, STG>(opi, G, b, st, o, gj, err, I, J);
-            }
+            down_tile<Op, STG>(opi, G, b, st, o, gj, err, I, J);
         }
         // make this item's panel (and state) stores visible, to the generic and
-        // the async proxy, before the release of its phase; order this item's
+        // the async proxy, before the release of its count; order this item's
         // shared-memory accesses before the next item's bulk copies into it
         asm volatile("fence.proxy.async.global;\n" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         __threadfence();
         __syncthreads();
-        if (threadIdx.x == 0) st_release(stage + t, p);
+        if (threadIdx.x == 0) add_release(stage + t, 1);
     }
 }
 
 template <class Op, bool STG>
-__global__ void __launch_bounds__(256) persistent_kernel(Op op, Geom G, typename Op::S *state,
+__global__ void __launch_bounds__(kMaxPersistentThreads) persistent_kernel(Op op, Geom G, typename Op::S *state,
                                                          typename Op::S *upp, typename Op::S *br,
                                                          int *stage, int *queue, int H, u64 g0,
                                                          int *err, int first, long long spin_limit) {

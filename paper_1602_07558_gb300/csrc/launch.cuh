@@ -39,6 +39,8 @@ struct OpTable {
     cudaError_t (*persistent)(const Geom &, const double *c, void *state, void *up, void *br,
                               int *sched, int H, u64 g0, int *err, const Tuning &, int first,
                               long long spin_limit, cudaStream_t);
+    int max_threads;              // largest block of the launch-per-phase swept kernels
+    int max_persistent_threads;   // largest block of the persistent kernel
 };
 
 constexpr int kBlock = 256;
@@ -173,7 +175,7 @@ struct Launch {
             return e;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        const long long nitems = (long long)G.T * G.Q * (2 * H + 1);
+        const long long nitems = persistent_items((long long)G.T * G.Q, H);
         long long grid = (long long)(per_sm > 0 ? per_sm : 1) * nsm;
         if (grid > nitems) grid = nitems;
         const int NT = G.T * G.Q;
@@ -195,7 +197,8 @@ struct Launch {
     static const OpTable *table() {
         static const OpTable t = {Op::NV,      Op::NST,     (int)sizeof(S), &swept_smem_bytes<Op>,
                                   &naive,      &up,         &bridge,        &octahedron,
-                                  &down,       Op::STAGE,   &swept_smem_for<Op>, &persistent};
+                                  &down,       Op::STAGE,   &swept_smem_for<Op>, &persistent,
+                                  kMaxSweptThreads, kMaxPersistentThreads};
         return &t;
     }
 };

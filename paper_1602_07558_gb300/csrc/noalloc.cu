@@ -18,7 +18,6 @@
 
 #include <cstdio>
 #include <cstring>
-#include <mutex>
 
 #include "../../include/swept2d.h"
 #include "launch.cuh"
@@ -33,10 +32,6 @@ constexpr size_t kScratchBytes = SWEPT2D_STATIC_SCRATCH_BYTES;
 // call reads was written earlier in that same call.
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void *g_scratch_ptr[kMaxDevices] = {nullptr};
-
 void set_err(char *err, int errlen, const char *msg) {
     if (err && errlen > 0) {
         strncpy(err, msg, (size_t)errlen - 1);
@@ -47,31 +42,19 @@ void set_err(char *err, int errlen, const char *msg) {
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 // Device address of g_scratch on the current device. In host code the name
-// g_scratch is only a host-side stand-in, so the address is looked up once per
-// device (with that device current) and cached.
+// g_scratch is only a host-side stand-in, so the address is looked up on every
+// call, with the caller's device current: a cached address would outlive a
+// cudaDeviceReset or a switch to another context on the same device, after
+// which the module is loaded again at another address.
 int scratch_address(void **out, char *err, int errlen) {
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) {
-        set_err(err, errlen, cudaGetErrorString(e));
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+    if (e != cudaSuccess || !p) {
+        set_err(err, errlen, e != cudaSuccess ? cudaGetErrorString(e)
+                                              : "cudaGetSymbolAddress returned NULL");
         return SWEPT2D_ECUDA;
     }
-    if (dev < 0 || dev >= kMaxDevices) {
-        set_err(err, errlen, "device index out of range for the static scratch table");
-        return SWEPT2D_EINVAL;
-    }
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_ptr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_scratch);
-        if (e != cudaSuccess || !p) {
-            set_err(err, errlen, e != cudaSuccess ? cudaGetErrorString(e)
-                                                  : "cudaGetSymbolAddress returned NULL");
-            return SWEPT2D_ECUDA;
-        }
-        g_scratch_ptr[dev] = p;
-    }
-    *out = g_scratch_ptr[dev];
+    *out = p;
     return SWEPT2D_OK;
 }
 

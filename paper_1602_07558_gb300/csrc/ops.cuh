@@ -9,6 +9,12 @@
 //   INPLACE  every stage writes only planes that it reads at the centre point
 //            alone (never at a neighbour), so a level may be computed in place
 //            in a single level buffer
+//   INPLACE_AFTER_AUX  the level computation's first pass folds every
+//            neighbour value it needs into the aux planes and its second pass
+//            reads only the centre point and the aux planes, so the second
+//            pass may write the level in place (one level buffer); the next
+//            level's ring or strip may then be copied in only after the first
+//            pass (the neighbour values change from one level to the next)
 //   operator()(stage, g, a, out): a(dx, dy, v) reads value v of the neighbour at
 //            offset (dx, dy) in {-1,0,1}^2 at the level below; out[0..NV) is the
 //            new point state; g is the global sub-step index.
@@ -33,6 +39,7 @@ struct HeatOp {
     static constexpr int NV = 1, NST = 1, AUX = 1;
     static constexpr bool STAGE = false;
     static constexpr bool INPLACE = false;
+    static constexpr bool INPLACE_AFTER_AUX = true;
     double r;
     __host__ __device__ explicit HeatOp(const double *c) : r(c[0]) {}
     template <class A>
@@ -72,6 +79,7 @@ struct HeatKahanOp {
     // binary32 ones are copied straight into the level buffers (more blocks fit)
     static constexpr bool STAGE = sizeof(SS) == 2;
     static constexpr bool INPLACE = false;
+    static constexpr bool INPLACE_AFTER_AUX = false;
     float r;
     __host__ __device__ explicit HeatKahanOp(const double *c) : r((float)c[0]) {}
     // the update from the centre (u, c) and the four edge neighbours' u
@@ -110,6 +118,7 @@ struct EulerKahanOp {
     // each stage writes only planes it reads at the centre alone, so a
     // level can be computed in place in one level buffer
     static constexpr bool INPLACE = true;
+    static constexpr bool INPLACE_AFTER_AUX = false;
     float gm1, cx, cy, kax, kay, tau0, tau1;
     __host__ __device__ explicit EulerKahanOp(const double *c)
         : gm1((float)c[0]), cx((float)c[1]), cy((float)c[2]), kax((float)c[3]),
@@ -192,6 +201,7 @@ struct WaveOp {
     static constexpr int NV = 2, NST = 1, AUX = 1;   // aux: pair sums of a level
     static constexpr bool STAGE = false;
     static constexpr bool INPLACE = false;
+    static constexpr bool INPLACE_AFTER_AUX = true;
     double C2;
     __host__ __device__ explicit WaveOp(const double *c) : C2(c[0]) {}
     template <class A>
@@ -211,6 +221,7 @@ struct IncrementOp {
     static constexpr int NV = 1, NST = 1, AUX = 0;
     static constexpr bool STAGE = false;
     static constexpr bool INPLACE = false;
+    static constexpr bool INPLACE_AFTER_AUX = false;
     __host__ __device__ explicit IncrementOp(const double *) {}
     template <class A>
     __device__ __forceinline__ void operator()(int, u64, const A &a, S *out) const {
@@ -224,6 +235,7 @@ struct LevelTagOp {
     static constexpr int NV = 1, NST = 1, AUX = 0;
     static constexpr bool STAGE = false;
     static constexpr bool INPLACE = false;
+    static constexpr bool INPLACE_AFTER_AUX = false;
     __host__ __device__ explicit LevelTagOp(const double *) {}
     template <class A>
     __device__ __forceinline__ void operator()(int, u64, const A &a, S *out) const {
@@ -251,6 +263,7 @@ struct HashOp {
     static constexpr int NV = 1, NST = 1, AUX = 0;
     static constexpr bool STAGE = false;
     static constexpr bool INPLACE = false;
+    static constexpr bool INPLACE_AFTER_AUX = false;
     __host__ __device__ explicit HashOp(const double *) {}
     template <class A>
     __device__ __forceinline__ void operator()(int, u64 g, const A &a, S *out) const {
@@ -271,6 +284,7 @@ struct Wide2Op {
     static constexpr int NV = 5, NST = 2, AUX = 0;
     static constexpr bool STAGE = false;
     static constexpr bool INPLACE = false;
+    static constexpr bool INPLACE_AFTER_AUX = false;
     __host__ __device__ explicit Wide2Op(const double *) {}
     template <class A>
     __device__ __forceinline__ void operator()(int stage, u64, const A &a, S *out) const {
@@ -303,6 +317,7 @@ struct EulerOp {
     // each stage writes only planes it reads at the centre alone, so a
     // level can be computed in place in one level buffer
     static constexpr bool INPLACE = true;
+    static constexpr bool INPLACE_AFTER_AUX = false;
     double gm1, cx, cy, kax, kay, tau0, tau1;
     __host__ __device__ explicit EulerOp(const double *c)
         : gm1(c[0]), cx(c[1]), cy(c[2]), kax(c[3]), kay(c[4]), tau0(c[5]), tau1(c[6]) {}

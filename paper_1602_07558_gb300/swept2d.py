@@ -76,11 +76,12 @@ def lib():
         L.swept2d_set_tuning.argtypes = [vp, i, i]
         L.swept2d_kernel_stats.argtypes = [vp, i, ctypes.POINTER(ll), ctypes.POINTER(d)]
         L.swept2d_measure_fp64_rate.argtypes = [vp, ctypes.POINTER(d)]
+        L.swept2d_measure_peaks.argtypes = [vp, ctypes.POINTER(d), i]
         L.swept2d_selftest_wait_timeout.argtypes = [vp, ll]
         for name in ("swept2d_create", "swept2d_set_state", "swept2d_advance",
                      "swept2d_get_state", "swept2d_destroy", "swept2d_query",
                      "swept2d_set_timing", "swept2d_kernel_stats", "swept2d_measure_fp64_rate",
-                     "swept2d_set_tuning", "swept2d_selftest_wait_timeout"):
+                     "swept2d_measure_peaks", "swept2d_set_tuning", "swept2d_selftest_wait_timeout"):
             getattr(L, name).restype = i
         _lib = L
         return L
@@ -122,6 +123,17 @@ def measure_fp64_rate(stream=None) -> float:
     if rc != OK:
         raise SweptError(rc, "measure_fp64_rate failed")
     return out.value
+
+
+def measure_peaks(stream=None) -> dict:
+    """Measured rates of the current device: FP64 and FP32 lane-operations per
+    second and shared-memory wavefronts per second (swept2d_measure_peaks)."""
+    out = (ctypes.c_double * 3)()
+    rc = lib().swept2d_measure_peaks(_stream_handle(stream), out, 3)
+    if rc != OK:
+        raise SweptError(rc, "measure_peaks failed")
+    return {"fp64_ops_per_s": out[0], "fp32_ops_per_s": out[1],
+            "smem_wavefronts_per_s": out[2]}
 
 
 class Swept2D:

@@ -8,7 +8,11 @@ against the squares and rectangles each level computes and reads.
   later level's ring (strip) in the same buffer, and a bridge's panel reads
   of a level never see a later level's strip.
 * One buffer (in-place levels): the next level's ring (strip), copied during a
-  level, never lands in the square (rectangle) that level computes.
+  level, never lands in the square (rectangle) that level computes, and a
+  bridge's panel reads of a level see only that level's values (the rectangle
+  the previous level computed and the level's own strip). The updates whose
+  first pass reads the neighbours (heat, wave) copy the next ring only after
+  that pass, so the overlap with the current ring's inner line is harmless.
 """
 import pytest
 
@@ -101,3 +105,12 @@ def test_in_place_levels_copy_the_next_ring_outside_the_computed_points(n):
     for k in range(h - 1):
         assert not down_square(n, k) & down_ring(n, k + 1), (n, k)
         assert not bridge_rect(n, k) & bridge_strip(n, k + 1), (n, k)
+
+
+@pytest.mark.parametrize("n", SIZES)
+def test_in_place_bridge_panel_reads_see_only_the_current_level(n):
+    h = n // 2
+    for k in range(h):
+        have = bridge_strip(n, k) | (bridge_rect(n, k - 1) if k else set())
+        for xb in (0, 1):
+            assert bridge_panel_reads(n, k, xb) <= have, (n, k, xb)

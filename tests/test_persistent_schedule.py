@@ -1,21 +1,27 @@
-"""Model check of the persistent form's dependency rule (no GPU): an item of
-phase p on tile (I, J) starts once every tile of its periodic 3 x 3
-neighbourhood has finished phase p-1. Random interleavings of concurrent
-items (each a start event, reads at any time while it runs, and an end event
-that writes and releases) must never let an item read a panel slot that is not
-the version it needs, nor let a writer overwrite a slot that a running item
-still reads.
+"""Model check of the persistent form's dependency rule (no GPU). Every tile
+counts its finished work items; an item of half cycle j on tile (I, J) starts
+once every tile of its periodic 3 x 3 neighbourhood has finished all of its
+items of the previous phase (count >= 1 + 3j for a bridge item, >= 3 + 3j for
+an octahedron or final Down item). Random interleavings of concurrent items
+(each a start event, reads at any time while it runs, and an end event that
+writes and counts) must never let an item read a panel slot that is not the
+version it needs, nor let a writer overwrite a slot that a running item still
+reads.
 
-Items (the launch-per-phase schedule of Algorithm 4 on one GPU, as work items):
-  phase 1            Up(I, J), frame 0: reads the state, writes up slot (I, J)
-  phase 2 + 2j       bridges of half cycle j: read up slots (I, J), (I, J+1),
-                     (I+1, J); write bridge slot (I, J)
-  phase 3 + 2j       octahedron (j < H-1) or final Down (j = H-1): read bridge
-                     slots (I, J), (I+1, J), (I, J+1); the octahedron writes up
-                     slot (I, J) for even j and (I+1, J+1) for odd j (its Up is
-                     in the shifted frame); the final Down writes the state of
-                     the four tiles its shifted tile overlaps (the first Ups
-                     read the state of their own tile).
+Items (the launch-per-phase schedule of Algorithm 4 on one GPU, as work items;
+panel slots are per tile and side group):
+  first Up(I, J), frame 0: reads the state, writes up slot (I, J)
+  half cycle j, y-bridge(I, J): reads up (I, J) and (I, J+1), writes the
+                     bridge slot (I, J) W/E sides
+  half cycle j, x-bridge(I, J): reads up (I, J) and (I+1, J), writes the
+                     bridge slot (I, J) N/S sides
+  half cycle j, octahedron (j < H-1) or final Down (j = H-1): reads the W/E
+                     sides of bridge slots (I, J), (I+1, J) and the N/S sides of
+                     (I, J), (I, J+1); the octahedron writes up slot (I, J) for
+                     even j and (I+1, J+1) for odd j (its Up is in the shifted
+                     frame); the final Down writes the state of the four tiles
+                     its shifted tile overlaps (the first Ups read the state of
+                     their own tile).
 """
 import random
 
@@ -23,27 +29,34 @@ import pytest
 
 
 def items_of(T, Q, H):
+    """(phase, I, J, reads, writes, need) in the kernel's item order; phase
+    numbers the launch-per-phase schedule (1, then 2 + 2j bridges and 3 + 2j
+    octahedra) and `need` is the neighbourhood count the item waits for."""
     out = []
     wrap = lambda i, j: ((i % T), (j % Q))
-    for p in range(1, 2 * H + 2):
+    for J in range(Q):
+        for I in range(T):
+            out.append((1, I, J, [("st",) + wrap(I, J)], [("up",) + wrap(I, J)], 0))
+    for j in range(H):
         for J in range(Q):
             for I in range(T):
-                reads, writes = [], []
-                if p == 1:
-                    reads.append(("st",) + wrap(I, J))
-                    writes.append(("up",) + wrap(I, J))
-                elif p % 2 == 0:
-                    j = (p - 2) // 2
-                    reads += [("up",) + wrap(I, J), ("up",) + wrap(I, J + 1), ("up",) + wrap(I + 1, J)]
-                    writes.append(("br",) + wrap(I, J))
-                else:
-                    j = (p - 3) // 2
-                    reads += [("br",) + wrap(I, J), ("br",) + wrap(I + 1, J), ("br",) + wrap(I, J + 1)]
-                    if j + 1 < H:
-                        writes.append(("up",) + (wrap(I, J) if j % 2 == 0 else wrap(I + 1, J + 1)))
-                    else:   # the final Down writes the state of the tile shifted by (h, h)
-                        writes += [("st",) + wrap(I + a, J + b) for a in (0, 1) for b in (0, 1)]
-                out.append((p, I, J, reads, writes))
+                for xb in (False, True):
+                    if xb:
+                        reads = [("up",) + wrap(I, J), ("up",) + wrap(I + 1, J)]
+                        writes = [("brNS",) + wrap(I, J)]
+                    else:
+                        reads = [("up",) + wrap(I, J), ("up",) + wrap(I, J + 1)]
+                        writes = [("brWE",) + wrap(I, J)]
+                    out.append((2 + 2 * j, I, J, reads, writes, 1 + 3 * j))
+        for J in range(Q):
+            for I in range(T):
+                reads = [("brWE",) + wrap(I, J), ("brWE",) + wrap(I + 1, J),
+                         ("brNS",) + wrap(I, J), ("brNS",) + wrap(I, J + 1)]
+                if j + 1 < H:
+                    writes = [("up",) + (wrap(I, J) if j % 2 == 0 else wrap(I + 1, J + 1))]
+                else:   # the final Down writes the state of the tile shifted by (h, h)
+                    writes = [("st",) + wrap(I + a, J + b) for a in (0, 1) for b in (0, 1)]
+                out.append((3 + 2 * j, I, J, reads, writes, 3 + 3 * j))
     return out
 
 
@@ -55,21 +68,21 @@ def needed_version(p, kind):
 
 def run_model(T, Q, H, rng):
     items = items_of(T, Q, H)
-    done = {(I, J): 0 for J in range(Q) for I in range(T)}   # last finished phase per tile
+    done = {(I, J): 0 for J in range(Q) for I in range(T)}   # finished items per tile
     version = {}                                               # slot -> phase of last write
     pending = list(range(len(items)))
     running = []
     while pending or running:
         ready = []
         for k in pending:
-            p, I, J, _, _ = items[k]
-            if all(done[((I + di) % T, (J + dj) % Q)] >= p - 1
+            p, I, J, _, _, need = items[k]
+            if all(done[((I + di) % T, (J + dj) % Q)] >= need
                    for di in (-1, 0, 1) for dj in (-1, 0, 1)):
                 ready.append(k)
         choices = [("start", k) for k in ready] + [("end", k) for k in running]
         assert choices, "deadlock"
         what, k = rng.choice(choices)
-        p, I, J, reads, writes = items[k]
+        p, I, J, reads, writes, _ = items[k]
         if what == "start":
             for slot in reads:
                 assert version.get(slot) == needed_version(p, slot[0]), (p, I, J, slot, version.get(slot))
@@ -82,7 +95,21 @@ def run_model(T, Q, H, rng):
                         assert slot not in items[r][3], ("overwrite while read", items[k][:3], items[r][:3], slot)
                 version[slot] = p
             running.remove(k)
-            done[(I, J)] = p
+            done[(I, J)] += 1
+
+
+def test_item_counts_and_needs_follow_the_kernel_layout():
+    """NT (1 + 3H) items; a tile's count after its first Up is 1, after the
+    bridges of half cycle j it is 3 + 3j, after the octahedron 4 + 3j."""
+    T, Q, H = 3, 2, 4
+    items = items_of(T, Q, H)
+    assert len(items) == T * Q * (1 + 3 * H)
+    per_tile = {}
+    for p, I, J, _, _, need in items:
+        per_tile.setdefault((I, J), []).append(need)
+    for needs in per_tile.values():
+        # the count a tile has reached when it starts each of its items
+        assert needs == [0] + sum(([1 + 3 * j, 1 + 3 * j, 3 + 3 * j] for j in range(H)), [])
 
 
 @pytest.mark.parametrize("T,Q", [(1, 1), (2, 1), (2, 2), (3, 2), (4, 3), (5, 5)])
@@ -102,13 +129,13 @@ def test_a_smaller_neighbourhood_is_not_enough():
     done = {(I, J): 0 for J in range(Q) for I in range(T)}
     version, pending, failures = {}, list(range(len(items))), 0
     while pending:
-        ready = [k for k in pending if done[(items[k][1], items[k][2])] >= items[k][0] - 1]
+        ready = [k for k in pending if done[(items[k][1], items[k][2])] >= items[k][5]]
         k = rng.choice(ready)
-        p, I, J, reads, writes = items[k]
+        p, I, J, reads, writes, _ = items[k]
         if any(version.get(s) != needed_version(p, s[0]) for s in reads):
             failures += 1
         for s in writes:
             version[s] = p
-        done[(I, J)] = p
+        done[(I, J)] += 1
         pending.remove(k)
     assert failures > 0

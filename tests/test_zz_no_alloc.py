@@ -60,6 +60,28 @@ def test_static_entry_point_equals_handle_path_on_two_calls_in_a_row():
         assert np.array_equal(d_in.cpu().numpy(), u0)          # input left as it was
 
 
+@pytest.mark.parametrize("nx,ny,tile,nsteps,seed", [
+    (64, 64, 16, 5, 2),     # fewer steps than a half cycle, odd naive count
+    (64, 64, 16, 6, 3),     # fewer steps than a half cycle, even naive count
+    (64, 64, 16, 0, 4),     # no step: a plain copy
+    (48, 32, 16, 8, 5),     # exactly one half cycle, no tail
+])
+def test_static_entry_point_short_advances_equal_handle_path(nx, ny, tile, nsteps, seed):
+    """Step counts below one half cycle run only the naive kernel, ping-ponging
+    through the scratch so that the last sub-step lands in u_out; zero steps
+    copy u_in. Each must equal the handle path bit for bit."""
+    stream = torch.cuda.Stream()
+    u0 = inputs.uniform(nx, ny, seed=seed)
+    d_in = torch.from_numpy(u0).to("cuda")
+    d_out = torch.full_like(d_in, float("nan"))
+    torch.cuda.synchronize()
+    rc, msg = call_static(d_in, d_out, nx, ny, tile, 0.2, nsteps, stream)
+    assert rc == swept2d.OK, msg
+    stream.synchronize()
+    assert np.array_equal(d_out.cpu().numpy(), handle_path(u0, tile, 0.2, nsteps))
+    assert np.array_equal(d_in.cpu().numpy(), u0)
+
+
 def test_static_entry_point_rejects_grids_beyond_its_scratch():
     """4096 x 4096 with tile 32 needs about 570 MB of panels, far above the
     static scratch: the call must refuse before touching the device."""
