@@ -7,7 +7,7 @@ path beside it), printing one JSON line (rank 0).
                               batch1024_euler]
 
 The default workload is the headline one: 2D heat, periodic 4096 x 4096 FP64,
-r = 0.2, 10,000 steps, smooth 32-mode initial field, tile 32. One bench step =
+r = 0.2, 10,000 steps, smooth 32-mode initial field, tile 64 (512 threads). One bench step =
 one pass of the whole hot path over the workload: reset the device state from a
 resident copy of the initial field (device to device) and advance all steps.
 
@@ -65,23 +65,15 @@ class Workload:
     init: str
     seed: int
     describe: str = ""
-    # algorithmic FP64 pipe operations per point and sub-step (0 = not an FP64-pipe
-    # workload): heat 4 (one own pair sum, one sum, two fused multiply-adds);
-    # wave 6 (the same Laplacian, 2u - u_old, one fused multiply-add); Euler 64
-    # per stage (one evaluation of each point's fluxes, 16 with the division
-    # counted as one, shared by its 4 neighbours, and 12 per conserved variable)
-    fp64_ops: int = 0
+    threads: int = 0                 # swept threads per block (0: the library's default)
     extra: dict = field(default_factory=dict)
 
 
-# Algorithmic FP64 operations of one heat update: the east+south pair sum of a
-# point is the west+north pair sum of its south-east neighbour, so a point needs
-# one pair sum of its own, one sum and two fused multiply-adds.
 WORKLOADS = {
-    "heat4096": Workload("heat", "f64", 4096, 10_000, 32, (0.2,), "smooth", 1,
-                         "heat 4096x4096 FP64 r=0.2, 10000 steps, 32-mode smooth field", 4),
+    "heat4096": Workload("heat", "f64", 4096, 10_000, 64, (0.2,), "smooth", 1,
+                         "heat 4096x4096 FP64 r=0.2, 10000 steps, 32-mode smooth field", 512),
     "heat64": Workload("heat", "f64", 64, 512, 16, (0.2,), "uniform", 0,
-                       "heat 64x64 FP64 r=0.2, 512 steps, U[0,1) field (seed 0)", 4),
+                       "heat 64x64 FP64 r=0.2, 512 steps, U[0,1) field (seed 0)"),
     "heat2048_f32": Workload("heat_kahan", "f32", 2048, 100_000, 64, (0.2,), "smooth", 1,
                              "heat 2048x2048, binary32 storage and arithmetic, Kahan-"
                              "compensated update, r=0.2, 100000 steps"),
@@ -89,7 +81,7 @@ WORKLOADS = {
                               "heat 2048x2048, bfloat16 storage, binary32 arithmetic, Kahan-"
                               "compensated update, r=0.2, 100000 steps"),
     "euler2048": Workload("euler_rk2", "f64", 2048, 5_000, 32, (GAMMA, CFL, KAPPA), "euler", 2,
-                          "Euler 2048x2048 FP64, midpoint RK2, CFL 0.3, 5000 steps", 64),
+                          "Euler 2048x2048 FP64, midpoint RK2, CFL 0.3, 5000 steps"),
     "euler2048_f32": Workload("euler_kahan", "f32", 2048, 5_000, 32, (GAMMA, CFL, KAPPA),
                               "euler", 2, "Euler 2048x2048, binary32 storage and arithmetic, "
                               "Kahan-compensated update, midpoint RK2, CFL 0.3, 5000 steps"),
@@ -108,7 +100,7 @@ WORKLOADS = {
                                 "time step, 2000 steps"),
     "wave1024": Workload("wave", "f64", 1024, 10_000, 32, (0.3,), "source", 0,
                          "wave 1024x1024 FP64 leapfrog, Courant 0.3, Gaussian source at the "
-                         "centre, 10000 steps", 6),
+                         "centre, 10000 steps"),
 }
 
 
@@ -125,6 +117,8 @@ def parse():
     p.add_argument("--no-naive", action="store_true", help="skip the naive comparison arm")
     p.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--quick-check", action="store_true",
+                   help="compare with the oracle after 53 steps (20 for Euler), not all steps")
     p.add_argument("--profile-case", action="store_true",
                    help="short run of the same grid for ncu captures (no timing claims)")
     p.add_argument("--threads", type=int, default=None, help="swept threads per block")
@@ -358,15 +352,77 @@ def bridge_updates(n):
 # launch by its number of tiles (reads equal the algorithmic panel bytes there;
 # part of the writes is still in L2 when the kernel ends). Kernels without a
 # capture of their current version report None.
-OCT_TRAFFIC_PER_TILE = {
-    ("heat", "f64", 32): (71.499264e6 + 29.265152e6) / 4096,
-    ("euler_kahan", "f32", 32): (427.939072e6 + 380.31488e6) / 4096,
+OCT_TRAFFIC_PER_TILE = {}
+
+# Algorithmic work of one point update (one point advanced one sub-step),
+# counted from the update formulas (a fused multiply-add or a division is one
+# operation): FP64 operations, binary32 operations, and level-buffer accesses
+# (every stored value the sub-step reads, read once, and every value it writes,
+# written once: the shared-memory traffic of a walk that keeps each point's
+# neighbours in registers).
+#   heat FP64: own east+south pair sum, the sum of two pair sums, two FMAs = 4;
+#     reads u, writes u = 2 accesses
+#   wave FP64: the same Laplacian (3), 2u, 2u - u_old, one FMA = 6; reads and
+#     writes (u, u_old) = 4
+#   Euler FP64, per stage: one point's fluxes 15 (shared by its neighbours: 1/r,
+#     u, v, ke 3, p 2, E+p, F and G 6), per conserved variable 12 = 63; stage 0
+#     reads U writes U*, stage 1 reads U* and U writes U: 10 on average
+#   heat binary32 + Kahan: 2 pair sums, sum, FMA, r d, - c, u + y, (u' - u) - y
+#     = 9; reads and writes (u, c) = 4
+#   Euler binary32 + Kahan: fluxes 15 and 12 per variable in stage 0, 16 per
+#     variable in stage 1 (compensated update): 71 on average; stage 0 reads U
+#     writes U*, stage 1 reads U*, U, C writes U, C: 14 on average
+WORK = {
+    ("heat", "f64"): (4, 0, 2),
+    ("wave", "f64"): (6, 0, 4),
+    ("euler_rk2", "f64"): (63, 0, 10),
+    ("heat_kahan", "f32"): (0, 9, 4),
+    ("heat_kahan", "bf16"): (0, 9, 4),
+    ("euler_kahan", "f32"): (0, 71, 14),
+    ("euler_kahan", "bf16"): (0, 71, 14),
 }
 
 
-def roofline(w: Workload, kern, fp64_rate, esize, nvars):
-    """Roofline of the dominant swept kernel (the octahedron): the slower of the
-    FP64-pipe bound and the HBM bound on its algorithmic work per launch."""
+def hbm_peak():
+    """(GB/s, source): MEASURED_PEAKS.json's copy rate, else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs (copy test)"
+    except (OSError, ValueError, KeyError):
+        return HBM_PEAK_GBPS, "fallback 6779.7 GB/s (an earlier copy test on this pool)"
+
+
+def bounds(w, esize, upd, hbm_bytes, seconds, peaks):
+    """The slowest of the HBM, FP64, FP32 and shared-memory bounds for `upd`
+    point updates moving `hbm_bytes` that took `seconds`."""
+    fp64, fp32, acc = WORK.get((w.op, w.dtype), (0, 0, 0))
+    wavefronts = acc * upd * max(1, esize // 4) / 32.0    # a warp access: 1 wavefront per 128 B
+    hbm_gbs, hbm_src = hbm_peak()
+    rows = {
+        "hbm": (hbm_bytes / (hbm_gbs * 1e9), hbm_bytes / seconds / 1e9, hbm_gbs, "GB/s", hbm_src),
+        "fp64": (fp64 * upd / peaks["fp64_ops_per_s"], fp64 * upd / seconds / 1e9,
+                 peaks["fp64_ops_per_s"] / 1e9, "Gop/s (FP64 pipe)",
+                 "measured in this run (FP64 FMA and add chains, maximum)"),
+        "fp32": (fp32 * upd / peaks["fp32_ops_per_s"], fp32 * upd / seconds / 1e9,
+                 peaks["fp32_ops_per_s"] / 1e9, "Gop/s (FP32 pipe)",
+                 "measured in this run (FP32 FMA chains)"),
+        "smem": (wavefronts / peaks["smem_wavefronts_per_s"], wavefronts / seconds / 1e9,
+                 peaks["smem_wavefronts_per_s"] / 1e9, "G wavefronts/s (shared memory)",
+                 "measured in this run (conflict-free 4-byte loads)"),
+    }
+    bound = max(rows, key=lambda k: rows[k][0])
+    t, achieved, peak, unit, src = rows[bound]
+    return {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+            "frac": t / seconds, "peak_source": src,
+            "per_update": {"fp64_ops": fp64, "fp32_ops": fp32, "smem_accesses": acc,
+                           "hbm_bytes": hbm_bytes / upd if upd else None},
+            "all_bounds_frac": {k: v[0] / seconds for k, v in rows.items()}}
+
+
+def roofline(w, kern, peaks, esize, nvars):
+    """Roofline of the dominant swept kernel (the octahedron): its algorithmic
+    work per launch over its CUDA-event launch time against the slowest of the
+    HBM, FP64, FP32 and shared-memory bounds; the bridge's beside it."""
     n, N = w.tile, w.grid
     tiles = (N // n) ** 2
     launches, ms = kern["octahedron"]
@@ -382,22 +438,13 @@ def roofline(w: Workload, kern, fp64_rate, esize, nvars):
            "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the same "
                               "kernel at 2048x2048 (4096 tiles), scaled by tiles")
            if per_tile else None}
-    t_hbm = hbm_bytes / (HBM_PEAK_GBPS * 1e9)
-    if w.fp64_ops:
-        t_alu = w.fp64_ops * upd / fp64_rate
-    else:
-        t_alu = 0.0
-    if t_alu >= t_hbm:
-        achieved = w.fp64_ops * upd / (avg_ms * 1e-3) / 1e9
-        peak = fp64_rate / 1e9
-        out.update({"bound": "alu", "unit": "Gop/s (FP64 pipe)", "achieved": achieved,
-                    "peak": peak, "frac": achieved / peak, "ops_per_update": w.fp64_ops,
-                    "peak_source": "measured in this run (FP64 FMA chains)"})
-    else:
-        achieved = hbm_bytes / (avg_ms * 1e-3) / 1e9
-        out.update({"bound": "hbm", "unit": "GB/s", "achieved": achieved, "peak": HBM_PEAK_GBPS,
-                    "frac": achieved / HBM_PEAK_GBPS,
-                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy test)"})
+    out.update(bounds(w, esize, upd, hbm_bytes, avg_ms * 1e-3, peaks))
+    bl, bms = kern["bridge"]
+    if bl:
+        bupd = 2 * bridge_updates(n) * tiles
+        b = bounds(w, esize, bupd, hbm_bytes, bms / bl * 1e-3, peaks)
+        out["bridge"] = {"avg_launch_ms": bms / bl, "updates_per_launch": bupd,
+                         "bound": b["bound"], "frac": b["frac"]}
     return out
 
 
@@ -445,6 +492,8 @@ def main():
             N, N, w.op, w.params, dtype=w.dtype, state=state_dev, stream=stream)
         args.stage = int(stage)
     sw = mk(w.tile)
+    if args.threads is None and w.threads:
+        args.threads = w.threads
     if args.threads is not None or args.stage is not None:
         sw.set_tuning(args.threads or int(sw.query("threads")),
                       bool(args.stage) if args.stage is not None else bool(sw.query("stage")))
@@ -504,18 +553,18 @@ def main():
 
     # per-kernel CUDA-event timing on one more pass (not the headline timing)
     peaks = measure_peaks(stream)
-    fp64_rate = peaks["fp64_ops_per_s"]
     sw.set_timing(True)
     with torch.cuda.stream(stream):
         sw.set_state(state_dev)
         sw.advance(w.nsteps, mode="swept")
     kern = {k: sw.kernel_stats(k) for k in ("up", "bridge", "octahedron", "down", "naive")}
     sw.set_timing(False)
-    rf = roofline(w, kern, fp64_rate, esize, nvars)
+    rf = roofline(w, kern, peaks, esize, nvars)
 
     result = None
     if rank == 0:
-        errors = accuracy_report(w, sw, state_host, state_dev, out_sw, stream, Swept2D)
+        errors = accuracy_report(w, sw, state_host, state_dev, out_sw, stream, Swept2D,
+                                 full=not args.quick_check)
         h_in = torch.from_numpy(state_host.copy()).pin_memory()
         h_out = torch.empty_like(h_in).pin_memory()
         e2e_t = []
@@ -543,17 +592,8 @@ def main():
         naive_rf = None
         if nv is not None:
             nk = naive_kernel_ms(nv, state_dev, stream, w)
-            naive_rf = {"avg_launch_ms": nk,
-                        "hbm_GBps_at_2_state_copies_per_update":
-                            2 * nvars * esize * cells / (nk * 1e-3) / 1e9}
-            if w.fp64_ops:
-                ach = w.fp64_ops * cells / (nk * 1e-3) / 1e9
-                naive_rf.update({"bound": "alu", "unit": "Gop/s (FP64 pipe)", "achieved": ach,
-                                 "peak": fp64_rate / 1e9, "frac": ach / (fp64_rate / 1e9)})
-            else:
-                ach = 2 * nvars * esize * cells / (nk * 1e-3) / 1e9
-                naive_rf.update({"bound": "hbm", "unit": "GB/s", "achieved": ach,
-                                 "peak": HBM_PEAK_GBPS, "frac": ach / HBM_PEAK_GBPS})
+            naive_rf = {"avg_launch_ms": nk}
+            naive_rf.update(bounds(w, esize, cells, 2 * nvars * esize * cells, nk * 1e-3, peaks))
         result = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_sw,
@@ -589,60 +629,83 @@ def main():
         print(json.dumps(result), flush=True)
 
 
-def accuracy_report(w, sw, state_host, state_dev, out_sw, stream, Swept2D):
-    """Error against FP64. For the FP64 workloads: the swept result against the
-    oracle on a sample (every point of the full grid after 53 steps; the 64x64
-    case in full). For the reduced-precision forms: the final state of the
-    timed run against the FP64 solution from the same initial field, computed
-    by the GPU FP64 path (bitwise equal to the oracle in the parity tests), plus
-    a bitwise check of the precision path itself against its oracle."""
+def rel_errors(got, ref, u0):
+    """max |a - b| / max(max|b|, max|u0|) and ||a - b||_2 / ||b||_2 (the first
+    stays meaningful where the solution has decayed to rounding noise)."""
+    denom = max(float(np.max(np.abs(ref))), float(np.max(np.abs(u0))))
+    d = got - ref
+    return float(np.max(np.abs(d)) / denom), float(np.linalg.norm(d) / max(np.linalg.norm(ref), 1e-300))
+
+
+def fp64_oracle_of(w, state_host):
+    """Initial state of the FP64 oracle run that a reduced-precision workload
+    is compared with (its stored values, exactly, in binary64)."""
+    if w.op == "heat_kahan":
+        return storage_to_f64(state_host[:1], w.dtype)
+    U0 = storage_to_f64(state_host[:4], w.dtype)
+    return np.concatenate([U0, U0])
+
+
+def accuracy_report(w, sw, state_host, state_dev, out_sw, stream, Swept2D, full=True):
+    """Error against FP64, on the final state of the timed run (all of the
+    workload's steps) against the CPU oracle run over the same steps from the
+    same initial values: for the FP64 workloads whether every point is equal
+    to the oracle's, and the max-norm and L2 errors; for the reduced-precision
+    forms the same errors against the FP64 oracle (the Euler form compares the
+    four conserved variables), plus a bitwise check of the precision path
+    itself against its own oracle after a few steps. With full=False the FP64
+    comparison is made after 53 steps (20 for Euler) instead."""
     import torch
     N = w.grid
     rep = {}
-    nchk = 20 if w.op in ("euler_rk2", "euler_kahan") else 53
-    with torch.cuda.stream(stream):
-        sw.set_state(state_dev)
-        sw.advance(nchk)
-    got = sw.get_state()
-    ref = oracle_advance(w, state_host, nchk)
-    if w.op == "euler_rk2":
-        got = got[:4]
-    rep[f"vs_oracle_{N}x{N}_{nchk}_steps_max_abs"] = float(np.max(np.abs(
-        storage_to_f64(got, w.dtype) - storage_to_f64(ref, w.dtype))))
-    if w.op == "heat_kahan":
-        u0 = storage_to_f64(state_host[0], w.dtype)
-        with Swept2D(N, N, op="heat", tile=w.tile, params=w.params, stream=stream) as f64:
-            f64.set_state(np.ascontiguousarray(u0[None]))
-            f64.advance(w.nsteps)
-            ref64 = f64.get_state()[0]
-        u = storage_to_f64(out_sw[0], w.dtype)
-        c = storage_to_f64(out_sw[1], w.dtype)
-        denom = max(np.max(np.abs(ref64)), np.max(np.abs(u0)))
-        rep.update({
-            "fp64_reference": f"GPU FP64 heat path, {w.nsteps} steps from the same initial field",
-            "u_max_rel": float(np.max(np.abs(u - ref64)) / denom),
-            "u_l2_rel": float(np.linalg.norm(u - ref64) / np.linalg.norm(ref64)),
-            "u_minus_c_max_rel": float(np.max(np.abs((u - c) - ref64)) / denom),
-        })
-    if w.op == "euler_kahan":
-        U0 = storage_to_f64(state_host[:4], w.dtype)
-        with Swept2D(N, N, op="euler_rk2", tile=w.tile, params=w.params, stream=stream) as f64:
-            f64.set_state(np.ascontiguousarray(np.concatenate([U0, U0])))
-            f64.advance(w.nsteps)
-            ref64 = f64.get_state()[:4]
-        U = storage_to_f64(out_sw[:4], w.dtype)
-        C = storage_to_f64(out_sw[8:12], w.dtype)
-        names = ("rho", "m", "q", "E")
-        rep["fp64_reference"] = (f"GPU FP64 Euler path, {w.nsteps} steps from the same "
-                                 "initial values")
-        for v in range(4):
-            denom = max(np.max(np.abs(ref64[v])), np.max(np.abs(U0[v])))
-            rep[f"{names[v]}_max_rel"] = float(np.max(np.abs(U[v] - ref64[v])) / denom)
-            rep[f"{names[v]}_l2_rel"] = float(np.linalg.norm(U[v] - ref64[v])
-                                              / max(np.linalg.norm(ref64[v]), 1e-300))
-        denom = max(np.max(np.abs(ref64)), np.max(np.abs(U0)))
-        rep["U_max_rel_to_max_abs"] = float(np.max(np.abs(U - ref64)) / denom)
-        rep["U_minus_C_max_rel_to_max_abs"] = float(np.max(np.abs((U - C) - ref64)) / denom)
+    t0 = time.perf_counter()
+    if full:
+        nsteps_ref, got = w.nsteps, out_sw
+    else:
+        nsteps_ref = 20 if w.op in ("euler_rk2", "euler_kahan") else 53
+        with torch.cuda.stream(stream):
+            sw.set_state(state_dev)
+            sw.advance(nsteps_ref)
+        got = sw.get_state()
+    if w.op in ("heat", "wave", "euler_rk2"):
+        ref = oracle_advance(w, state_host, nsteps_ref)
+        nv = 4 if w.op == "euler_rk2" else ref.shape[0]
+        got64, ref64 = got[:nv].astype(np.float64), ref[:nv].astype(np.float64)
+        mx, l2 = rel_errors(got64, ref64, state_host[:nv])
+        rep.update({"reference": f"CPU FP64 oracle, {nsteps_ref} steps, every point",
+                    "equal_to_oracle_bitwise": bool(np.array_equal(got[:nv], ref[:nv])),
+                    "max_abs": float(np.max(np.abs(got64 - ref64))),
+                    "max_rel": mx, "l2_rel": l2})
+    else:
+        # the precision path itself, bitwise against its oracle after a few steps
+        nchk = 20
+        with torch.cuda.stream(stream):
+            sw.set_state(state_dev)
+            sw.advance(nchk)
+        own = sw.get_state()
+        rep[f"equal_to_own_oracle_bitwise_{nchk}_steps"] = bool(
+            np.array_equal(own, oracle_advance(w, state_host, nchk)))
+        import oracle
+        init64 = fp64_oracle_of(w, state_host)
+        if w.op == "heat_kahan":
+            ref64 = oracle.heat(init64[0], w.params[0], nsteps_ref)[None]
+            U = storage_to_f64(got[:1], w.dtype)
+            C = storage_to_f64(got[1:2], w.dtype)
+        else:
+            a, dt = oracle.euler_setup(init64[:4], GAMMA, CFL)
+            ref64 = oracle.euler_rk2(init64[:4], GAMMA, dt, KAPPA, a, nsteps_ref)
+            U = storage_to_f64(got[:4], w.dtype)
+            C = storage_to_f64(got[8:12], w.dtype)
+        mx, l2 = rel_errors(U, ref64, init64[:ref64.shape[0]])
+        rep.update({"reference": f"CPU FP64 oracle, {nsteps_ref} steps from the same initial "
+                                 "values, every point",
+                    "max_rel": mx, "l2_rel": l2,
+                    "u_minus_c_max_rel": rel_errors(U - C, ref64, init64[:ref64.shape[0]])[0]})
+        if w.op == "euler_kahan":
+            for v, name in enumerate(("rho", "m", "q", "E")):
+                rep[f"{name}_max_rel"], rep[f"{name}_l2_rel"] = rel_errors(
+                    U[v], ref64[v], init64[v])
+    rep["oracle_seconds"] = time.perf_counter() - t0
     return rep
 
 

@@ -114,3 +114,4 @@ def test_in_place_bridge_panel_reads_see_only_the_current_level(n):
         have = bridge_strip(n, k) | (bridge_rect(n, k - 1) if k else set())
         for xb in (0, 1):
             assert bridge_panel_reads(n, k, xb) <= have, (n, k, xb)
+
