@@ -348,11 +348,13 @@ def bridge_updates(n):
 
 
 # DRAM traffic (read + write bytes) per tile of one octahedron launch, from one
-# ncu capture of the same kernel on a 2048 x 2048 grid (4096 tiles), scaled to a
+# ncu capture of the same kernel on a 2048 x 2048 grid (1024 tiles of 64), scaled to a
 # launch by its number of tiles (reads equal the algorithmic panel bytes there;
 # part of the writes is still in L2 when the kernel ends). Kernels without a
 # capture of their current version report None.
-OCT_TRAFFIC_PER_TILE = {}
+OCT_TRAFFIC_PER_TILE = {
+    ("heat", "f64", 64): (69.219328e6 + 27.585536e6) / 1024,
+}
 
 # Algorithmic work of one point update (one point advanced one sub-step),
 # counted from the update formulas (a fused multiply-add or a division is one
@@ -436,12 +438,12 @@ def roofline(w, kern, peaks, esize, nvars):
            "share_of_kernel_time": ms / total_ms if total_ms else None,
            "traffic": per_tile * tiles if per_tile else None,
            "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the same "
-                              "kernel at 2048x2048 (4096 tiles), scaled by tiles")
+                              "kernel at 2048x2048, scaled by tiles")
            if per_tile else None}
     out.update(bounds(w, esize, upd, hbm_bytes, avg_ms * 1e-3, peaks))
     bl, bms = kern["bridge"]
     if bl:
-        bupd = 2 * bridge_updates(n) * tiles
+        bupd = bridge_updates(n) * tiles              # both bridges of every tile
         b = bounds(w, esize, bupd, hbm_bytes, bms / bl * 1e-3, peaks)
         out["bridge"] = {"avg_launch_ms": bms / bl, "updates_per_launch": bupd,
                          "bound": b["bound"], "frac": b["frac"]}

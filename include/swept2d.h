@@ -232,8 +232,12 @@ int swept2d_kernel_stats(swept2d_t *h, int kind, long long *launches, double *to
  *   out[1]  FP32 lane-operations per second (16 fused multiply-add chains per
  *           thread, 8 blocks of 256 threads per SM);
  *   out[2]  shared-memory wavefronts per second: warp loads of 32 consecutive
- *           4-byte words (one wavefront each, no bank conflict).
- * nout >= 1; entries beyond 3 are left alone. Allocates a small device buffer
+ *           4-byte words (one wavefront each, no bank conflict);
+ *   out[3]  FP64 fused multiply-add warp instructions per second with all 32
+ *           lanes of every warp active (8 chains, 8 blocks of 256 per SM);
+ *   out[4]  the same with one active lane per warp (equal to out[3] where the
+ *           FP64 pipe's time is per warp instruction, not per lane).
+ * nout >= 1; entries beyond 5 are left alone. Allocates a small device buffer
  * for the kernels' results (freed before returning).
  * Errors: EINVAL (out NULL or nout < 1), ENOMEM, ECUDA. */
 int swept2d_measure_peaks(void *stream, double *out, int nout);

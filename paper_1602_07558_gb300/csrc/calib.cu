@@ -28,6 +28,24 @@ __global__ void __launch_bounds__(256) dfma_chains(double *out, double a, double
     out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+// The same 8 chains on `active` lanes of every warp (the others skip the loop):
+// the FP64 pipe's time per warp instruction with few lanes busy.
+__global__ void __launch_bounds__(256) dfma_lanes(double *out, double a, double b, int active) {
+    double x[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = threadIdx.x + i;
+    if ((int)(threadIdx.x & 31) < active) {
+        for (int it = 0; it < kIters; ++it) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) x[i] = __fma_rn(x[i], a, b);
+        }
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) s = __dadd_rn(s, x[i]);
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 template <int CH>
 __global__ void __launch_bounds__(256) dadd_chains(double *out, double a, double b) {
     double x[CH];
@@ -125,7 +143,7 @@ extern "C" int swept2d_measure_peaks(void *stream, double *out, int nout) {
     double *buf = nullptr;
     if (cudaMalloc(&buf, (size_t)max_blocks * threads * sizeof(double)) != cudaSuccess)
         return SWEPT2D_ENOMEM;
-    double fp64 = 0.0, fp32 = 0.0, smem = 0.0;
+    double fp64 = 0.0, fp32 = 0.0, smem = 0.0, warp32 = 0.0, warp1 = 0.0;
     int rc = SWEPT2D_OK;
     float ms = 0.f;
     // FP64: chains x blocks per SM, fused multiply-add and add
@@ -152,11 +170,21 @@ extern "C" int swept2d_measure_peaks(void *stream, double *out, int nout) {
         if ((rc = best_ms(st, [&] { lds_stream<<<blocks, threads, 0, st>>>(buf, rounds); }, &ms)) == 0)
             smem = (double)blocks * (threads / 32) * rounds * 8 / (ms * 1e-3);   // warp loads = wavefronts
     }
+    if (rc == SWEPT2D_OK && nout > 3) {
+        const int blocks = sms * 8;
+        const double winstr = (double)blocks * (threads / 32) * kIters * 8;
+        if ((rc = best_ms(st, [&] { dfma_lanes<<<blocks, threads, 0, st>>>(buf, 0.999, 1e-3, 32); }, &ms)) == 0)
+            warp32 = winstr / (ms * 1e-3);
+        if (rc == 0 && (rc = best_ms(st, [&] { dfma_lanes<<<blocks, threads, 0, st>>>(buf, 0.999, 1e-3, 1); }, &ms)) == 0)
+            warp1 = winstr / (ms * 1e-3);
+    }
     cudaFree(buf);
     if (rc != SWEPT2D_OK) return rc;
     out[0] = fp64;
     if (nout > 1) out[1] = fp32;
     if (nout > 2) out[2] = smem;
+    if (nout > 3) out[3] = warp32;
+    if (nout > 4) out[4] = warp1;
     return SWEPT2D_OK;
 }
 

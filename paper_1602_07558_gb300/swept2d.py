@@ -127,13 +127,15 @@ def measure_fp64_rate(stream=None) -> float:
 
 def measure_peaks(stream=None) -> dict:
     """Measured rates of the current device: FP64 and FP32 lane-operations per
-    second and shared-memory wavefronts per second (swept2d_measure_peaks)."""
-    out = (ctypes.c_double * 3)()
-    rc = lib().swept2d_measure_peaks(_stream_handle(stream), out, 3)
+    second, shared-memory wavefronts per second, and FP64 warp instructions per
+    second with 32 and with 1 active lane (swept2d_measure_peaks)."""
+    out = (ctypes.c_double * 5)()
+    rc = lib().swept2d_measure_peaks(_stream_handle(stream), out, 5)
     if rc != OK:
         raise SweptError(rc, "measure_peaks failed")
     return {"fp64_ops_per_s": out[0], "fp32_ops_per_s": out[1],
-            "smem_wavefronts_per_s": out[2]}
+            "smem_wavefronts_per_s": out[2], "fp64_warp_instr_per_s_32_lanes": out[3],
+            "fp64_warp_instr_per_s_1_lane": out[4]}
 
 
 class Swept2D:
