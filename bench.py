@@ -596,6 +596,9 @@ def main():
             nk = naive_kernel_ms(nv, state_dev, stream, w)
             naive_rf = {"avg_launch_ms": nk}
             naive_rf.update(bounds(w, esize, cells, 2 * nvars * esize * cells, nk * 1e-3, peaks))
+        trace = None
+        if args.persistent:
+            trace = persistent_trace(sw, w, state_dev, stream, clocks.summary().get("sm_mhz"))
         result = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_sw,
@@ -622,6 +625,7 @@ def main():
                     "d2h_bytes_per_step": int(state_host.nbytes)},
             "gpu_launches": launches,
             "gpu_launches_per_step": launches // max(1, args.steps),
+            "persistent_trace": trace,
             "clocks": clocks.summary(),
         }
     if dist is not None:
@@ -709,6 +713,44 @@ def accuracy_report(w, sw, state_host, state_dev, out_sw, stream, Swept2D, full=
                     U[v], ref64[v], init64[v])
     rep["oracle_seconds"] = time.perf_counter() - t0
     return rep
+
+
+def persistent_trace(sw, w, state_dev, stream, sm_mhz):
+    """One persistent advance with the per-item trace on: the mean SM cycles
+    (and microseconds at the sampled SM clock) a block waited for an item's
+    3 x 3 neighbourhood and spent on the item, per kind of item."""
+    import torch
+    n, N = w.tile, w.grid
+    NT = (N // n) ** 2
+    nst = 2 if w.op in ("euler_rk2", "euler_kahan") else 1
+    H = w.nsteps * nst // (n // 2)
+    items = NT * (1 + 3 * H)
+    buf = torch.zeros(2 * items, dtype=torch.int32, device="cuda")
+    sw.set_trace(buf)
+    with torch.cuda.stream(stream):
+        sw.set_state(state_dev)
+        sw.advance(w.nsteps, mode="persistent")
+    torch.cuda.synchronize()
+    sw.set_trace(None)
+    t = buf.cpu().numpy().view(np.uint32).astype(np.float64).reshape(items, 2)
+    kind = np.empty(items, dtype=object)
+    kind[:NT] = "first_up"
+    r = np.arange(items - NT) % (3 * NT)
+    kind[NT:] = np.where(r < 2 * NT, "bridge", "octahedron")
+    last = NT + (H - 1) * 3 * NT + 2 * NT
+    kind[last:] = "final_down"
+    mhz = sm_mhz or 2070.0
+    out = {"sm_mhz_used": mhz, "items": int(items), "half_cycles": int(H)}
+    for k in ("first_up", "bridge", "octahedron", "final_down"):
+        sel = kind == k
+        if sel.any():
+            out[k] = {"count": int(sel.sum()),
+                      "wait_us_mean": float(t[sel, 0].mean() / mhz),
+                      "work_us_mean": float(t[sel, 1].mean() / mhz),
+                      "wait_us_max": float(t[sel, 0].max() / mhz)}
+    tot_wait, tot_work = t[:, 0].sum(), t[:, 1].sum()
+    out["wait_share_of_block_time"] = float(tot_wait / max(tot_wait + tot_work, 1.0))
+    return out
 
 
 def naive_kernel_ms(nv, state_dev, stream, w):

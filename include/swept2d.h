@@ -199,7 +199,7 @@ const char *swept2d_last_error(const swept2d_t *h);
 int swept2d_query(const swept2d_t *h, int what, double *out);
 
 /* Launch shape of the swept kernels of a handle (a tuning knob, not a change
- * of results: every setting gives the same bits). threads: 64, 128, 256 or 512
+ * of results: every setting gives the same bits). threads: 32, 64, 128, 256 or 512
  * per block (default 256; the persistent form also takes up to 512). stage: 1 =
  * the bridge and downward-pyramid blocks bring their whole input panel set
  * into shared memory with TMA bulk copies at block start; 0 = they copy every
@@ -221,6 +221,18 @@ int swept2d_set_tuning(swept2d_t *h, int threads, int stage);
 #define SWEPT2D_K_REDUCE      5
 #define SWEPT2D_K_COUNT       6
 int swept2d_set_timing(swept2d_t *h, int on);
+
+/* Per-item trace of the persistent form (a measurement aid; no counterpart in
+ * the paper). With a device buffer of `items` pairs of unsigned 32-bit words
+ * (the caller's; the library allocates nothing for it), every later persistent
+ * advance of the handle records, for work item i in the kernel's order (tiles
+ * T*Q first Ups, then per half cycle 2 T*Q bridge items and T*Q octahedron or
+ * final Down items), buf[2i] = SM clock cycles the block waited for the item's
+ * 3 x 3 neighbourhood and buf[2i+1] = cycles it spent on the item up to its
+ * release. NULL and 0 turn it off. An advance with more items than `items`
+ * fails with EINVAL. Captured graphs of the handle are dropped.
+ * Errors: EINVAL (buffer without size or the reverse), ECUDA. */
+int swept2d_set_trace(swept2d_t *h, void *device_buffer, long long items);
 int swept2d_kernel_stats(swept2d_t *h, int kind, long long *launches, double *total_ms);
 
 /* Measured rates of this GPU for the roofline, each timed with CUDA events on

@@ -27,12 +27,18 @@ from .swept2d import Swept2D, SweptError
 
 def fit_cost_model(N2, probes):
     """s and tau of t(n) = N2 s + 4 tau / n from two (n, seconds per sub-step)
-    probes."""
-    (na, ta), (nb, tb) = probes
+    probes. Where the probes fall faster than 1/n (per-level overheads that
+    the model leaves out grow as the tile shrinks) the exact fit would give
+    s < 0; s is then taken as 0 and tau from the larger tile's probe, so the
+    model still ranks the tiles by their 1/n term."""
+    (na, ta), (nb, tb) = sorted(probes)
     if na == nb:
         return ta / N2, 0.0
     b = (ta - tb) / (1.0 / na - 1.0 / nb)          # 4 tau
-    return (ta - b / na) / N2, b / 4.0
+    s = (ta - b / na) / N2
+    if s < 0:
+        return 0.0, tb * nb / 4.0
+    return s, b / 4.0
 
 
 def predict(N2, s, tau, n):
@@ -174,7 +180,7 @@ def _probe_state(b, op):
 
 
 def autotune_batch(nx, ny, op, params, dtype=None, state=None, stream=None, probe_steps=64,
-                   tiles=(16, 32, 64), stages=(False, True), threads=(64, 128, 256), top=2):
+                   tiles=(16, 32, 64), stages=(False, True), threads=(32, 64, 128, 256), top=2):
     """Per size class (grids sharing the same candidate tiles), fit the cost
     model of autotune() to probes of the class's smallest and largest tile on
     the class's own grids (a batch of them, so the probe launches have the real

@@ -502,8 +502,8 @@ static int drop_graphs(swept2d_batch *b) {
 
 int swept2d_batch_set_tuning(swept2d_batch_t *b, int threads, int stage) {
     if (!b) return SWEPT2D_EINVAL;
-    if (threads != 64 && threads != 128 && threads != 256 && threads != 512)
-        return bfail(b, SWEPT2D_EINVAL, "set_tuning: threads must be 64, 128, 256 or 512");
+    if (threads != 32 && threads != 64 && threads != 128 && threads != 256 && threads != 512)
+        return bfail(b, SWEPT2D_EINVAL, "set_tuning: threads must be 32, 64, 128, 256 or 512");
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
@@ -521,8 +521,8 @@ int swept2d_batch_set_tuning(swept2d_batch_t *b, int threads, int stage) {
 
 int swept2d_batch_set_class_tuning(swept2d_batch_t *b, int tile, int threads, int stage) {
     if (!b) return SWEPT2D_EINVAL;
-    if (threads != 64 && threads != 128 && threads != 256 && threads != 512)
-        return bfail(b, SWEPT2D_EINVAL, "set_class_tuning: threads must be 64, 128, 256 or 512");
+    if (threads != 32 && threads != 64 && threads != 128 && threads != 256 && threads != 512)
+        return bfail(b, SWEPT2D_EINVAL, "set_class_tuning: threads must be 32, 64, 128, 256 or 512");
     for (auto &c : b->classes) {
         if (c.n != tile || tile == 0) continue;
         int dev = 0, optin = 0;

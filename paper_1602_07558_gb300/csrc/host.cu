@@ -53,6 +53,8 @@ struct swept2d {
     unsigned long long *scratch8 = nullptr;
     int *errword = nullptr;   // set by a kernel whose bounded wait gave up
     int *sched = nullptr;     // persistent form: T*Q phase counters + queue counter
+    unsigned *trace = nullptr;   // persistent form: caller's per-item cycle record (or none)
+    long long trace_items = 0;
     swept::Tuning tune;
     size_t state_bytes = 0, panel_bytes = 0, smem_bytes = 0;
     double consts[8] = {0};
@@ -214,7 +216,7 @@ int swept_substeps(swept2d *h, long long total, bool persistent) {
         int rc = launch(h, SWEPT2D_K_OCTAHEDRON, "persistent kernel", [&] {
             return h->ops->persistent(h->G, h->consts, h->state, h->up, h->br, h->sched, (int)H,
                                       g_start, h->errword, h->tune, 0,
-                                      swept::kPersistSpinLimit, h->stream);
+                                      swept::kPersistSpinLimit, h->trace, h->stream);
         });
         if (rc) return rc;
         h->substeps += H * half;
@@ -493,7 +495,7 @@ int swept2d_selftest_wait_timeout(swept2d_t *h, long long spin_limit) {
     rc = launch(h, SWEPT2D_K_OCTAHEDRON, "persistent kernel (wait-timeout self-test)", [&] {
         return h->ops->persistent(h->G, h->consts, h->state, h->up, h->br, h->sched, 1,
                                   (u64)h->substeps, h->errword, h->tune, NT, spin_limit,
-                                  h->stream);
+                                  nullptr, h->stream);
     });
     if (rc) return rc;
     if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return cuda_fail(h, e, "selftest sync");
@@ -521,8 +523,11 @@ int swept2d_advance(swept2d_t *h, long long nsteps, int mode) {
         if (mode != SWEPT2D_SWEPT) return fail(h, SWEPT2D_EINVAL, "advance: persistent needs the swept mode");
         if (h->tune.threads > h->ops->max_persistent_threads)
             return fail(h, SWEPT2D_EINVAL, "advance: the persistent form takes at most 512 threads per block");
-        const int rc = persistent_prepare(h, nsteps * h->nst / (h->n / 2));
+        const long long H = nsteps * h->nst / (h->n / 2);
+        const int rc = persistent_prepare(h, H);
         if (rc) return rc;
+        if (h->trace && swept::persistent_items((long long)h->G.T * h->G.Q, H) > h->trace_items)
+            return fail(h, SWEPT2D_EINVAL, "advance: the trace buffer holds fewer items than this advance has");
         mode |= persistent;
     }
     if (graph) {
@@ -583,8 +588,8 @@ int swept2d_query(const swept2d_t *h, int what, double *out) {
 
 int swept2d_set_tuning(swept2d_t *h, int threads, int stage) {
     if (!h) return SWEPT2D_EINVAL;
-    if (threads != 64 && threads != 128 && threads != 256 && threads != 512)
-        return fail(h, SWEPT2D_EINVAL, "set_tuning: threads must be 64, 128, 256 or 512");
+    if (threads != 32 && threads != 64 && threads != 128 && threads != 256 && threads != 512)
+        return fail(h, SWEPT2D_EINVAL, "set_tuning: threads must be 32, 64, 128, 256 or 512");
     if (h->n == 0) return fail(h, SWEPT2D_EINVAL, "set_tuning: naive-only handle");
     const size_t sm = h->ops->smem_for(h->n, stage != 0);
     int dev = 0, optin = 0;
@@ -605,6 +610,23 @@ int swept2d_set_tuning(swept2d_t *h, int threads, int stage) {
     h->tune.threads = threads;
     h->tune.stage = stage != 0;
     h->smem_bytes = sm;
+    return SWEPT2D_OK;
+}
+
+int swept2d_set_trace(swept2d_t *h, void *device_buffer, long long items) {
+    if (!h) return SWEPT2D_EINVAL;
+    if ((device_buffer == nullptr) != (items == 0) || items < 0)
+        return fail(h, SWEPT2D_EINVAL, "set_trace: give a buffer and its item count, or NULL and 0");
+    // captured graphs hold the old pointer: drop them
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "set_trace sync");
+    for (auto &g : h->graphs) {
+        cudaGraphExecDestroy(g.exec);
+        cudaGraphDestroy(g.graph);
+    }
+    h->graphs.clear();
+    h->trace = (unsigned *)device_buffer;
+    h->trace_items = items;
     return SWEPT2D_OK;
 }
 

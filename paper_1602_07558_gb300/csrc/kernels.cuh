@@ -1033,12 +1033,17 @@ __host__ __device__ inline long long persistent_items(long long NT, long long H)
 // located by `at`. `first` is the first work item taken (0; a positive value
 // skips items, which only the wait-timeout self-test does: the skipped items
 // are never counted, so every wait runs out).
+// `trace` (nullptr: none) receives, per work item, the SM clock cycles its
+// block spent waiting for the item's neighbourhood (trace[2 item]) and running
+// the item up to its release (trace[2 item + 1]).
 template <class Op, bool STG, class Loc>
 __device__ __forceinline__ void persistent_loop(const Op &op, const Loc &at, int NT, int n,
                                                 typename Op::S *state, typename Op::S *upp,
                                                 typename Op::S *br, int *stage, int *queue, int H,
-                                                u64 g0, int *err, int first, long long spin_limit) {
+                                                u64 g0, int *err, int first, long long spin_limit,
+                                                unsigned *trace = nullptr) {
     __shared__ int s_item, s_fail;
+    long long t_start = 0, t_ready = 0;
     const int h = n / 2;
     const int nitems = (int)persistent_items(NT, H);
     for (;;) {
@@ -1075,6 +1080,7 @@ __device__ __forceinline__ void persistent_loop(const Op &op, const Loc &at, int
         const Geom &G = w.G;
         const int I = w.I, J = w.J;
         const Op opi = w.c ? Op(w.c) : op;
+        if (trace && threadIdx.x == 0) t_start = clock64();
         if (kind != 0 && threadIdx.x < 32) {
             // lanes 0..8 wait for one tile each of the periodic 3 x 3 neighbourhood
             bool bad = false;
@@ -1102,6 +1108,7 @@ __device__ __forceinline__ void persistent_loop(const Op &op, const Loc &at, int
         }
         __syncthreads();
         if (s_fail) return;
+        if (trace && threadIdx.x == 0) t_ready = clock64();
         // the acquired panels are read next by bulk copies (the async proxy)
         if (threadIdx.x == 0) asm volatile("fence.proxy.async.global;\n" ::: "memory");
         typename Op::S *st = state + w.soff, *u = upp + w.poff, *b = br + w.poff;
@@ -1123,7 +1130,13 @@ __device__ __forceinline__ void persistent_loop(const Op &op, const Loc &at, int
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         __threadfence();
         __syncthreads();
-        if (threadIdx.x == 0) add_release(stage + t, 1);
+        if (threadIdx.x == 0) {
+            if (trace) {
+                trace[2 * (size_t)item] = (unsigned)(t_ready - t_start);
+                trace[2 * (size_t)item + 1] = (unsigned)(clock64() - t_ready);
+            }
+            add_release(stage + t, 1);
+        }
     }
 }
 
@@ -1131,9 +1144,10 @@ template <class Op, bool STG>
 __global__ void __launch_bounds__(kMaxPersistentThreads) persistent_kernel(Op op, Geom G, typename Op::S *state,
                                                          typename Op::S *upp, typename Op::S *br,
                                                          int *stage, int *queue, int H, u64 g0,
-                                                         int *err, int first, long long spin_limit) {
+                                                         int *err, int first, long long spin_limit,
+                                                         unsigned *trace) {
     persistent_loop<Op, STG>(op, OneGrid{G}, G.T * G.Q, G.n, state, upp, br, stage, queue, H, g0,
-                             err, first, spin_limit);
+                             err, first, spin_limit, trace);
 }
 
 }  // namespace swept

@@ -38,7 +38,7 @@ struct OpTable {
     // launch; sched: T*Q phase counters followed by the queue counter, zeroed
     cudaError_t (*persistent)(const Geom &, const double *c, void *state, void *up, void *br,
                               int *sched, int H, u64 g0, int *err, const Tuning &, int first,
-                              long long spin_limit, cudaStream_t);
+                              long long spin_limit, unsigned *trace, cudaStream_t);
     int max_threads;              // largest block of the launch-per-phase swept kernels
     int max_persistent_threads;   // largest block of the persistent kernel
 };
@@ -165,7 +165,8 @@ struct Launch {
     template <bool STG>
     static cudaError_t persistent_t(const Geom &G, const double *c, void *state, void *upp,
                                     void *br, int *sched, int H, u64 g0, int *err, int threads,
-                                    int first, long long spin_limit, cudaStream_t st) {
+                                    int first, long long spin_limit, unsigned *trace,
+                                    cudaStream_t st) {
         const size_t sm = down_smem<Op>(G.n, STG);
         cudaError_t e = allow_smem(persistent_kernel<Op, STG>, sm);
         if (e != cudaSuccess) return e;
@@ -182,17 +183,17 @@ struct Launch {
         persistent_kernel<Op, STG><<<(int)grid, threads, sm, st>>>(Op(c), G, (S *)state,
                                                                    (S *)upp, (S *)br, sched,
                                                                    sched + NT, H, g0, err, first,
-                                                                   spin_limit);
+                                                                   spin_limit, trace);
         return cudaGetLastError();
     }
     static cudaError_t persistent(const Geom &G, const double *c, void *state, void *upp,
                                   void *br, int *sched, int H, u64 g0, int *err,
                                   const Tuning &tn, int first, long long spin_limit,
-                                  cudaStream_t st) {
+                                  unsigned *trace, cudaStream_t st) {
         return tn.stage ? persistent_t<true>(G, c, state, upp, br, sched, H, g0, err, tn.threads,
-                                             first, spin_limit, st)
+                                             first, spin_limit, trace, st)
                         : persistent_t<false>(G, c, state, upp, br, sched, H, g0, err, tn.threads,
-                                              first, spin_limit, st);
+                                              first, spin_limit, trace, st);
     }
     static const OpTable *table() {
         static const OpTable t = {Op::NV,      Op::NST,     (int)sizeof(S), &swept_smem_bytes<Op>,

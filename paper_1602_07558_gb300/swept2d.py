@@ -78,10 +78,11 @@ def lib():
         L.swept2d_measure_fp64_rate.argtypes = [vp, ctypes.POINTER(d)]
         L.swept2d_measure_peaks.argtypes = [vp, ctypes.POINTER(d), i]
         L.swept2d_selftest_wait_timeout.argtypes = [vp, ll]
+        L.swept2d_set_trace.argtypes = [vp, vp, ll]
         for name in ("swept2d_create", "swept2d_set_state", "swept2d_advance",
                      "swept2d_get_state", "swept2d_destroy", "swept2d_query",
                      "swept2d_set_timing", "swept2d_kernel_stats", "swept2d_measure_fp64_rate",
-                     "swept2d_measure_peaks", "swept2d_set_tuning", "swept2d_selftest_wait_timeout"):
+                     "swept2d_measure_peaks", "swept2d_set_tuning", "swept2d_set_trace", "swept2d_selftest_wait_timeout"):
             getattr(L, name).restype = i
         _lib = L
         return L
@@ -198,6 +199,18 @@ class Swept2D:
     def set_tuning(self, threads=256, stage=False):
         """Launch shape of the swept kernels (same results for every setting)."""
         self._check(lib().swept2d_set_tuning(self._h, int(threads), 1 if stage else 0))
+
+    def set_trace(self, buf=None):
+        """Record the persistent form's per-item (wait, work) SM cycles into a
+        contiguous device tensor of 2 x items 32-bit words (None: stop)."""
+        if buf is None:
+            self._check(lib().swept2d_set_trace(self._h, None, 0))
+            self._trace = None
+            return
+        if not buf.is_cuda or not buf.is_contiguous() or buf.element_size() != 4:
+            raise ValueError("trace buffer: a contiguous CUDA tensor of 32-bit words")
+        self._trace = buf                       # keep the memory alive while recording
+        self._check(lib().swept2d_set_trace(self._h, buf.data_ptr(), buf.numel() // 2))
 
     def set_timing(self, on=True):
         self._check(lib().swept2d_set_timing(self._h, 1 if on else 0))

@@ -32,3 +32,14 @@ def test_per_node_optimum_of_eq_cost():
     h = 1e-3 * n_star
     assert f(n_star) < f(n_star - h) and f(n_star) < f(n_star + h)
     assert (f(n_star + h) - f(n_star - h)) / (2 * h) == pytest.approx(0.0, abs=1e-9)
+
+
+def test_fit_falls_back_when_the_probes_fall_faster_than_one_over_n():
+    """Probes t(16) = 10, t(64) = 1 (per sub-step) fall faster than 1/n: the
+    exact fit would give s < 0; the fit keeps s = 0 and takes tau from the
+    larger tile, so the model goes through that probe and ranks by 1/n."""
+    N2 = 1.0e6
+    s_fit, tau_fit = fit_cost_model(N2, [(16, 10.0), (64, 1.0)])
+    assert s_fit == 0.0
+    assert predict(N2, s_fit, tau_fit, 64) == pytest.approx(1.0)
+    assert predict(N2, s_fit, tau_fit, 16) > predict(N2, s_fit, tau_fit, 32) > 1.0

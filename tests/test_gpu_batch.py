@@ -148,7 +148,7 @@ def test_batch_euler_every_grid_has_its_own_time_step(oracle_lib, dtype, mode):
 def test_batch_tuning_gives_identical_bits():
     states = _states("heat_kahan", "f32", seed=3)
     outs = []
-    for threads, stage in [(256, False), (128, True), (64, False)]:
+    for threads, stage in [(256, False), (128, True), (64, False), (32, False), (32, True)]:
         for mode in ("swept", "persistent"):
             with SweptBatch([s[0] for s in SIZES], [s[1] for s in SIZES], [s[2] for s in SIZES],
                             op="heat_kahan", params=(0.2,), dtype="f32") as b:

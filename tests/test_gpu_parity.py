@@ -187,8 +187,8 @@ def test_heat_kahan_2048_full_grid_matches_oracle(oracle_lib, storage):
     ("heat", "f64", (0.2,)), ("heat_kahan", "f32", (0.2,)), ("heat_kahan", "bf16", (0.2,)),
     ("hash", "u64", ()), ("wide2", "u64", ()), ("euler_kahan", "f32", (GAMMA, CFL, KAPPA)),
 ])
-@pytest.mark.parametrize("threads,stage", [(64, False), (128, True), (256, True), (256, False),
-                                           (512, False), (512, True)])
+@pytest.mark.parametrize("threads,stage", [(32, False), (32, True), (64, False), (128, True),
+                                           (256, True), (256, False), (512, False), (512, True)])
 def test_tuning_gives_identical_bits(op, dtype, params, threads, stage):
     """Threads per block and TMA panel staging change the schedule, never the
     result: every setting equals the naive path bit for bit."""
@@ -322,6 +322,34 @@ def test_persistent_wait_timeout_is_reported_and_the_context_stays_usable(oracle
         s.set_state(u0.reshape(s.shape))
         assert s.selftest_wait_timeout(4096) == ETIMEOUT
         assert np.array_equal(s.get_state().reshape(64, 64), u0)    # no work item ran
+        s.advance(40, mode="persistent")
+        assert np.array_equal(s.get_state().reshape(64, 64), ref)
+
+
+def test_persistent_trace_records_every_item_and_changes_nothing(oracle_lib):
+    """With a trace buffer the persistent advance records a (wait, work) cycle
+    pair for every work item; the result stays the oracle's, and a buffer too
+    small for an advance is refused."""
+    import torch
+    from paper_1602_07558_gb300.swept2d import EINVAL, SweptError
+    u0 = inputs.uniform(64, 64, seed=9)
+    ref = oracle_lib.heat(u0, 0.2, 40)
+    NT, H = 16, 5                           # 4 x 4 tiles of 16, 40 steps = 5 half cycles
+    items = NT * (1 + 3 * H)
+    buf = torch.zeros(2 * items, dtype=torch.int32, device="cuda")
+    with Swept2D(64, 64, op="heat", tile=16, params=(0.2,)) as s:
+        s.set_trace(buf)
+        s.set_state(u0.reshape(s.shape))
+        s.advance(40, mode="persistent")
+        assert np.array_equal(s.get_state().reshape(64, 64), ref)
+        t = buf.cpu().numpy().view(np.uint32).reshape(items, 2)
+        assert (t[:, 1] > 0).all()                      # every item ran and was timed
+        s.set_trace(buf[:2 * (items - 1)])
+        s.set_state(u0.reshape(s.shape))
+        with pytest.raises(SweptError) as ei:
+            s.advance(40, mode="persistent")
+        assert ei.value.code == EINVAL
+        s.set_trace(None)
         s.advance(40, mode="persistent")
         assert np.array_equal(s.get_state().reshape(64, 64), ref)
 
