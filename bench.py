@@ -66,6 +66,7 @@ class Workload:
     seed: int
     describe: str = ""
     threads: int = 0                 # swept threads per block (0: the library's default)
+    persistent: bool = False         # the swept arm's default form (measured fastest)
     extra: dict = field(default_factory=dict)
 
 
@@ -76,19 +77,19 @@ WORKLOADS = {
                        "heat 64x64 FP64 r=0.2, 512 steps, U[0,1) field (seed 0)"),
     "heat2048_f32": Workload("heat_kahan", "f32", 2048, 100_000, 64, (0.2,), "smooth", 1,
                              "heat 2048x2048, binary32 storage and arithmetic, Kahan-"
-                             "compensated update, r=0.2, 100000 steps"),
+                             "compensated update, r=0.2, 100000 steps", persistent=True),
     "heat2048_bf16": Workload("heat_kahan", "bf16", 2048, 100_000, 64, (0.2,), "smooth", 1,
                               "heat 2048x2048, bfloat16 storage, binary32 arithmetic, Kahan-"
-                              "compensated update, r=0.2, 100000 steps"),
+                              "compensated update, r=0.2, 100000 steps", persistent=True),
     "euler2048": Workload("euler_rk2", "f64", 2048, 5_000, 32, (GAMMA, CFL, KAPPA), "euler", 2,
                           "Euler 2048x2048 FP64, midpoint RK2, CFL 0.3, 5000 steps"),
     "euler2048_f32": Workload("euler_kahan", "f32", 2048, 5_000, 32, (GAMMA, CFL, KAPPA),
                               "euler", 2, "Euler 2048x2048, binary32 storage and arithmetic, "
                               "Kahan-compensated update, midpoint RK2, CFL 0.3, 5000 steps"),
-    "euler2048_bf16": Workload("euler_kahan", "bf16", 2048, 5_000, 32, (GAMMA, CFL, KAPPA),
+    "euler2048_bf16": Workload("euler_kahan", "bf16", 2048, 5_000, 16, (GAMMA, CFL, KAPPA),
                                "euler", 2, "Euler 2048x2048, bfloat16 storage, binary32 "
                                "arithmetic, Kahan-compensated update, midpoint RK2, CFL 0.3, "
-                               "5000 steps"),
+                               "5000 steps", 128),
     "batch1024": Workload("heat_kahan", "f32", 0, 20_000, 0, (0.2,), "batch", 3,
                           "1024 independent periodic grids, nx and ny uniform in {32,48,...,512} "
                           "(seed 3), heat with binary32 storage and Kahan-compensated update, "
@@ -100,7 +101,7 @@ WORKLOADS = {
                                 "time step, 2000 steps"),
     "wave1024": Workload("wave", "f64", 1024, 10_000, 32, (0.3,), "source", 0,
                          "wave 1024x1024 FP64 leapfrog, Courant 0.3, Gaussian source at the "
-                         "centre, 10000 steps"),
+                         "centre, 10000 steps", persistent=True),
 }
 
 
@@ -119,6 +120,8 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--quick-check", action="store_true",
                    help="compare with the oracle after 53 steps (20 for Euler), not all steps")
+    p.add_argument("--oracle-steps", type=int, default=None,
+                   help="compare with the CPU oracle after this many steps (default: all)")
     p.add_argument("--profile-case", action="store_true",
                    help="short run of the same grid for ncu captures (no timing claims)")
     p.add_argument("--threads", type=int, default=None, help="swept threads per block")
@@ -129,8 +132,12 @@ def parse():
                    help="run each advance (swept and naive) as a captured CUDA graph")
     p.add_argument("--persistent", action="store_true",
                    help="swept arm: one persistent launch per advance")
+    p.add_argument("--launch-per-phase", action="store_true",
+                   help="swept arm: one launch per phase (the default of most workloads)")
     a = p.parse_args()
     w = WORKLOADS[a.workload]
+    if not a.persistent and not a.launch_per_phase:
+        a.persistent = w.persistent
     for k in ("grid", "nsteps", "tile"):
         if getattr(a, k) is not None:
             setattr(w, k, getattr(a, k))
@@ -566,7 +573,7 @@ def main():
     result = None
     if rank == 0:
         errors = accuracy_report(w, sw, state_host, state_dev, out_sw, stream, Swept2D,
-                                 full=not args.quick_check)
+                                 full=not args.quick_check, oracle_steps=args.oracle_steps)
         h_in = torch.from_numpy(state_host.copy()).pin_memory()
         h_out = torch.empty_like(h_in).pin_memory()
         e2e_t = []
@@ -652,23 +659,27 @@ def fp64_oracle_of(w, state_host):
     return np.concatenate([U0, U0])
 
 
-def accuracy_report(w, sw, state_host, state_dev, out_sw, stream, Swept2D, full=True):
+def accuracy_report(w, sw, state_host, state_dev, out_sw, stream, Swept2D, full=True,
+                    oracle_steps=None):
     """Error against FP64, on the final state of the timed run (all of the
     workload's steps) against the CPU oracle run over the same steps from the
     same initial values: for the FP64 workloads whether every point is equal
     to the oracle's, and the max-norm and L2 errors; for the reduced-precision
     forms the same errors against the FP64 oracle (the Euler form compares the
     four conserved variables), plus a bitwise check of the precision path
-    itself against its own oracle after a few steps. With full=False the FP64
-    comparison is made after 53 steps (20 for Euler) instead."""
+    itself against its own oracle after a few steps, and for those forms the
+    same errors over all steps against the GPU FP64 path of the same update
+    (bitwise equal to the oracle in the parity tests). With full=False the
+    oracle comparison is made after 53 steps (20 for Euler) instead, with
+    oracle_steps after that many."""
     import torch
     N = w.grid
     rep = {}
     t0 = time.perf_counter()
-    if full:
+    if full and (oracle_steps is None or oracle_steps >= w.nsteps):
         nsteps_ref, got = w.nsteps, out_sw
     else:
-        nsteps_ref = 20 if w.op in ("euler_rk2", "euler_kahan") else 53
+        nsteps_ref = oracle_steps or (20 if w.op in ("euler_rk2", "euler_kahan") else 53)
         with torch.cuda.stream(stream):
             sw.set_state(state_dev)
             sw.advance(nsteps_ref)
@@ -711,6 +722,15 @@ def accuracy_report(w, sw, state_host, state_dev, out_sw, stream, Swept2D, full=
             for v, name in enumerate(("rho", "m", "q", "E")):
                 rep[f"{name}_max_rel"], rep[f"{name}_l2_rel"] = rel_errors(
                     U[v], ref64[v], init64[v])
+        # all steps against the GPU FP64 path (the final state of the timed run)
+        op64 = "heat" if w.op == "heat_kahan" else "euler_rk2"
+        with Swept2D(N, N, op=op64, tile=w.tile, params=w.params, stream=stream) as f64:
+            f64.set_state(np.ascontiguousarray(init64))
+            f64.advance(w.nsteps)
+            g64 = f64.get_state()[:ref64.shape[0]]
+        Uf = storage_to_f64(out_sw[:g64.shape[0]], w.dtype)
+        mx, l2 = rel_errors(Uf, g64, init64[:g64.shape[0]])
+        rep["vs_gpu_fp64_all_steps"] = {"steps": w.nsteps, "max_rel": mx, "l2_rel": l2}
     rep["oracle_seconds"] = time.perf_counter() - t0
     return rep
 
