@@ -66,14 +66,9 @@ __host__ __device__ inline SmemPlan smem_plan(int n, int stage_segments, bool st
     const size_t levels = (size_t)((one_buffer<Op>() ? 1 : 2) * Op::NV + Op::AUX) * P * P * sizeof(S);
     SmemPlan pl;
     pl.stage_off = (levels + 15) & ~(size_t)15;
-    // staged: the block's whole input panel set; otherwise, for the updates
-    // computed in place after their first pass, one level's panel lines (up
-    // to 4 sides x 2 lines of n values per plane) moved by TMA bulk copies
-    const bool lines = !staged && Op::INPLACE_AFTER_AUX;
-    const size_t stage = staged ? (size_t)stage_segments * Op::NV * panel_stride(n) * sizeof(S)
-                         : lines ? (size_t)8 * n * Op::NV * sizeof(S) : 0;
+    const size_t stage = staged ? (size_t)stage_segments * Op::NV * panel_stride(n) * sizeof(S) : 0;
     pl.bar_off = (pl.stage_off + stage + 7) & ~(size_t)7;
-    pl.total = pl.bar_off + ((staged && stage_segments) || lines ? 8 : 0);
+    pl.total = pl.bar_off + (staged && stage_segments ? 8 : 0);
     return pl;
 }
 
@@ -168,44 +163,6 @@ __device__ __forceinline__ bool block_wait_bulk(unsigned long long *bar, int *er
     return true;
 }
 
-// Every thread waits for phase `parity` of `bar` (a barrier used once per
-// level); false (the same for the whole block) if the wait gave up, after
-// recording it in *err and letting the copies in flight land.
-__device__ __forceinline__ bool block_wait_parity(unsigned long long *bar, unsigned parity,
-                                                  int *err) {
-    bool ok = false;
-    for (long long it = 0; it < kSpinLimit && !ok; ++it) ok = mbar_try_wait(bar, parity);
-    const int bad = __syncthreads_or(!ok);
-    if (bad) {
-        if (threadIdx.x == 0) {
-            if (err) atomicExch(err, 1);
-            for (long long it = 0; it < kSpinLimit; ++it)
-                if (mbar_try_wait(bar, parity)) break;
-        }
-        __syncthreads();
-        return false;
-    }
-    return true;
-}
-
-// ---- TMA bulk copies shared -> global (completed through bulk groups).
-__device__ __forceinline__ void bulk_s2g(void *gdst, const void *ssrc, unsigned bytes) {
-    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(gdst),
-                 "r"(smem_u32(ssrc)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
-// the bulk stores issued so far have read their shared-memory source
-__device__ __forceinline__ void bulk_wait_read_all() {
-    asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
-}
-// the bulk stores issued so far are complete in device memory
-__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
-// orders this thread's shared-memory accesses before later async-proxy (TMA) ones
-__device__ __forceinline__ void fence_async_shared() {
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-}
-
 // Threads take consecutive points of a W-wide rectangle (point e = t, t + T,
 // t + 2T, ... in row order, T = blockDim), so warps stay full; the (column,
 // row) of the next point follows by adding (T mod W, T div W) with a carry,
@@ -258,67 +215,6 @@ __device__ __forceinline__ void for_each_point(int W, int H, F &&f) {
             f(2 * w.yy + (w.xx & 1), w.xx >> 1);
     } else {
         for (LinearWalk w(W); w.yy < H; w.next(W)) f(w.xx, w.yy);
-    }
-}
-
-// ---- One level's panel lines moved by TMA (the updates computed in place
-// after their first pass). A panel side holds a level's two lines of L values
-// contiguously from its level offset, per value plane, so one bulk copy moves
-// a (side, plane) pair of lines. The staging area holds them at
-// stg[((side * NV + v) * 2 + d) * L + p]; the level buffer copies are one
-// element per thread, consecutive threads on consecutive staging elements.
-// Bulk copies need 16-byte sizes and addresses: every line length and level
-// offset is even, so 8-byte values always qualify.
-
-// thread 0: one bulk load per (side, plane) of `nsides` panel sides, completed
-// on `bar`
-template <class S, int NV>
-__device__ __forceinline__ void lines_load(const S *const *seg, int nsides, int L, int off,
-                                           int PS, S *stg, unsigned long long *bar) {
-    static_assert(sizeof(S) == 8, "bulk line copies of 8-byte values");
-    if (threadIdx.x == 0) {
-        const unsigned bytes = 2u * (unsigned)L * (unsigned)sizeof(S);
-        fence_async_shared();   // earlier reads of the staging area before the copy's writes
-        mbar_expect_tx(bar, (unsigned)(nsides * NV) * bytes);
-        for (int sd = 0; sd < nsides; ++sd)
-            for (int v = 0; v < NV; ++v)
-                bulk_g2s(stg + (sd * NV + v) * 2 * L, seg[sd] + (size_t)v * PS + off, bytes, bar);
-    }
-}
-// thread 0: one bulk store per (side, plane) of `nsides` panel sides
-template <class S, int NV>
-__device__ __forceinline__ void lines_store(S *const *seg, int nsides, int L, int off, int PS,
-                                            const S *stg) {
-    if (threadIdx.x == 0) {
-        const unsigned bytes = 2u * (unsigned)L * (unsigned)sizeof(S);
-        for (int sd = 0; sd < nsides; ++sd)
-            for (int v = 0; v < NV; ++v)
-                bulk_s2g(seg[sd] + (size_t)v * PS + off, stg + (sd * NV + v) * 2 * L, bytes);
-        bulk_commit();
-    }
-}
-// staging -> level buffer (pos(side, d, p): the element's offset in plane 0)
-template <class S, int NV, class Pos>
-__device__ __forceinline__ void stage_to_buf(const S *stg, S *buf, int plane, int nsides, int L,
-                                             Pos &&pos) {
-    const int total = nsides * NV * 2 * L;
-    const float rl = recip_small(L);
-    for (int e = threadIdx.x; e < total; e += blockDim.x) {
-        const int q = div_small(e, rl);          // (side * NV + v) * 2 + d
-        const int p = e - q * L, d = q & 1, sv = q >> 1, side = sv / NV, v = sv - side * NV;
-        buf[v * plane + pos(side, d, p)] = stg[e];
-    }
-}
-// level buffer -> staging, the same element order
-template <class S, int NV, class Pos>
-__device__ __forceinline__ void buf_to_stage(const S *buf, S *stg, int plane, int nsides, int L,
-                                             Pos &&pos) {
-    const int total = nsides * NV * 2 * L;
-    const float rl = recip_small(L);
-    for (int e = threadIdx.x; e < total; e += blockDim.x) {
-        const int q = div_small(e, rl);
-        const int p = e - q * L, d = q & 1, sv = q >> 1, side = sv / NV, v = sv - side * NV;
-        stg[e] = buf[v * plane + pos(side, d, p)];
     }
 }
 
@@ -716,42 +612,9 @@ __global__ void __launch_bounds__(256) naive_heat_kahan_kernel(HeatKahanOp<SS> o
 template <class Op>
 __device__ __forceinline__ void up_body(const Op &op, const Geom &G, typename Op::S *buf0,
                                         typename Op::S *buf1, typename Op::S *aux, int P, u64 g0,
-                                        typename Op::S *up, int slot, int first_parity,
-                                        unsigned char *smem_raw) {
+                                        typename Op::S *up, int slot, int first_parity) {
     typedef typename Op::S S;
-    constexpr int NV = Op::NV;
     const int n = G.n, h = n / 2;
-    if constexpr (Op::INPLACE_AFTER_AUX) {
-        // in place, one buffer; each level's up panels gathered into the
-        // staging area in the level's first pass and stored by TMA after it
-        S *buf = buf0;
-        const int plane = P * P;
-        S *stg = reinterpret_cast<S *>(smem_raw + smem_plan<Op>(n, 0, false).stage_off);
-        S *dseg[4];
-        for (int side = 0; side < 4; ++side) dseg[side] = up + ((size_t)slot * 4 + side) * NV * G.PS;
-        for (int k = 0; k < h; ++k) {
-            const int L = n - 2 * k, off = 2 * k * (n - k + 1);
-            buf_to_stage<S, NV>(buf, stg, plane, 4, L, [&](int side, int d, int p) {
-                int a, b;
-                up_panel_xy(side, n, k, d, p, a, b);
-                return (b + 1) * P + (a + 1);
-            });
-            fence_async_shared();   // the staging writes before the TMA store reads them
-            if (k + 1 < h) {
-                const u64 g = g0 + k;
-                compute_rect_mid(op, (int)(g % Op::NST), g, buf, buf, aux, P, k + 1, k + 1,
-                                 n - 2 * k - 2, n - 2 * k - 2,
-                                 [&] { lines_store<S, NV>(dseg, 4, L, off, G.PS, stg); });
-            } else {
-                __syncthreads();
-                lines_store<S, NV>(dseg, 4, L, off, G.PS, stg);
-            }
-            if (threadIdx.x == 0) bulk_wait_read_all();   // staging free for the next level
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) bulk_wait_all();   // the panels complete before the block ends
-        return;
-    }
     for (int k = 0; k < h; ++k) {
         const int par = (first_parity + k) & 1;
         const S *cur = par ? buf1 : buf0;
@@ -790,7 +653,7 @@ __device__ __forceinline__ void up_tile(const Op &op, const Geom &G, const typen
             buf0[v * plane + (b + 1) * P + (a + 1)] = state[v * gplane + (size_t)y * G.nx + x];
     }
     __syncthreads();
-    up_body(op, G, buf0, buf1, aux, P, g0, up, J * G.T + I, 0, smem_raw);
+    up_body(op, G, buf0, buf1, aux, P, g0, up, J * G.T + I, 0);
 }
 
 template <class Op>
@@ -831,79 +694,6 @@ __device__ __forceinline__ void bridge_tile(const Op &op, const Geom &G, const t
     const int lo_w_shift = xb ? -2 : 0, hi_w_shift = xb ? 0 : -2;
     const S *seg[2] = {up + ((size_t)slot * 4 + lo_side) * NV * G.PS,
                        up + ((size_t)hi_slot * 4 + hi_side) * NV * G.PS};
-
-    if constexpr (Op::INPLACE_AFTER_AUX && !STG) {
-        // in place, one buffer; the strips of each level come into one half of
-        // the staging area by TMA during the level before it (copied into the
-        // level buffer once the level's first pass has read what they
-        // overwrite), and each level's bridge panels are gathered into the
-        // other half in the level's first pass and stored by TMA after it
-        S *buf = bufs[0];
-        const SmemPlan pl = smem_plan<Op>(n, 2, false);
-        S *stg_in = reinterpret_cast<S *>(smem_raw + pl.stage_off);
-        S *stg_out = stg_in + 4 * n * NV;
-        unsigned long long *bar = reinterpret_cast<unsigned long long *>(smem_raw + pl.bar_off);
-        S *oseg[2] = {br + ((size_t)slot * 4 + out_lo) * NV * G.PS,
-                      br + ((size_t)slot * 4 + out_hi) * NV * G.PS};
-        auto strip_pos = [&](int k, int which, int d, int p) {
-            const int ww = which ? h + k + d : h - 1 - k - d, uu = k + p;
-            const int x = xb ? ww : uu, y = xb ? uu : ww;
-            return (y + 1) * P + (x + 1);
-        };
-        auto out_pos = [&](int k, int which, int d, int p) {
-            const int uu = which ? n - 1 - k - d : k + d;
-            const int ww = h - k + (which ? hi_w_shift : lo_w_shift) + p;
-            const int x = xb ? ww : uu, y = xb ? uu : ww;
-            return (y + 1) * P + (x + 1);
-        };
-        if (threadIdx.x == 0) mbar_init(bar, 1);
-        __syncthreads();
-        unsigned phase = 0;
-        lines_load<S, NV>(seg, 2, n, 0, G.PS, stg_in, bar);
-        if (!block_wait_parity(bar, phase, err)) return;
-        phase ^= 1;
-        stage_to_buf<S, NV>(stg_in, buf, plane, 2, n,
-                            [&](int which, int d, int p) { return strip_pos(0, which, d, p); });
-        __syncthreads();
-        bool ok = true;
-        for (int k = 0; k < h && ok; ++k) {
-            const bool more = k + 1 < h;
-            const int L1 = n - 2 * k - 2;              // the next strips' line length
-            if (more)
-                lines_load<S, NV>(seg, 2, L1, 2 * (k + 1) * (n - k), G.PS, stg_in, bar);
-            const int L = 2 * k + 2, off = 2 * k * (k + 1);
-            buf_to_stage<S, NV>(buf, stg_out, plane, 2, L,
-                                [&](int which, int d, int p) { return out_pos(k, which, d, p); });
-            fence_async_shared();   // the staging writes before the TMA store reads them
-            if (more) {
-                const u64 g = g0 + k;
-                const int u0 = k + 1, uw = n - 2 * k - 2, w0 = h - k - 1, ww = 2 * k + 2;
-                auto mid = [&] {
-                    lines_store<S, NV>(oseg, 2, L, off, G.PS, stg_out);
-                    ok = block_wait_parity(bar, phase, err);
-                    phase ^= 1;
-                    if (ok)
-                        stage_to_buf<S, NV>(stg_in, buf, plane, 2, L1, [&](int which, int d, int p) {
-                            return strip_pos(k + 1, which, d, p);
-                        });
-                };
-                if (xb)
-                    compute_rect_mid(op, (int)(g % Op::NST), g, buf, buf, aux, P, w0, u0, ww, uw, mid);
-                else
-                    compute_rect_mid(op, (int)(g % Op::NST), g, buf, buf, aux, P, u0, w0, uw, ww, mid);
-            } else {
-                __syncthreads();
-                lines_store<S, NV>(oseg, 2, L, off, G.PS, stg_out);
-            }
-            if (threadIdx.x == 0) bulk_wait_read_all();   // staging free for the next level
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) {
-            bulk_wait_all();   // the panels complete before the block ends
-            mbar_inval(bar);
-        }
-        return;
-    }
 
     const S *stg = nullptr;
     if constexpr (STG) {
@@ -1029,57 +819,6 @@ __device__ __forceinline__ bool down_body(const Op &op, const Geom &G, unsigned 
     // east <- W of y-bridge(I+1,J), north <- S of x-bridge(I,J), south <- N of x-bridge(I,J+1)
     const S *seg[4] = {br + ((size_t)slot * 4 + 3) * NV * G.PS, br + ((size_t)east * 4 + 2) * NV * G.PS,
                        br + ((size_t)slot * 4 + 1) * NV * G.PS, br + ((size_t)south * 4 + 0) * NV * G.PS};
-    // element p of line d of ring side `side` at level k, in the level buffer
-    auto ring_pos = [&](int k, int side, int d, int p) {
-        int bx, by, ax, ay;
-        switch (side) {
-            case 0: bx = h - 1 - k - d; by = h - k - 2; ax = 0; ay = 1; break;   // west
-            case 1: bx = h + k + d; by = h - k; ax = 0; ay = 1; break;           // east
-            case 2: bx = h - k; by = h - 1 - k - d; ax = 1; ay = 0; break;       // north
-            default: bx = h - k - 2; by = h + k + d; ax = 1; ay = 0; break;      // south
-        }
-        return (by + 1 + p * ay) * P + (bx + 1 + p * ax);
-    };
-    if constexpr (Op::INPLACE_AFTER_AUX && !STG) {
-        // in place, one buffer; each level's ring (its two lines per side and
-        // plane contiguous in the bridge panels) is brought into the staging
-        // area by TMA during the level before it and copied into the level
-        // buffer once the level's first pass has read the neighbours it
-        // overwrites
-        S *buf = buf0;
-        const SmemPlan pl = smem_plan<Op>(n, 4, false);
-        S *stg = reinterpret_cast<S *>(smem_raw + pl.stage_off);
-        unsigned long long *bar = reinterpret_cast<unsigned long long *>(smem_raw + pl.bar_off);
-        if (threadIdx.x == 0) mbar_init(bar, 1);
-        __syncthreads();
-        unsigned phase = 0;
-        lines_load<S, NV>(seg, 4, 2, 0, G.PS, stg, bar);
-        if (!block_wait_parity(bar, phase, err)) return false;
-        phase ^= 1;
-        stage_to_buf<S, NV>(stg, buf, plane, 4, 2,
-                            [&](int side, int d, int p) { return ring_pos(0, side, d, p); });
-        __syncthreads();
-        bool ok = true;
-        for (int k = 0; k < h && ok; ++k) {
-            const bool more = k + 1 < h;
-            const int L1 = 2 * k + 4;                  // the next ring's line length
-            if (more) lines_load<S, NV>(seg, 4, L1, 2 * (k + 1) * (k + 2), G.PS, stg, bar);
-            const u64 g = g0 + k;
-            compute_rect_mid(op, (int)(g % Op::NST), g, buf, buf, aux, P, h - k - 1, h - k - 1,
-                             2 * k + 2, 2 * k + 2, [&] {
-                                 if (!more) return;
-                                 ok = block_wait_parity(bar, phase, err);
-                                 phase ^= 1;
-                                 if (ok)
-                                     stage_to_buf<S, NV>(stg, buf, plane, 4, L1, [&](int side, int d, int p) {
-                                         return ring_pos(k + 1, side, d, p);
-                                     });
-                             });
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) mbar_inval(bar);
-        return ok;
-    }
     const S *stg = nullptr;
     if constexpr (STG) {
         const SmemPlan pl = smem_plan<Op>(n, 4, true);
@@ -1177,7 +916,7 @@ __device__ __forceinline__ void octahedron_tile(const Op &op, const Geom &G,
         I = I + 1 == G.T ? 0 : I + 1;
         J = J + 1 == G.Q ? 0 : J + 1;
     }
-    up_body(op, G, buf0, buf1, aux, P, g0 + h, up, J * G.T + I, h & 1, smem_raw);
+    up_body(op, G, buf0, buf1, aux, P, g0 + h, up, J * G.T + I, h & 1);
 }
 
 template <class Op, bool STG>
