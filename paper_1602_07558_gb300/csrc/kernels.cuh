@@ -110,6 +110,20 @@ constexpr int kMaxSweptThreads = 512;
 // than the launch-per-phase kernels).
 constexpr int kMaxPersistentThreads = 512;
 
+// Launch bounds of the single-grid swept kernels per update: the largest block
+// and the blocks per SM its registers must allow. The FP64 heat kernels keep
+// to 32 registers a thread (four 512-thread blocks' worth), so that three
+// blocks of up to 512 threads per SM at tile 64, or eight of 256 at tile 32,
+// are never short of registers; the other updates may use more.
+template <class Op>
+struct SweptBounds {
+    static constexpr int kThreads = kMaxSweptThreads, kMinBlocks = 1;
+};
+template <>
+struct SweptBounds<HeatOp> {
+    static constexpr int kThreads = kMaxSweptThreads, kMinBlocks = 4;
+};
+
 __device__ __forceinline__ unsigned smem_u32(const void *p) {
     return (unsigned)__cvta_generic_to_shared(p);
 }
@@ -657,7 +671,7 @@ __device__ __forceinline__ void up_tile(const Op &op, const Geom &G, const typen
 }
 
 template <class Op>
-__global__ void __launch_bounds__(kMaxSweptThreads)
+__global__ void __launch_bounds__(SweptBounds<Op>::kThreads, SweptBounds<Op>::kMinBlocks)
 up_kernel(Op op, Geom G, const typename Op::S *state,
                                                  typename Op::S *up, int o, u64 g0) {
     up_tile(op, G, state, up, o, g0, blockIdx.x, blockIdx.y);
@@ -795,7 +809,7 @@ __device__ __forceinline__ void bridge_tile(const Op &op, const Geom &G, const t
 }
 
 template <class Op, bool STG>
-__global__ void __launch_bounds__(kMaxSweptThreads)
+__global__ void __launch_bounds__(SweptBounds<Op>::kThreads, SweptBounds<Op>::kMinBlocks)
 bridge_kernel(Op op, Geom G, const typename Op::S *up,
                                                      typename Op::S *br, u64 g0, int *err) {
     bridge_tile<Op, STG>(op, G, up, br, g0, err, blockIdx.x, blockIdx.y, blockIdx.z == 1);
@@ -920,7 +934,7 @@ __device__ __forceinline__ void octahedron_tile(const Op &op, const Geom &G,
 }
 
 template <class Op, bool STG>
-__global__ void __launch_bounds__(kMaxSweptThreads)
+__global__ void __launch_bounds__(SweptBounds<Op>::kThreads, SweptBounds<Op>::kMinBlocks)
 octahedron_kernel(Op op, Geom G, const typename Op::S *br,
                                                          typename Op::S *up, int o, u64 g0,
                                                          int *err) {
@@ -953,7 +967,7 @@ __device__ __forceinline__ void down_tile(const Op &op, const Geom &G, const typ
 }
 
 template <class Op, bool STG>
-__global__ void __launch_bounds__(kMaxSweptThreads)
+__global__ void __launch_bounds__(SweptBounds<Op>::kThreads, SweptBounds<Op>::kMinBlocks)
 down_kernel(Op op, Geom G, const typename Op::S *br,
                                                    typename Op::S *state, int o, u64 g0, int *err) {
     down_tile<Op, STG>(op, G, br, state, o, g0, err, blockIdx.x, blockIdx.y);

@@ -199,7 +199,7 @@ struct Launch {
         static const OpTable t = {Op::NV,      Op::NST,     (int)sizeof(S), &swept_smem_bytes<Op>,
                                   &naive,      &up,         &bridge,        &octahedron,
                                   &down,       Op::STAGE,   &swept_smem_for<Op>, &persistent,
-                                  kMaxSweptThreads, kMaxPersistentThreads};
+                                  SweptBounds<Op>::kThreads, kMaxPersistentThreads};
         return &t;
     }
 };
