@@ -54,16 +54,38 @@ __host__ __device__ inline int panel_stride(int n) { return ((n * n / 2 + n) + 7
 template <class Op>
 __host__ __device__ constexpr bool one_buffer() { return Op::INPLACE || Op::INPLACE_AFTER_AUX; }
 
+// Row pitch of a level's packed flux planes (Euler): W + 2, or W + 4 when
+// (W + 2) / 2 is even: an odd half-pitch keeps the 32 points of a column-pair
+// walk on 32 banks (4-byte fluxes).
+__host__ __device__ constexpr int flux_pitch(int W) { return ((W + 2) & 3) == 0 ? W + 4 : W + 2; }
+
+// Elements of one aux plane of a swept block. A level packs its aux values for
+// the rectangle it computes, grown by one: pair sums (heat, wave) with row
+// pitch W + 1 over H + 1 rows, fluxes (Euler) with row pitch flux_pitch(W) over
+// H + 2 rows. A bridge's levels (W + H = n) need at most (n/2 + 1)^2 and
+// (n/2 + 3)^2; the pyramids' largest level is the whole n x n tile.
+template <class Op>
+__host__ __device__ inline size_t aux_elems(int n, bool bridge) {
+    const size_t h = (size_t)n / 2;
+    if constexpr (Op::INPLACE_AFTER_AUX)
+        return bridge ? (h + 1) * (h + 1) : (size_t)(n + 1) * (n + 1);
+    else
+        return bridge ? (h + 3) * (h + 3) : (size_t)flux_pitch(n) * (n + 2);
+}
+
 // Dynamic shared memory of a swept block: level buffers (+ aux planes), then
-// (when staged) the block's input panels, then an mbarrier.
+// (when staged) the block's input panels, then an mbarrier. `bridge`: the plan
+// of a bridge block, whose levels are smaller than the tile.
 struct SmemPlan {
     size_t stage_off, bar_off, total;
 };
 template <class Op>
-__host__ __device__ inline SmemPlan smem_plan(int n, int stage_segments, bool staged) {
+__host__ __device__ inline SmemPlan smem_plan(int n, int stage_segments, bool staged,
+                                              bool bridge = false) {
     typedef typename Op::S S;
     const size_t P = (size_t)n + 2;
-    const size_t levels = (size_t)((one_buffer<Op>() ? 1 : 2) * Op::NV + Op::AUX) * P * P * sizeof(S);
+    const size_t levels = ((size_t)(one_buffer<Op>() ? 1 : 2) * Op::NV * P * P +
+                           (size_t)Op::AUX * aux_elems<Op>(n, bridge)) * sizeof(S);
     SmemPlan pl;
     pl.stage_off = (levels + 15) & ~(size_t)15;
     const size_t stage = staged ? (size_t)stage_segments * Op::NV * panel_stride(n) * sizeof(S) : 0;
@@ -294,7 +316,9 @@ __device__ __forceinline__ void compute_rect(const Op &op, int stage, u64 g,
 // with the same roundings as HeatOp::operator() (the pair sums commute).
 // Pass 2 reads only the centre and the pair sums, so it may write the level in
 // place (src == dst); `mid` runs after the barrier between the passes, when
-// no neighbour value of the level is read any more.
+// no neighbour value of the level is read any more. The pair sums of a level
+// are packed with row pitch W + 1 (entry e of pass 1 at aux[e]), so the aux
+// buffer needs only the largest (W + 1)(H + 1) of the block's levels.
 template <class Mid>
 __device__ __forceinline__ void compute_rect_mid(const HeatOp &op, int, u64, const double *src,
                                                  double *dst, double *aux, int P, int x0, int y0,
@@ -306,7 +330,7 @@ __device__ __forceinline__ void compute_rect_mid(const HeatOp &op, int, u64, con
     for (int e = threadIdx.x; e < cnt1; e += blockDim.x) {
         const int yy = div_small(e, rw1), xx = e - yy * W1;
         const int off = (y0 + yy) * P + (x0 + xx);      // point (x0-1+xx, y0-1+yy)
-        aux[off] = __dadd_rn(src[off + 1], src[off + P]);
+        aux[e] = __dadd_rn(src[off + 1], src[off + P]);
     }
     __syncthreads();
     mid();
@@ -314,8 +338,9 @@ __device__ __forceinline__ void compute_rect_mid(const HeatOp &op, int, u64, con
     for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
         const int yy = div_small(e, rw), xx = e - yy * W;
         const int off = (y0 + yy + 1) * P + (x0 + xx + 1);
+        const int a = e + yy;                            // Pr(x-1, y-1); Pr(x, y) at a + W + 2
         const double c = src[off];
-        const double sum = __dadd_rn(aux[off], aux[off - P - 1]);
+        const double sum = __dadd_rn(aux[a + W1 + 1], aux[a]);
         dst[off] = __fma_rn(op.r, __fma_rn(-4.0, c, sum), c);
     }
 }
@@ -374,32 +399,38 @@ __device__ __forceinline__ void compute_rect(const HeatKahanOp<SS> &op, int, u64
 // primitives per point), and each point then combines its neighbours' fluxes
 // (pass 2): each point's fluxes are used by its 4 neighbours instead of being
 // recomputed by each of them. Same values as EulerOp::operator().
+// The flux planes of a level are packed: row pitch A = flux_pitch(W), plane
+// pitch A (H + 2), so the aux buffer needs only the largest such rectangle of
+// the block's levels (a bridge's levels are far smaller than a tile).
 __device__ __forceinline__ void compute_rect(const EulerOp &op, int stage, u64, const double *src,
                                              double *dst, double *aux, int P, int x0, int y0,
                                              int W, int H) {
     const int plane = P * P, w0 = stage == 0 ? 0 : 4;
     if (W <= 0 || H <= 0) return;
+    const int A = flux_pitch(W), fp = A * (H + 2);
     for_each_point<false>(W + 2, H + 2, [&](int xx, int yy) {
         const int off = (y0 + yy) * P + (x0 + xx);     // point (x0-1+xx, y0-1+yy)
+        const int a = yy * A + xx;
         double F[4], G[4];
         op.fluxes(src[w0 * plane + off], src[(w0 + 1) * plane + off],
                   src[(w0 + 2) * plane + off], src[(w0 + 3) * plane + off], F, G);
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-            aux[c * plane + off] = F[c];
-            aux[(4 + c) * plane + off] = G[c];
+            aux[c * fp + a] = F[c];
+            aux[(4 + c) * fp + a] = G[c];
         }
     });
     __syncthreads();
     for_each_point<false>(W, H, [&](int xx, int yy) {
         const int off = (y0 + yy + 1) * P + (x0 + xx + 1);
+        const int a = (yy + 1) * A + xx + 1;
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             const double *Wc = src + (w0 + c) * plane + off;
-            const double *F = aux + c * plane + off, *G = aux + (4 + c) * plane + off;
+            const double *F = aux + c * fp + a, *G = aux + (4 + c) * fp + a;
             double res;
             op.combine(stage, c, Wc[0], Wc[1], Wc[-1], Wc[P], Wc[-P], __dsub_rn(F[1], F[-1]),
-                       __dsub_rn(G[P], G[-P]), src[c * plane + off], res);
+                       __dsub_rn(G[A], G[-A]), src[c * plane + off], res);
             // (in place, src == dst: the passed-through plane is already there)
             if (stage == 0) {
                 if (src != dst) dst[c * plane + off] = src[c * plane + off];
@@ -423,27 +454,30 @@ __device__ __forceinline__ void compute_rect(const EulerKahanOp<SS> &op, int sta
     float *aux = reinterpret_cast<float *>(aux_s);
     const int plane = P * P, w0 = stage == 0 ? 0 : 4;
     if (W <= 0 || H <= 0) return;
+    const int A = flux_pitch(W), fp = A * (H + 2);   // packed as for EulerOp
     for_each_point<sizeof(SS) == 4>(W + 2, H + 2, [&](int xx, int yy) {
         const int off = (y0 + yy) * P + (x0 + xx);     // point (x0-1+xx, y0-1+yy)
+        const int a = yy * A + xx;
         float F[4], G[4];
         op.fluxes(St::ld(src[w0 * plane + off]), St::ld(src[(w0 + 1) * plane + off]),
                   St::ld(src[(w0 + 2) * plane + off]), St::ld(src[(w0 + 3) * plane + off]), F, G);
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-            aux[c * plane + off] = F[c];
-            aux[(4 + c) * plane + off] = G[c];
+            aux[c * fp + a] = F[c];
+            aux[(4 + c) * fp + a] = G[c];
         }
     });
     __syncthreads();
     for_each_point<sizeof(SS) == 4>(W, H, [&](int xx, int yy) {
         const int off = (y0 + yy + 1) * P + (x0 + xx + 1);
+        const int a = (yy + 1) * A + xx + 1;
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             const SS *Wc = src + (w0 + c) * plane + off;
-            const float *F = aux + c * plane + off, *G = aux + (4 + c) * plane + off;
+            const float *F = aux + c * fp + a, *G = aux + (4 + c) * fp + a;
             const float L = op.rate(St::ld(Wc[0]), St::ld(Wc[1]), St::ld(Wc[-1]), St::ld(Wc[P]),
                                     St::ld(Wc[-P]), __fsub_rn(F[1], F[-1]),
-                                    __fsub_rn(G[P], G[-P]));
+                                    __fsub_rn(G[A], G[-A]));
             // (in place, src == dst: the passed-through planes are already there)
             if (stage == 0) {
                 dst[(4 + c) * plane + off] = op.midpoint(L, St::ld(src[c * plane + off]));
@@ -461,7 +495,8 @@ __device__ __forceinline__ void compute_rect(const EulerKahanOp<SS> &op, int sta
 }
 
 // Wave: the same pair-sum sharing as the heat update (pass 1 forms the
-// east+south pair sums of the rectangle grown by one into the aux plane), then
+// east+south pair sums of the rectangle grown by one into the aux buffer,
+// packed with row pitch W + 1), then
 // u' = (2u - u_old) + C^2 d, u_old' = u. Pass 2 reads only the centre's two
 // values and the pair sums, so it may write the level in place; `mid` runs
 // between the passes.
@@ -475,7 +510,7 @@ __device__ __forceinline__ void compute_rect_mid(const WaveOp &op, int, u64, con
     for (int e = threadIdx.x; e < cnt1; e += blockDim.x) {
         const int yy = div_small(e, rw1), xx = e - yy * W1;
         const int off = (y0 + yy) * P + (x0 + xx);      // point (x0-1+xx, y0-1+yy)
-        aux[off] = __dadd_rn(src[off + 1], src[off + P]);
+        aux[e] = __dadd_rn(src[off + 1], src[off + P]);
     }
     __syncthreads();
     mid();
@@ -483,8 +518,9 @@ __device__ __forceinline__ void compute_rect_mid(const WaveOp &op, int, u64, con
     for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
         const int yy = div_small(e, rw), xx = e - yy * W;
         const int off = (y0 + yy + 1) * P + (x0 + xx + 1);
+        const int a = e + yy;                            // packed as for the heat update
         const double c = src[off], old = src[plane + off];
-        const double d = __fma_rn(-4.0, c, __dadd_rn(aux[off], aux[off - P - 1]));
+        const double d = __fma_rn(-4.0, c, __dadd_rn(aux[a + W1 + 1], aux[a]));
         dst[off] = __fma_rn(op.C2, d, __dsub_rn(__dmul_rn(2.0, c), old));
         dst[plane + off] = c;
     }
@@ -712,7 +748,7 @@ __device__ __forceinline__ void bridge_tile(const Op &op, const Geom &G, const t
     const S *stg = nullptr;
     if constexpr (STG) {
         // the two input panels (every level) arrive in shared memory by TMA
-        const SmemPlan pl = smem_plan<Op>(n, 2, true);
+        const SmemPlan pl = smem_plan<Op>(n, 2, true, true);
         S *st = reinterpret_cast<S *>(smem_raw + pl.stage_off);
         unsigned long long *bar = reinterpret_cast<unsigned long long *>(smem_raw + pl.bar_off);
         if (threadIdx.x == 0) mbar_init(bar, 1);

@@ -46,11 +46,12 @@ struct OpTable {
 constexpr int kBlock = 256;
 
 // Dynamic shared memory of each swept kernel: the up kernel stages nothing,
-// the bridge stages 2 input panels, the octahedron and the final down 4.
+// the bridge stages 2 input panels (and packs smaller levels' aux values), the
+// octahedron and the final down 4. The persistent kernel takes the largest.
 template <class Op>
 inline size_t up_smem(int n) { return smem_plan<Op>(n, 0, false).total; }
 template <class Op>
-inline size_t bridge_smem(int n, bool stage) { return smem_plan<Op>(n, 2, stage).total; }
+inline size_t bridge_smem(int n, bool stage) { return smem_plan<Op>(n, 2, stage, true).total; }
 template <class Op>
 inline size_t down_smem(int n, bool stage) { return smem_plan<Op>(n, 4, stage).total; }
 template <class Op>

@@ -13,6 +13,10 @@ against the squares and rectangles each level computes and reads.
   the previous level computed and the level's own strip). The updates whose
   first pass reads the neighbours (heat, wave) copy the next ring only after
   that pass, so the overlap with the current ring's inner line is harmless.
+* Packed aux values: a level's pair sums (heat, wave) and fluxes (Euler) are
+  packed for its own rectangle; every level of a block fits the block's aux
+  buffer, the second pass finds each neighbour's value where the first pass
+  put it, and the flux pitch keeps a column-pair walk conflict-free.
 """
 import pytest
 
@@ -115,3 +119,76 @@ def test_in_place_bridge_panel_reads_see_only_the_current_level(n):
         for xb in (0, 1):
             assert bridge_panel_reads(n, k, xb) <= have, (n, k, xb)
 
+
+
+# ---- packed aux values of a level (pair sums; Euler fluxes), restated from
+# aux_elems, flux_pitch and the index formulas of the level computations
+
+def kernel_levels(n, kind):
+    """(W, H) of every level rectangle a block of the kind computes."""
+    h = n // 2
+    if kind == "up":
+        return [(n - 2 * k - 2, n - 2 * k - 2) for k in range(h - 1)]
+    if kind == "bridge":
+        out = []
+        for k in range(h - 1):
+            out += [(n - 2 * k - 2, 2 * k + 2), (2 * k + 2, n - 2 * k - 2)]
+        return out
+    return [(2 * k + 2, 2 * k + 2) for k in range(h)]          # down (and octahedron's down)
+
+
+def flux_pitch(W):
+    return W + 4 if (W + 2) % 4 == 0 else W + 2
+
+
+def aux_elems(n, bridge, pair_sums):
+    h = n // 2
+    if pair_sums:
+        return (h + 1) ** 2 if bridge else (n + 1) ** 2
+    return (h + 3) ** 2 if bridge else flux_pitch(n) * (n + 2)
+
+
+EVEN_SIZES = [4, 6, 8, 10, 16, 18, 32, 34, 64, 128]
+
+
+@pytest.mark.parametrize("n", EVEN_SIZES)
+def test_packed_pair_sums_fit_and_index_the_right_neighbours(n):
+    for kind in ("up", "bridge", "down"):
+        cap = aux_elems(n, kind == "bridge", True)
+        for W, H in kernel_levels(n, kind):
+            W1, cnt1 = W + 1, (W + 1) * (H + 1)
+            assert cnt1 <= cap, (n, kind, W, H)
+            # pass 1: entry e holds Pr(x0 - 1 + e % W1, y0 - 1 + e // W1)
+            where = {e: (e % W1 - 1, e // W1 - 1) for e in range(cnt1)}
+            for e in range(W * H):
+                yy, xx = divmod(e, W)
+                a = e + yy
+                assert where[a] == (xx - 1, yy - 1)        # Pr(x-1, y-1)
+                assert where[a + W1 + 1] == (xx, yy)        # Pr(x, y)
+
+
+@pytest.mark.parametrize("n", EVEN_SIZES)
+def test_packed_flux_planes_fit_index_and_keep_column_pairs_on_distinct_banks(n):
+    for kind in ("up", "bridge", "down"):
+        cap = aux_elems(n, kind == "bridge", False)
+        for W, H in kernel_levels(n, kind):
+            A = flux_pitch(W)
+            assert A >= W + 2 and A * (H + 2) <= cap, (n, kind, W, H)
+            # pass 2 of point (xx, yy): its own slot and the four neighbours'
+            for yy in range(H):
+                for xx in range(W):
+                    a = (yy + 1) * A + xx + 1
+                    for d in (1, -1, A, -A):
+                        q = a + d
+                        assert 0 <= q < A * (H + 2) and q % A < W + 2
+            # 32 consecutive points of a column pair (16 rows x 2 columns) in
+            # 4-byte fluxes fall on 32 different banks
+            if H + 2 >= 16:
+                banks = {(r * A + c) % 32 for r in range(16) for c in range(2)}
+                assert len(banks) == 32, (n, W, A)
+
+
+@pytest.mark.parametrize("n", EVEN_SIZES)
+def test_bridge_plan_is_not_larger_than_the_pyramids(n):
+    for pair_sums in (True, False):
+        assert aux_elems(n, True, pair_sums) <= aux_elems(n, False, pair_sums)
