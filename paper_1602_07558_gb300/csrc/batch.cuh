@@ -19,7 +19,8 @@ struct GridDesc {
 };
 // Tile and block tables hold (grid index, tile or block index within the grid).
 
-template <class Op>
+// NC > 0: every grid of the launch's class has tile side NC (see fixed_tile).
+template <class Op, int NC = 0>
 __global__ void __launch_bounds__(kMaxSweptThreads) batch_up_kernel(const GridDesc *grids,
                                                                     const int2 *tile_grid,
                                                                     const typename Op::S *state,
@@ -28,10 +29,10 @@ __global__ void __launch_bounds__(kMaxSweptThreads) batch_up_kernel(const GridDe
     const int2 e = tile_grid[blockIdx.x];
     const GridDesc gd = grids[e.x];
     const int J = e.y / gd.G.T, I = e.y - J * gd.G.T;
-    up_tile(Op(gd.c), gd.G, state + gd.state_off, up + gd.panel_off, o, g0, I, J);
+    up_tile(Op(gd.c), fixed_tile<NC>(gd.G), state + gd.state_off, up + gd.panel_off, o, g0, I, J);
 }
 
-template <class Op, bool STG>
+template <class Op, bool STG, int NC = 0>
 __global__ void __launch_bounds__(kMaxSweptThreads) batch_bridge_kernel(const GridDesc *grids,
                                                                         const int2 *tile_grid,
                                                                         const typename Op::S *up,
@@ -40,30 +41,30 @@ __global__ void __launch_bounds__(kMaxSweptThreads) batch_bridge_kernel(const Gr
     const int2 e = tile_grid[blockIdx.x];
     const GridDesc gd = grids[e.x];
     const int J = e.y / gd.G.T, I = e.y - J * gd.G.T;
-    bridge_tile<Op, STG>(Op(gd.c), gd.G, up + gd.panel_off, br + gd.panel_off, g0, err, I, J,
-                         blockIdx.y == 1);
+    bridge_tile<Op, STG>(Op(gd.c), fixed_tile<NC>(gd.G), up + gd.panel_off, br + gd.panel_off,
+                         g0, err, I, J, blockIdx.y == 1);
 }
 
-template <class Op, bool STG>
+template <class Op, bool STG, int NC = 0>
 __global__ void __launch_bounds__(kMaxSweptThreads) batch_octahedron_kernel(
     const GridDesc *grids, const int2 *tile_grid, const typename Op::S *br, typename Op::S *up,
     int o, u64 g0, int *err) {
     const int2 e = tile_grid[blockIdx.x];
     const GridDesc gd = grids[e.x];
     const int J = e.y / gd.G.T, I = e.y - J * gd.G.T;
-    octahedron_tile<Op, STG>(Op(gd.c), gd.G, br + gd.panel_off, up + gd.panel_off, o, g0, err, I,
-                             J);
+    octahedron_tile<Op, STG>(Op(gd.c), fixed_tile<NC>(gd.G), br + gd.panel_off,
+                             up + gd.panel_off, o, g0, err, I, J);
 }
 
-template <class Op, bool STG>
+template <class Op, bool STG, int NC = 0>
 __global__ void __launch_bounds__(kMaxSweptThreads) batch_down_kernel(
     const GridDesc *grids, const int2 *tile_grid, const typename Op::S *br, typename Op::S *state,
     int o, u64 g0, int *err) {
     const int2 e = tile_grid[blockIdx.x];
     const GridDesc gd = grids[e.x];
     const int J = e.y / gd.G.T, I = e.y - J * gd.G.T;
-    down_tile<Op, STG>(Op(gd.c), gd.G, br + gd.panel_off, state + gd.state_off, o, g0, err, I,
-                       J);
+    down_tile<Op, STG>(Op(gd.c), fixed_tile<NC>(gd.G), br + gd.panel_off, state + gd.state_off,
+                       o, g0, err, I, J);
 }
 
 // Persistent form over every tile of a class: the tile table lists each
@@ -87,13 +88,13 @@ struct GridTiles {
     }
 };
 
-template <class Op, bool STG>
+template <class Op, bool STG, int NC = 0>
 __global__ void __launch_bounds__(256) batch_persistent_kernel(
     const GridDesc *grids, const int2 *tile_grid, int ntiles, int n, typename Op::S *state,
     typename Op::S *up, typename Op::S *br, int *stage, int *queue, int H, u64 g0, int *err) {
     // the update's constants come from each item's grid (TileAt::c)
-    persistent_loop<Op, STG>(Op(grids[0].c), GridTiles{grids, tile_grid}, ntiles, n, state, up,
-                             br, stage, queue, H, g0, err, 0, kPersistSpinLimit);
+    persistent_loop<Op, STG, NC>(Op(grids[0].c), GridTiles{grids, tile_grid}, ntiles, n, state,
+                                 up, br, stage, queue, H, g0, err, 0, kPersistSpinLimit);
 }
 
 // One sub-step of every grid in a block table: block b covers a 32 x 8 patch of
@@ -158,21 +159,28 @@ struct BatchLaunch {
     static cudaError_t up(const GridDesc *d, const int2 *tg, int ntiles, int n, const void *state,
                           void *upp, int o, u64 g0, cudaStream_t st) {
         const size_t sm = up_smem<Op>(n);
-        cudaError_t e = allow_smem(batch_up_kernel<Op>, sm);
-        if (e != cudaSuccess) return e;
-        batch_up_kernel<Op><<<ntiles, kBlock, sm, st>>>(d, tg, (const S *)state, (S *)upp, o, g0);
-        return cudaGetLastError();
+        return with_tile<Op>(n, [&](auto nc) {
+            constexpr int NC = decltype(nc)::value;
+            cudaError_t e = allow_smem(batch_up_kernel<Op, NC>, sm);
+            if (e != cudaSuccess) return e;
+            batch_up_kernel<Op, NC><<<ntiles, kBlock, sm, st>>>(d, tg, (const S *)state, (S *)upp,
+                                                                o, g0);
+            return cudaGetLastError();
+        });
     }
     template <bool STG>
     static cudaError_t bridge_t(const GridDesc *d, const int2 *tg, int ntiles, int n,
                                 const void *upp, void *br, u64 g0, int *err, int threads,
                                 cudaStream_t st) {
         const size_t sm = bridge_smem<Op>(n, STG);
-        cudaError_t e = allow_smem(batch_bridge_kernel<Op, STG>, sm);
-        if (e != cudaSuccess) return e;
-        batch_bridge_kernel<Op, STG><<<dim3(ntiles, 2), threads, sm, st>>>(d, tg, (const S *)upp,
-                                                                           (S *)br, g0, err);
-        return cudaGetLastError();
+        return with_tile<Op>(n, [&](auto nc) {
+            constexpr int NC = decltype(nc)::value;
+            cudaError_t e = allow_smem(batch_bridge_kernel<Op, STG, NC>, sm);
+            if (e != cudaSuccess) return e;
+            batch_bridge_kernel<Op, STG, NC><<<dim3(ntiles, 2), threads, sm, st>>>(
+                d, tg, (const S *)upp, (S *)br, g0, err);
+            return cudaGetLastError();
+        });
     }
     static cudaError_t bridge(const GridDesc *d, const int2 *tg, int ntiles, int n,
                               const void *upp, void *br, u64 g0, int *err, const Tuning &tn,
@@ -184,11 +192,14 @@ struct BatchLaunch {
     static cudaError_t oct_t(const GridDesc *d, const int2 *tg, int ntiles, int n, const void *br,
                              void *upp, int o, u64 g0, int *err, int threads, cudaStream_t st) {
         const size_t sm = down_smem<Op>(n, STG);
-        cudaError_t e = allow_smem(batch_octahedron_kernel<Op, STG>, sm);
-        if (e != cudaSuccess) return e;
-        batch_octahedron_kernel<Op, STG><<<ntiles, threads, sm, st>>>(d, tg, (const S *)br,
-                                                                      (S *)upp, o, g0, err);
-        return cudaGetLastError();
+        return with_tile<Op>(n, [&](auto nc) {
+            constexpr int NC = decltype(nc)::value;
+            cudaError_t e = allow_smem(batch_octahedron_kernel<Op, STG, NC>, sm);
+            if (e != cudaSuccess) return e;
+            batch_octahedron_kernel<Op, STG, NC><<<ntiles, threads, sm, st>>>(
+                d, tg, (const S *)br, (S *)upp, o, g0, err);
+            return cudaGetLastError();
+        });
     }
     static cudaError_t octahedron(const GridDesc *d, const int2 *tg, int ntiles, int n,
                                   const void *br, void *upp, int o, u64 g0, int *err,
@@ -200,11 +211,14 @@ struct BatchLaunch {
     static cudaError_t down_t(const GridDesc *d, const int2 *tg, int ntiles, int n, const void *br,
                               void *state, int o, u64 g0, int *err, int threads, cudaStream_t st) {
         const size_t sm = down_smem<Op>(n, STG);
-        cudaError_t e = allow_smem(batch_down_kernel<Op, STG>, sm);
-        if (e != cudaSuccess) return e;
-        batch_down_kernel<Op, STG><<<ntiles, threads, sm, st>>>(d, tg, (const S *)br,
-                                                                (S *)state, o, g0, err);
-        return cudaGetLastError();
+        return with_tile<Op>(n, [&](auto nc) {
+            constexpr int NC = decltype(nc)::value;
+            cudaError_t e = allow_smem(batch_down_kernel<Op, STG, NC>, sm);
+            if (e != cudaSuccess) return e;
+            batch_down_kernel<Op, STG, NC><<<ntiles, threads, sm, st>>>(d, tg, (const S *)br,
+                                                                        (S *)state, o, g0, err);
+            return cudaGetLastError();
+        });
     }
     static cudaError_t down(const GridDesc *d, const int2 *tg, int ntiles, int n, const void *br,
                             void *state, int o, u64 g0, int *err, const Tuning &tn,
@@ -217,20 +231,24 @@ struct BatchLaunch {
                                     void *state, void *upp, void *br, int *sched, int H, u64 g0,
                                     int *err, int threads, cudaStream_t st) {
         const size_t sm = down_smem<Op>(n, STG);
-        cudaError_t e = allow_smem(batch_persistent_kernel<Op, STG>, sm);
-        if (e != cudaSuccess) return e;
-        int per_sm = 0, dev = 0, nsm = 0;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                 &per_sm, batch_persistent_kernel<Op, STG>, threads, sm)) != cudaSuccess)
-            return e;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        const long long nitems = persistent_items(ntiles, H);
-        long long grid = (long long)(per_sm > 0 ? per_sm : 1) * nsm;
-        if (grid > nitems) grid = nitems;
-        batch_persistent_kernel<Op, STG><<<(int)grid, threads, sm, st>>>(
-            d, tg, ntiles, n, (S *)state, (S *)upp, (S *)br, sched, sched + ntiles, H, g0, err);
-        return cudaGetLastError();
+        return with_tile<Op>(n, [&](auto nc) {
+            constexpr int NC = decltype(nc)::value;
+            const auto kern = batch_persistent_kernel<Op, STG, NC>;
+            cudaError_t e = allow_smem(kern, sm);
+            if (e != cudaSuccess) return e;
+            int per_sm = 0, dev = 0, nsm = 0;
+            if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, sm)) !=
+                cudaSuccess)
+                return e;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+            const long long nitems = persistent_items(ntiles, H);
+            long long grid = (long long)(per_sm > 0 ? per_sm : 1) * nsm;
+            if (grid > nitems) grid = nitems;
+            kern<<<(int)grid, threads, sm, st>>>(d, tg, ntiles, n, (S *)state, (S *)upp, (S *)br,
+                                                 sched, sched + ntiles, H, g0, err);
+            return cudaGetLastError();
+        });
     }
     static cudaError_t persistent(const GridDesc *d, const int2 *tg, int ntiles, int n,
                                   void *state, void *upp, void *br, int *sched, int H, u64 g0,

@@ -1,24 +1,13 @@
-// Instantiation unit: the batched kernels for the point updates that support
-// batches (heat FP64, heat with compensated binary32 update in binary32 or
-// bfloat16 storage, the hash test update, and Euler in FP64 or in binary32 with
-// binary32 or bfloat16 storage), and the per-grid wave-speed reduction that
-// fixes each Euler grid's time step.
+// Instantiation unit: the batched kernels of heat FP64, the hash test update and
+// Euler FP64, and the per-grid wave-speed reduction that fixes each Euler
+// grid's time step. The compensated binary32 forms (built for several tile
+// sides) have units of their own: batch_heat_kahan.cu, batch_euler_kahan.cu.
 #include "batch.cuh"
 
 namespace swept {
 const BatchTable *batchtable_heat() { return BatchLaunch<HeatOp>::table(); }
-const BatchTable *batchtable_heat_kahan_f32() { return BatchLaunch<HeatKahanOp<float>>::table(); }
-const BatchTable *batchtable_heat_kahan_bf16() {
-    return BatchLaunch<HeatKahanOp<__nv_bfloat16>>::table();
-}
 const BatchTable *batchtable_hash() { return BatchLaunch<HashOp>::table(); }
 const BatchTable *batchtable_euler() { return BatchLaunch<EulerOp>::table(); }
-const BatchTable *batchtable_euler_kahan_f32() {
-    return BatchLaunch<EulerKahanOp<float>>::table();
-}
-const BatchTable *batchtable_euler_kahan_bf16() {
-    return BatchLaunch<EulerKahanOp<__nv_bfloat16>>::table();
-}
 
 namespace {
 

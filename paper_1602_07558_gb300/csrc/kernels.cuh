@@ -50,6 +50,17 @@ struct Geom {
 
 __host__ __device__ inline int panel_stride(int n) { return ((n * n / 2 + n) + 7) & ~7; }
 
+// The geometry a swept kernel works with: NC > 0 fixes the tile side at compile
+// time (the launch picks such an instantiation only when G.n == NC), so every
+// shared-memory pitch and plane offset of the inlined level code is a constant
+// and folds into the load and store instructions; NC = 0 keeps G.n.
+template <int NC>
+__device__ __forceinline__ Geom fixed_tile(const Geom &G) {
+    Geom g = G;
+    if constexpr (NC > 0) g.n = NC;
+    return g;
+}
+
 // Updates whose levels are computed in place in one level buffer.
 template <class Op>
 __host__ __device__ constexpr bool one_buffer() { return Op::INPLACE || Op::INPLACE_AFTER_AUX; }
@@ -706,11 +717,10 @@ __device__ __forceinline__ void up_tile(const Op &op, const Geom &G, const typen
     up_body(op, G, buf0, buf1, aux, P, g0, up, J * G.T + I, 0);
 }
 
-template <class Op>
+template <class Op, int NC = 0>
 __global__ void __launch_bounds__(SweptBounds<Op>::kThreads, SweptBounds<Op>::kMinBlocks)
-up_kernel(Op op, Geom G, const typename Op::S *state,
-                                                 typename Op::S *up, int o, u64 g0) {
-    up_tile(op, G, state, up, o, g0, blockIdx.x, blockIdx.y);
+up_kernel(Op op, Geom G, const typename Op::S *state, typename Op::S *up, int o, u64 g0) {
+    up_tile(op, fixed_tile<NC>(G), state, up, o, g0, blockIdx.x, blockIdx.y);
 }
 
 // ------------------------------------------- Bridges (Algorithms 2 and 3)
@@ -844,11 +854,11 @@ __device__ __forceinline__ void bridge_tile(const Op &op, const Geom &G, const t
     }
 }
 
-template <class Op, bool STG>
+template <class Op, bool STG, int NC = 0>
 __global__ void __launch_bounds__(SweptBounds<Op>::kThreads, SweptBounds<Op>::kMinBlocks)
-bridge_kernel(Op op, Geom G, const typename Op::S *up,
-                                                     typename Op::S *br, u64 g0, int *err) {
-    bridge_tile<Op, STG>(op, G, up, br, g0, err, blockIdx.x, blockIdx.y, blockIdx.z == 1);
+bridge_kernel(Op op, Geom G, const typename Op::S *up, typename Op::S *br, u64 g0, int *err) {
+    bridge_tile<Op, STG>(op, fixed_tile<NC>(G), up, br, g0, err, blockIdx.x, blockIdx.y,
+                         blockIdx.z == 1);
 }
 
 // --------------------------------------------- DownwardPyramid (Algorithm 5)
@@ -969,12 +979,11 @@ __device__ __forceinline__ void octahedron_tile(const Op &op, const Geom &G,
     up_body(op, G, buf0, buf1, aux, P, g0 + h, up, J * G.T + I, h & 1);
 }
 
-template <class Op, bool STG>
+template <class Op, bool STG, int NC = 0>
 __global__ void __launch_bounds__(SweptBounds<Op>::kThreads, SweptBounds<Op>::kMinBlocks)
-octahedron_kernel(Op op, Geom G, const typename Op::S *br,
-                                                         typename Op::S *up, int o, u64 g0,
-                                                         int *err) {
-    octahedron_tile<Op, STG>(op, G, br, up, o, g0, err, blockIdx.x, blockIdx.y);
+octahedron_kernel(Op op, Geom G, const typename Op::S *br, typename Op::S *up, int o, u64 g0,
+                  int *err) {
+    octahedron_tile<Op, STG>(op, fixed_tile<NC>(G), br, up, o, g0, err, blockIdx.x, blockIdx.y);
 }
 
 // K4: final Down of an advance; writes the tile at level h to the state.
@@ -1002,11 +1011,11 @@ __device__ __forceinline__ void down_tile(const Op &op, const Geom &G, const typ
     }
 }
 
-template <class Op, bool STG>
+template <class Op, bool STG, int NC = 0>
 __global__ void __launch_bounds__(SweptBounds<Op>::kThreads, SweptBounds<Op>::kMinBlocks)
-down_kernel(Op op, Geom G, const typename Op::S *br,
-                                                   typename Op::S *state, int o, u64 g0, int *err) {
-    down_tile<Op, STG>(op, G, br, state, o, g0, err, blockIdx.x, blockIdx.y);
+down_kernel(Op op, Geom G, const typename Op::S *br, typename Op::S *state, int o, u64 g0,
+            int *err) {
+    down_tile<Op, STG>(op, fixed_tile<NC>(G), br, state, o, g0, err, blockIdx.x, blockIdx.y);
 }
 
 // ------------------------------------------------------- persistent form
@@ -1086,7 +1095,7 @@ __host__ __device__ inline long long persistent_items(long long NT, long long H)
 // `trace` (nullptr: none) receives, per work item, the SM clock cycles its
 // block spent waiting for the item's neighbourhood (trace[2 item]) and running
 // the item up to its release (trace[2 item + 1]).
-template <class Op, bool STG, class Loc>
+template <class Op, bool STG, int NC = 0, class Loc>
 __device__ __forceinline__ void persistent_loop(const Op &op, const Loc &at, int NT, int n,
                                                 typename Op::S *state, typename Op::S *upp,
                                                 typename Op::S *br, int *stage, int *queue, int H,
@@ -1094,7 +1103,7 @@ __device__ __forceinline__ void persistent_loop(const Op &op, const Loc &at, int
                                                 unsigned *trace = nullptr) {
     __shared__ int s_item, s_fail;
     long long t_start = 0, t_ready = 0;
-    const int h = n / 2;
+    const int h = (NC > 0 ? NC : n) / 2;
     const int nitems = (int)persistent_items(NT, H);
     for (;;) {
         if (threadIdx.x == 0) {
@@ -1127,7 +1136,7 @@ __device__ __forceinline__ void persistent_loop(const Op &op, const Loc &at, int
             }
         }
         const TileAt w = at(t);
-        const Geom &G = w.G;
+        const Geom G = fixed_tile<NC>(w.G);
         const int I = w.I, J = w.J;
         const Op opi = w.c ? Op(w.c) : op;
         if (trace && threadIdx.x == 0) t_start = clock64();
@@ -1190,14 +1199,14 @@ __device__ __forceinline__ void persistent_loop(const Op &op, const Loc &at, int
     }
 }
 
-template <class Op, bool STG>
-__global__ void __launch_bounds__(kMaxPersistentThreads) persistent_kernel(Op op, Geom G, typename Op::S *state,
-                                                         typename Op::S *upp, typename Op::S *br,
-                                                         int *stage, int *queue, int H, u64 g0,
-                                                         int *err, int first, long long spin_limit,
-                                                         unsigned *trace) {
-    persistent_loop<Op, STG>(op, OneGrid{G}, G.T * G.Q, G.n, state, upp, br, stage, queue, H, g0,
-                             err, first, spin_limit, trace);
+template <class Op, bool STG, int NC = 0>
+__global__ void __launch_bounds__(kMaxPersistentThreads)
+persistent_kernel(Op op, Geom G, typename Op::S *state, typename Op::S *upp, typename Op::S *br,
+                  int *stage, int *queue, int H, u64 g0, int *err, int first,
+                  long long spin_limit, unsigned *trace) {
+    const Geom Gf = fixed_tile<NC>(G);
+    persistent_loop<Op, STG, NC>(op, OneGrid{Gf}, Gf.T * Gf.Q, Gf.n, state, upp, br, stage, queue,
+                                 H, g0, err, first, spin_limit, trace);
 }
 
 }  // namespace swept

@@ -59,6 +59,33 @@ inline size_t swept_smem_bytes(int n) { return down_smem<Op>(n, Op::STAGE); }
 template <class Op>
 inline size_t swept_smem_for(int n, bool stage) { return down_smem<Op>(n, stage); }
 
+// Updates whose swept kernels are also built for fixed tile sides 16, 32 and 64
+// (the tile side then a compile-time constant: see fixed_tile). The binary32 /
+// bfloat16 forms are bound by instruction issue, where the constant pitches
+// save the address arithmetic of every shared-memory access; the FP64 forms
+// are bound by the FP64 pipe and keep one instantiation.
+template <class Op>
+struct FixedTiles : std::false_type {};
+template <class SS>
+struct FixedTiles<HeatKahanOp<SS>> : std::true_type {};
+template <class SS>
+struct FixedTiles<EulerKahanOp<SS>> : std::true_type {};
+
+// Calls f(std::integral_constant<int, NC>) with NC = n when the update has an
+// instantiation for tile side n, else NC = 0 (tile side read at run time).
+template <class Op, class F>
+inline cudaError_t with_tile(int n, F &&f) {
+    if constexpr (FixedTiles<Op>::value) {
+        switch (n) {
+            case 16: return f(std::integral_constant<int, 16>());
+            case 32: return f(std::integral_constant<int, 32>());
+            case 64: return f(std::integral_constant<int, 64>());
+            default: break;
+        }
+    }
+    return f(std::integral_constant<int, 0>());
+}
+
 // Raise the dynamic shared-memory limit of a kernel when it needs more than
 // the default 48 KB (the attribute is per kernel and per device).
 template <class K>
@@ -112,21 +139,27 @@ struct Launch {
     static cudaError_t up(const Geom &G, const double *c, const void *state, void *up, int o,
                           u64 g0, cudaStream_t st) {
         const size_t sm = up_smem<Op>(G.n);
-        cudaError_t e = allow_smem(up_kernel<Op>, sm);
-        if (e != cudaSuccess) return e;
-        up_kernel<Op><<<dim3(G.T, G.Q), kBlock, sm, st>>>(Op(c), G, (const S *)state, (S *)up, o,
-                                                          g0);
-        return cudaGetLastError();
+        return with_tile<Op>(G.n, [&](auto nc) {
+            constexpr int NC = decltype(nc)::value;
+            cudaError_t e = allow_smem(up_kernel<Op, NC>, sm);
+            if (e != cudaSuccess) return e;
+            up_kernel<Op, NC><<<dim3(G.T, G.Q), kBlock, sm, st>>>(Op(c), G, (const S *)state,
+                                                                  (S *)up, o, g0);
+            return cudaGetLastError();
+        });
     }
     template <bool STG>
     static cudaError_t bridge_t(const Geom &G, const double *c, const void *up, void *br, u64 g0,
                                 int *err, int threads, cudaStream_t st) {
         const size_t sm = bridge_smem<Op>(G.n, STG);
-        cudaError_t e = allow_smem(bridge_kernel<Op, STG>, sm);
-        if (e != cudaSuccess) return e;
-        bridge_kernel<Op, STG><<<dim3(G.T, G.Q, 2), threads, sm, st>>>(Op(c), G, (const S *)up,
-                                                                       (S *)br, g0, err);
-        return cudaGetLastError();
+        return with_tile<Op>(G.n, [&](auto nc) {
+            constexpr int NC = decltype(nc)::value;
+            cudaError_t e = allow_smem(bridge_kernel<Op, STG, NC>, sm);
+            if (e != cudaSuccess) return e;
+            bridge_kernel<Op, STG, NC><<<dim3(G.T, G.Q, 2), threads, sm, st>>>(
+                Op(c), G, (const S *)up, (S *)br, g0, err);
+            return cudaGetLastError();
+        });
     }
     static cudaError_t bridge(const Geom &G, const double *c, const void *up, void *br, u64 g0,
                               int *err, const Tuning &tn, cudaStream_t st) {
@@ -137,11 +170,14 @@ struct Launch {
     static cudaError_t octahedron_t(const Geom &G, const double *c, const void *br, void *up,
                                     int o, u64 g0, int *err, int threads, cudaStream_t st) {
         const size_t sm = down_smem<Op>(G.n, STG);
-        cudaError_t e = allow_smem(octahedron_kernel<Op, STG>, sm);
-        if (e != cudaSuccess) return e;
-        octahedron_kernel<Op, STG><<<dim3(G.T, G.Q), threads, sm, st>>>(Op(c), G, (const S *)br,
-                                                                        (S *)up, o, g0, err);
-        return cudaGetLastError();
+        return with_tile<Op>(G.n, [&](auto nc) {
+            constexpr int NC = decltype(nc)::value;
+            cudaError_t e = allow_smem(octahedron_kernel<Op, STG, NC>, sm);
+            if (e != cudaSuccess) return e;
+            octahedron_kernel<Op, STG, NC><<<dim3(G.T, G.Q), threads, sm, st>>>(
+                Op(c), G, (const S *)br, (S *)up, o, g0, err);
+            return cudaGetLastError();
+        });
     }
     static cudaError_t octahedron(const Geom &G, const double *c, const void *br, void *up, int o,
                                   u64 g0, int *err, const Tuning &tn, cudaStream_t st) {
@@ -152,11 +188,14 @@ struct Launch {
     static cudaError_t down_t(const Geom &G, const double *c, const void *br, void *state, int o,
                               u64 g0, int *err, int threads, cudaStream_t st) {
         const size_t sm = down_smem<Op>(G.n, STG);
-        cudaError_t e = allow_smem(down_kernel<Op, STG>, sm);
-        if (e != cudaSuccess) return e;
-        down_kernel<Op, STG><<<dim3(G.T, G.Q), threads, sm, st>>>(Op(c), G, (const S *)br,
-                                                                  (S *)state, o, g0, err);
-        return cudaGetLastError();
+        return with_tile<Op>(G.n, [&](auto nc) {
+            constexpr int NC = decltype(nc)::value;
+            cudaError_t e = allow_smem(down_kernel<Op, STG, NC>, sm);
+            if (e != cudaSuccess) return e;
+            down_kernel<Op, STG, NC><<<dim3(G.T, G.Q), threads, sm, st>>>(
+                Op(c), G, (const S *)br, (S *)state, o, g0, err);
+            return cudaGetLastError();
+        });
     }
     static cudaError_t down(const Geom &G, const double *c, const void *br, void *state, int o,
                             u64 g0, int *err, const Tuning &tn, cudaStream_t st) {
@@ -169,23 +208,25 @@ struct Launch {
                                     int first, long long spin_limit, unsigned *trace,
                                     cudaStream_t st) {
         const size_t sm = down_smem<Op>(G.n, STG);
-        cudaError_t e = allow_smem(persistent_kernel<Op, STG>, sm);
-        if (e != cudaSuccess) return e;
-        int per_sm = 0, dev = 0, nsm = 0;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel<Op, STG>,
-                                                               threads, sm)) != cudaSuccess)
-            return e;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        const long long nitems = persistent_items((long long)G.T * G.Q, H);
-        long long grid = (long long)(per_sm > 0 ? per_sm : 1) * nsm;
-        if (grid > nitems) grid = nitems;
-        const int NT = G.T * G.Q;
-        persistent_kernel<Op, STG><<<(int)grid, threads, sm, st>>>(Op(c), G, (S *)state,
-                                                                   (S *)upp, (S *)br, sched,
-                                                                   sched + NT, H, g0, err, first,
-                                                                   spin_limit, trace);
-        return cudaGetLastError();
+        return with_tile<Op>(G.n, [&](auto nc) {
+            constexpr int NC = decltype(nc)::value;
+            const auto kern = persistent_kernel<Op, STG, NC>;
+            cudaError_t e = allow_smem(kern, sm);
+            if (e != cudaSuccess) return e;
+            int per_sm = 0, dev = 0, nsm = 0;
+            if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, sm)) !=
+                cudaSuccess)
+                return e;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+            const long long nitems = persistent_items((long long)G.T * G.Q, H);
+            long long grid = (long long)(per_sm > 0 ? per_sm : 1) * nsm;
+            if (grid > nitems) grid = nitems;
+            const int NT = G.T * G.Q;
+            kern<<<(int)grid, threads, sm, st>>>(Op(c), G, (S *)state, (S *)upp, (S *)br, sched,
+                                                 sched + NT, H, g0, err, first, spin_limit, trace);
+            return cudaGetLastError();
+        });
     }
     static cudaError_t persistent(const Geom &G, const double *c, void *state, void *upp,
                                   void *br, int *sched, int H, u64 g0, int *err,
