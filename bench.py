@@ -86,10 +86,10 @@ WORKLOADS = {
     "euler2048_f32": Workload("euler_kahan", "f32", 2048, 5_000, 32, (GAMMA, CFL, KAPPA),
                               "euler", 2, "Euler 2048x2048, binary32 storage and arithmetic, "
                               "Kahan-compensated update, midpoint RK2, CFL 0.3, 5000 steps"),
-    "euler2048_bf16": Workload("euler_kahan", "bf16", 2048, 5_000, 16, (GAMMA, CFL, KAPPA),
+    "euler2048_bf16": Workload("euler_kahan", "bf16", 2048, 5_000, 32, (GAMMA, CFL, KAPPA),
                                "euler", 2, "Euler 2048x2048, bfloat16 storage, binary32 "
                                "arithmetic, Kahan-compensated update, midpoint RK2, CFL 0.3, "
-                               "5000 steps", 128),
+                               "5000 steps", 256),
     "batch1024": Workload("heat_kahan", "f32", 0, 20_000, 0, (0.2,), "batch", 3,
                           "1024 independent periodic grids, nx and ny uniform in {32,48,...,512} "
                           "(seed 3), heat with binary32 storage and Kahan-compensated update, "

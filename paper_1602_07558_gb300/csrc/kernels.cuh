@@ -406,10 +406,12 @@ __device__ __forceinline__ void compute_rect(const HeatKahanOp<SS> &op, int, u64
 }
 
 // Euler: the x- and y-fluxes of every point of the rectangle grown by one are
-// formed once per level into 8 aux planes (pass 1, one evaluation of the
+// formed once per level into 6 aux planes (pass 1, one evaluation of the
 // primitives per point), and each point then combines its neighbours' fluxes
 // (pass 2): each point's fluxes are used by its 4 neighbours instead of being
-// recomputed by each of them. Same values as EulerOp::operator().
+// recomputed by each of them. Same values as EulerOp::operator(). The density
+// fluxes F0 = m and G0 = q are the stage's own input values, so pass 2 reads
+// them from the level buffer and only F1-F3 and G1-G3 are stored.
 // The flux planes of a level are packed: row pitch A = flux_pitch(W), plane
 // pitch A (H + 2), so the aux buffer needs only the largest such rectangle of
 // the block's levels (a bridge's levels are far smaller than a tile).
@@ -426,9 +428,9 @@ __device__ __forceinline__ void compute_rect(const EulerOp &op, int stage, u64, 
         op.fluxes(src[w0 * plane + off], src[(w0 + 1) * plane + off],
                   src[(w0 + 2) * plane + off], src[(w0 + 3) * plane + off], F, G);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            aux[c * fp + a] = F[c];
-            aux[(4 + c) * fp + a] = G[c];
+        for (int c = 1; c < 4; ++c) {
+            aux[(c - 1) * fp + a] = F[c];
+            aux[(2 + c) * fp + a] = G[c];
         }
     });
     __syncthreads();
@@ -438,10 +440,19 @@ __device__ __forceinline__ void compute_rect(const EulerOp &op, int stage, u64, 
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             const double *Wc = src + (w0 + c) * plane + off;
-            const double *F = aux + c * fp + a, *G = aux + (4 + c) * fp + a;
+            double dF, dG;
+            if (c == 0) {   // F0 = m, G0 = q
+                const double *M = src + (w0 + 1) * plane + off, *Q = src + (w0 + 2) * plane + off;
+                dF = __dsub_rn(M[1], M[-1]);
+                dG = __dsub_rn(Q[P], Q[-P]);
+            } else {
+                const double *F = aux + (c - 1) * fp + a, *G = aux + (2 + c) * fp + a;
+                dF = __dsub_rn(F[1], F[-1]);
+                dG = __dsub_rn(G[A], G[-A]);
+            }
             double res;
-            op.combine(stage, c, Wc[0], Wc[1], Wc[-1], Wc[P], Wc[-P], __dsub_rn(F[1], F[-1]),
-                       __dsub_rn(G[A], G[-A]), src[c * plane + off], res);
+            op.combine(stage, c, Wc[0], Wc[1], Wc[-1], Wc[P], Wc[-P], dF, dG,
+                       src[c * plane + off], res);
             // (in place, src == dst: the passed-through plane is already there)
             if (stage == 0) {
                 if (src != dst) dst[c * plane + off] = src[c * plane + off];
@@ -455,8 +466,9 @@ __device__ __forceinline__ void compute_rect(const EulerOp &op, int stage, u64, 
 }
 
 // Euler in binary32 with reduced-precision storage: the same two passes as
-// EulerOp (binary32 fluxes of the grown rectangle in the aux planes, then the
-// per-point combination). Same values as EulerKahanOp::operator().
+// EulerOp (binary32 fluxes F1-F3, G1-G3 of the grown rectangle in the aux
+// planes, then the per-point combination). Same values as
+// EulerKahanOp::operator().
 template <class SS>
 __device__ __forceinline__ void compute_rect(const EulerKahanOp<SS> &op, int stage, u64,
                                              const SS *src, SS *dst, SS *aux_s, int P, int x0,
@@ -473,9 +485,9 @@ __device__ __forceinline__ void compute_rect(const EulerKahanOp<SS> &op, int sta
         op.fluxes(St::ld(src[w0 * plane + off]), St::ld(src[(w0 + 1) * plane + off]),
                   St::ld(src[(w0 + 2) * plane + off]), St::ld(src[(w0 + 3) * plane + off]), F, G);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            aux[c * fp + a] = F[c];
-            aux[(4 + c) * fp + a] = G[c];
+        for (int c = 1; c < 4; ++c) {
+            aux[(c - 1) * fp + a] = F[c];
+            aux[(2 + c) * fp + a] = G[c];
         }
     });
     __syncthreads();
@@ -485,10 +497,18 @@ __device__ __forceinline__ void compute_rect(const EulerKahanOp<SS> &op, int sta
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             const SS *Wc = src + (w0 + c) * plane + off;
-            const float *F = aux + c * fp + a, *G = aux + (4 + c) * fp + a;
+            float dF, dG;
+            if (c == 0) {   // F0 = m, G0 = q
+                const SS *M = src + (w0 + 1) * plane + off, *Q = src + (w0 + 2) * plane + off;
+                dF = __fsub_rn(St::ld(M[1]), St::ld(M[-1]));
+                dG = __fsub_rn(St::ld(Q[P]), St::ld(Q[-P]));
+            } else {
+                const float *F = aux + (c - 1) * fp + a, *G = aux + (2 + c) * fp + a;
+                dF = __fsub_rn(F[1], F[-1]);
+                dG = __fsub_rn(G[A], G[-A]);
+            }
             const float L = op.rate(St::ld(Wc[0]), St::ld(Wc[1]), St::ld(Wc[-1]), St::ld(Wc[P]),
-                                    St::ld(Wc[-P]), __fsub_rn(F[1], F[-1]),
-                                    __fsub_rn(G[A], G[-A]));
+                                    St::ld(Wc[-P]), dF, dG);
             // (in place, src == dst: the passed-through planes are already there)
             if (stage == 0) {
                 dst[(4 + c) * plane + off] = op.midpoint(L, St::ld(src[c * plane + off]));

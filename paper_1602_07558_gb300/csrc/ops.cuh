@@ -111,8 +111,9 @@ struct HeatKahanOp {
 template <class SS>
 struct EulerKahanOp {
     typedef SS S;
-    // aux: the 8 binary32 flux planes of a level, counted in SS elements
-    static constexpr int NV = 12, NST = 2, AUX = 8 * (int)(sizeof(float) / sizeof(SS));
+    // aux: the 6 binary32 flux planes of a level (F1-F3, G1-G3), counted in SS
+    // elements
+    static constexpr int NV = 12, NST = 2, AUX = 6 * (int)(sizeof(float) / sizeof(SS));
     // bfloat16 panels are staged by TMA (element copies of 2 bytes are slow)
     static constexpr bool STAGE = sizeof(SS) == 2;
     // each stage writes only planes it reads at the centre alone, so a
@@ -312,7 +313,7 @@ struct Wide2Op {
 // Host-precomputed constants c[] = {gamma-1, cx, cy, kax, kay, tau0, tau1}.
 struct EulerOp {
     typedef double S;
-    static constexpr int NV = 8, NST = 2, AUX = 8;   // aux: F and G of a level
+    static constexpr int NV = 8, NST = 2, AUX = 6;   // aux: F1-F3 and G1-G3 of a level
     static constexpr bool STAGE = false;
     // each stage writes only planes it reads at the centre alone, so a
     // level can be computed in place in one level buffer
