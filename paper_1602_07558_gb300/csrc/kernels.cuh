@@ -405,14 +405,18 @@ __device__ __forceinline__ void compute_rect(const HeatKahanOp<SS> &op, int, u64
     }
 }
 
-// Euler: the x- and y-fluxes of every point of the rectangle grown by one are
-// formed once per level into 6 aux planes (pass 1, one evaluation of the
-// primitives per point), and each point then combines its neighbours' fluxes
-// (pass 2): each point's fluxes are used by its 4 neighbours instead of being
-// recomputed by each of them. Same values as EulerOp::operator(). The density
-// fluxes F0 = m and G0 = q are the stage's own input values, so pass 2 reads
-// them from the level buffer and only F1-F3 and G1-G3 are stored.
-// The flux planes of a level are packed: row pitch A = flux_pitch(W), plane
+// Euler: the primitives (u, v, p, E + p) of every point of the rectangle grown
+// by one are formed once per level into 4 aux planes (pass 1: one division and
+// one evaluation of the pressure per point), and each point then forms the
+// fluxes of its 4 neighbours from their primitives and conserved values (pass
+// 2): F1-F3 at its east and west neighbours, G1-G3 at its south and north
+// ones (one or two operations each), F0 = m and G0 = q being the level's own
+// values. A point's primitives serve its 4 neighbours instead of being
+// recomputed by each of them, and 4 planes (instead of 8 flux planes) keep the
+// block small enough for two (FP64) or three (binary32) blocks per SM at
+// n = 32. Same values as EulerOp::operator() (each flux is the same sequence
+// of operations on the same operands).
+// The aux planes of a level are packed: row pitch A = flux_pitch(W), plane
 // pitch A (H + 2), so the aux buffer needs only the largest such rectangle of
 // the block's levels (a bridge's levels are far smaller than a tile).
 __device__ __forceinline__ void compute_rect(const EulerOp &op, int stage, u64, const double *src,
@@ -424,35 +428,34 @@ __device__ __forceinline__ void compute_rect(const EulerOp &op, int stage, u64, 
     for_each_point<false>(W + 2, H + 2, [&](int xx, int yy) {
         const int off = (y0 + yy) * P + (x0 + xx);     // point (x0-1+xx, y0-1+yy)
         const int a = yy * A + xx;
-        double F[4], G[4];
-        op.fluxes(src[w0 * plane + off], src[(w0 + 1) * plane + off],
-                  src[(w0 + 2) * plane + off], src[(w0 + 3) * plane + off], F, G);
-#pragma unroll
-        for (int c = 1; c < 4; ++c) {
-            aux[(c - 1) * fp + a] = F[c];
-            aux[(2 + c) * fp + a] = G[c];
-        }
+        double u, v, pr, Ep;
+        op.prims(src[w0 * plane + off], src[(w0 + 1) * plane + off],
+                 src[(w0 + 2) * plane + off], src[(w0 + 3) * plane + off], u, v, pr, Ep);
+        aux[a] = u;
+        aux[fp + a] = v;
+        aux[2 * fp + a] = pr;
+        aux[3 * fp + a] = Ep;
     });
     __syncthreads();
     for_each_point<false>(W, H, [&](int xx, int yy) {
         const int off = (y0 + yy + 1) * P + (x0 + xx + 1);
         const int a = (yy + 1) * A + xx + 1;
+        const double *M = src + (w0 + 1) * plane + off, *Q = src + (w0 + 2) * plane + off;
+        double FE[4], FW[4], GS[4], GN[4];
+        op.xflux_p(M[1], Q[1], aux[a + 1], aux[2 * fp + a + 1], aux[3 * fp + a + 1], FE);
+        op.xflux_p(M[-1], Q[-1], aux[a - 1], aux[2 * fp + a - 1], aux[3 * fp + a - 1], FW);
+        op.yflux_p(M[P], Q[P], aux[fp + a + A], aux[2 * fp + a + A], aux[3 * fp + a + A], GS);
+        op.yflux_p(M[-P], Q[-P], aux[fp + a - A], aux[2 * fp + a - A], aux[3 * fp + a - A], GN);
+        FE[0] = M[1];
+        FW[0] = M[-1];
+        GS[0] = Q[P];
+        GN[0] = Q[-P];
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             const double *Wc = src + (w0 + c) * plane + off;
-            double dF, dG;
-            if (c == 0) {   // F0 = m, G0 = q
-                const double *M = src + (w0 + 1) * plane + off, *Q = src + (w0 + 2) * plane + off;
-                dF = __dsub_rn(M[1], M[-1]);
-                dG = __dsub_rn(Q[P], Q[-P]);
-            } else {
-                const double *F = aux + (c - 1) * fp + a, *G = aux + (2 + c) * fp + a;
-                dF = __dsub_rn(F[1], F[-1]);
-                dG = __dsub_rn(G[A], G[-A]);
-            }
             double res;
-            op.combine(stage, c, Wc[0], Wc[1], Wc[-1], Wc[P], Wc[-P], dF, dG,
-                       src[c * plane + off], res);
+            op.combine(stage, c, Wc[0], Wc[1], Wc[-1], Wc[P], Wc[-P], __dsub_rn(FE[c], FW[c]),
+                       __dsub_rn(GS[c], GN[c]), src[c * plane + off], res);
             // (in place, src == dst: the passed-through plane is already there)
             if (stage == 0) {
                 if (src != dst) dst[c * plane + off] = src[c * plane + off];
@@ -466,8 +469,8 @@ __device__ __forceinline__ void compute_rect(const EulerOp &op, int stage, u64, 
 }
 
 // Euler in binary32 with reduced-precision storage: the same two passes as
-// EulerOp (binary32 fluxes F1-F3, G1-G3 of the grown rectangle in the aux
-// planes, then the per-point combination). Same values as
+// EulerOp (binary32 primitives of the grown rectangle in the aux planes, then
+// the per-point fluxes and combination). Same values as
 // EulerKahanOp::operator().
 template <class SS>
 __device__ __forceinline__ void compute_rect(const EulerKahanOp<SS> &op, int stage, u64,
@@ -481,34 +484,37 @@ __device__ __forceinline__ void compute_rect(const EulerKahanOp<SS> &op, int sta
     for_each_point<sizeof(SS) == 4>(W + 2, H + 2, [&](int xx, int yy) {
         const int off = (y0 + yy) * P + (x0 + xx);     // point (x0-1+xx, y0-1+yy)
         const int a = yy * A + xx;
-        float F[4], G[4];
-        op.fluxes(St::ld(src[w0 * plane + off]), St::ld(src[(w0 + 1) * plane + off]),
-                  St::ld(src[(w0 + 2) * plane + off]), St::ld(src[(w0 + 3) * plane + off]), F, G);
-#pragma unroll
-        for (int c = 1; c < 4; ++c) {
-            aux[(c - 1) * fp + a] = F[c];
-            aux[(2 + c) * fp + a] = G[c];
-        }
+        float u, v, pr, Ep;
+        op.prims(St::ld(src[w0 * plane + off]), St::ld(src[(w0 + 1) * plane + off]),
+                 St::ld(src[(w0 + 2) * plane + off]), St::ld(src[(w0 + 3) * plane + off]), u, v,
+                 pr, Ep);
+        aux[a] = u;
+        aux[fp + a] = v;
+        aux[2 * fp + a] = pr;
+        aux[3 * fp + a] = Ep;
     });
     __syncthreads();
     for_each_point<sizeof(SS) == 4>(W, H, [&](int xx, int yy) {
         const int off = (y0 + yy + 1) * P + (x0 + xx + 1);
         const int a = (yy + 1) * A + xx + 1;
+        const SS *M = src + (w0 + 1) * plane + off, *Q = src + (w0 + 2) * plane + off;
+        const float mE = St::ld(M[1]), mW = St::ld(M[-1]), mS = St::ld(M[P]), mN = St::ld(M[-P]);
+        const float qE = St::ld(Q[1]), qW = St::ld(Q[-1]), qS = St::ld(Q[P]), qN = St::ld(Q[-P]);
+        float FE[4], FW[4], GS[4], GN[4];
+        op.xflux(mE, qE, aux[a + 1], aux[2 * fp + a + 1], aux[3 * fp + a + 1], FE);
+        op.xflux(mW, qW, aux[a - 1], aux[2 * fp + a - 1], aux[3 * fp + a - 1], FW);
+        op.yflux(mS, qS, aux[fp + a + A], aux[2 * fp + a + A], aux[3 * fp + a + A], GS);
+        op.yflux(mN, qN, aux[fp + a - A], aux[2 * fp + a - A], aux[3 * fp + a - A], GN);
+        FE[0] = mE;
+        FW[0] = mW;
+        GS[0] = qS;
+        GN[0] = qN;
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             const SS *Wc = src + (w0 + c) * plane + off;
-            float dF, dG;
-            if (c == 0) {   // F0 = m, G0 = q
-                const SS *M = src + (w0 + 1) * plane + off, *Q = src + (w0 + 2) * plane + off;
-                dF = __fsub_rn(St::ld(M[1]), St::ld(M[-1]));
-                dG = __fsub_rn(St::ld(Q[P]), St::ld(Q[-P]));
-            } else {
-                const float *F = aux + (c - 1) * fp + a, *G = aux + (2 + c) * fp + a;
-                dF = __fsub_rn(F[1], F[-1]);
-                dG = __fsub_rn(G[A], G[-A]);
-            }
             const float L = op.rate(St::ld(Wc[0]), St::ld(Wc[1]), St::ld(Wc[-1]), St::ld(Wc[P]),
-                                    St::ld(Wc[-P]), dF, dG);
+                                    St::ld(Wc[-P]), __fsub_rn(FE[c], FW[c]),
+                                    __fsub_rn(GS[c], GN[c]));
             // (in place, src == dst: the passed-through planes are already there)
             if (stage == 0) {
                 dst[(4 + c) * plane + off] = op.midpoint(L, St::ld(src[c * plane + off]));

@@ -111,9 +111,9 @@ struct HeatKahanOp {
 template <class SS>
 struct EulerKahanOp {
     typedef SS S;
-    // aux: the 6 binary32 flux planes of a level (F1-F3, G1-G3), counted in SS
-    // elements
-    static constexpr int NV = 12, NST = 2, AUX = 6 * (int)(sizeof(float) / sizeof(SS));
+    // aux: the 4 binary32 primitive planes of a level (u, v, p, E + p), counted
+    // in SS elements
+    static constexpr int NV = 12, NST = 2, AUX = 4 * (int)(sizeof(float) / sizeof(SS));
     // bfloat16 panels are staged by TMA (element copies of 2 bytes are slow)
     static constexpr bool STAGE = sizeof(SS) == 2;
     // each stage writes only planes it reads at the centre alone, so a
@@ -125,21 +125,37 @@ struct EulerKahanOp {
         : gm1((float)c[0]), cx((float)c[1]), cy((float)c[2]), kax((float)c[3]),
           kay((float)c[4]), tau0((float)c[5]), tau1((float)c[6]) {}
 
-    __device__ __forceinline__ void fluxes(float r, float m, float q, float E, float *F,
-                                           float *G) const {
+    // primitives u = m/rho, v = q/rho, p and E + p of one point
+    __device__ __forceinline__ void prims(float r, float m, float q, float E, float &u, float &v,
+                                          float &pr, float &Ep) const {
         const float iv = __fdiv_rn(1.0f, r);
-        const float u = __fmul_rn(m, iv), v = __fmul_rn(q, iv);
+        u = __fmul_rn(m, iv);
+        v = __fmul_rn(q, iv);
         const float ke = __fmul_rn(0.5f, __fmaf_rn(m, u, __fmul_rn(q, v)));
-        const float pr = __fmul_rn(gm1, __fsub_rn(E, ke));
-        const float Ep = __fadd_rn(E, pr);
-        F[0] = m;
+        pr = __fmul_rn(gm1, __fsub_rn(E, ke));
+        Ep = __fadd_rn(E, pr);
+    }
+    // F1-F3 and G1-G3 of a point from its primitives (F0 = m, G0 = q)
+    __device__ __forceinline__ void xflux(float m, float q, float u, float pr, float Ep,
+                                          float *F) const {
         F[1] = __fmaf_rn(m, u, pr);
         F[2] = __fmul_rn(q, u);
         F[3] = __fmul_rn(Ep, u);
-        G[0] = q;
+    }
+    __device__ __forceinline__ void yflux(float m, float q, float v, float pr, float Ep,
+                                          float *G) const {
         G[1] = __fmul_rn(m, v);
         G[2] = __fmaf_rn(q, v, pr);
         G[3] = __fmul_rn(Ep, v);
+    }
+    __device__ __forceinline__ void fluxes(float r, float m, float q, float E, float *F,
+                                           float *G) const {
+        float u, v, pr, Ep;
+        prims(r, m, q, E, u, v, pr, Ep);
+        F[0] = m;
+        xflux(m, q, u, pr, Ep, F);
+        G[0] = q;
+        yflux(m, q, v, pr, Ep, G);
     }
     // L of one conserved variable from the stencil values and flux differences
     __device__ __forceinline__ float rate(float wc, float wE, float wW, float wS, float wN,
@@ -313,7 +329,7 @@ struct Wide2Op {
 // Host-precomputed constants c[] = {gamma-1, cx, cy, kax, kay, tau0, tau1}.
 struct EulerOp {
     typedef double S;
-    static constexpr int NV = 8, NST = 2, AUX = 6;   // aux: F1-F3 and G1-G3 of a level
+    static constexpr int NV = 8, NST = 2, AUX = 4;   // aux: u, v, p, E + p of a level
     static constexpr bool STAGE = false;
     // each stage writes only planes it reads at the centre alone, so a
     // level can be computed in place in one level buffer
@@ -332,28 +348,24 @@ struct EulerOp {
         pr = __dmul_rn(gm1, __dsub_rn(E, ke));
         Ep = __dadd_rn(E, pr);
     }
-    __device__ __forceinline__ void xflux(double r, double m, double q, double E, double *F) const {
-        double u, v, pr, Ep;
-        prims(r, m, q, E, u, v, pr, Ep);
-        F[0] = m;
+    // F1-F3 and G1-G3 of a point from its primitives (F0 = m, G0 = q)
+    __device__ __forceinline__ void xflux_p(double m, double q, double u, double pr, double Ep,
+                                            double *F) const {
         F[1] = __fma_rn(m, u, pr);
         F[2] = __dmul_rn(q, u);
         F[3] = __dmul_rn(Ep, u);
     }
-    // F and G of one point from one evaluation of its primitives (the same
-    // values xflux and yflux give)
-    __device__ __forceinline__ void fluxes(double r, double m, double q, double E, double *F,
-                                           double *G) const {
-        double u, v, pr, Ep;
-        prims(r, m, q, E, u, v, pr, Ep);
-        F[0] = m;
-        F[1] = __fma_rn(m, u, pr);
-        F[2] = __dmul_rn(q, u);
-        F[3] = __dmul_rn(Ep, u);
-        G[0] = q;
+    __device__ __forceinline__ void yflux_p(double m, double q, double v, double pr, double Ep,
+                                            double *G) const {
         G[1] = __dmul_rn(m, v);
         G[2] = __fma_rn(q, v, pr);
         G[3] = __dmul_rn(Ep, v);
+    }
+    __device__ __forceinline__ void xflux(double r, double m, double q, double E, double *F) const {
+        double u, v, pr, Ep;
+        prims(r, m, q, E, u, v, pr, Ep);
+        F[0] = m;
+        xflux_p(m, q, u, pr, Ep, F);
     }
     // the stage update of one point from its fluxes' differences (shared by the
     // per-point operator below and the swept level computation)
@@ -371,9 +383,7 @@ struct EulerOp {
         double u, v, pr, Ep;
         prims(r, m, q, E, u, v, pr, Ep);
         G[0] = q;
-        G[1] = __dmul_rn(m, v);
-        G[2] = __fma_rn(q, v, pr);
-        G[3] = __dmul_rn(Ep, v);
+        yflux_p(m, q, v, pr, Ep, G);
     }
     template <class A>
     __device__ __forceinline__ void operator()(int stage, u64, const A &a, S *out) const {
