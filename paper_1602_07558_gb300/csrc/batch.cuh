@@ -242,9 +242,8 @@ struct BatchLaunch {
                 return e;
             cudaGetDevice(&dev);
             cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-            const long long nitems = persistent_items(ntiles, H);
-            long long grid = (long long)(per_sm > 0 ? per_sm : 1) * nsm;
-            if (grid > nitems) grid = nitems;
+            const long long grid =
+                persistent_grid(per_sm, nsm, ntiles, persistent_items(ntiles, H));
             kern<<<(int)grid, threads, sm, st>>>(d, tg, ntiles, n, (S *)state, (S *)upp, (S *)br,
                                                  sched, sched + ntiles, H, g0, err);
             return cudaGetLastError();

@@ -86,6 +86,20 @@ inline cudaError_t with_tile(int n, F &&f) {
     return f(std::integral_constant<int, 0>());
 }
 
+// Blocks of a persistent launch: every block that fits at once, but no more
+// than 3 per tile (one half cycle's two bridges and octahedron of every tile
+// can then run together). The items are handed out in order, so a block
+// beyond that would only take an item of a later phase and poll its
+// neighbourhood flags, adding traffic to the flags and the queue that the
+// items on the critical path wait behind (small grids, where the tiles are
+// fewer than the SMs).
+inline long long persistent_grid(int per_sm, int nsm, long long ntiles, long long nitems) {
+    long long grid = (long long)(per_sm > 0 ? per_sm : 1) * nsm;
+    if (grid > 3 * ntiles) grid = 3 * ntiles;
+    if (grid > nitems) grid = nitems;
+    return grid > 0 ? grid : 1;
+}
+
 // Raise the dynamic shared-memory limit of a kernel when it needs more than
 // the default 48 KB (the attribute is per kernel and per device).
 template <class K>
@@ -219,10 +233,8 @@ struct Launch {
                 return e;
             cudaGetDevice(&dev);
             cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-            const long long nitems = persistent_items((long long)G.T * G.Q, H);
-            long long grid = (long long)(per_sm > 0 ? per_sm : 1) * nsm;
-            if (grid > nitems) grid = nitems;
             const int NT = G.T * G.Q;
+            const long long grid = persistent_grid(per_sm, nsm, NT, persistent_items(NT, H));
             kern<<<(int)grid, threads, sm, st>>>(Op(c), G, (S *)state, (S *)upp, (S *)br, sched,
                                                  sched + NT, H, g0, err, first, spin_limit, trace);
             return cudaGetLastError();
