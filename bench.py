@@ -355,12 +355,18 @@ def bridge_updates(n):
 
 
 # DRAM traffic (read + write bytes) per tile of one octahedron launch, from one
-# ncu capture of the same kernel on a 2048 x 2048 grid (1024 tiles of 64), scaled to a
-# launch by its number of tiles (reads equal the algorithmic panel bytes there;
-# part of the writes is still in L2 when the kernel ends). Kernels without a
-# capture of their current version report None.
+# ncu capture of the same kernel (the grid side it was taken on, 1024 or 2048),
+# scaled to a launch by its number of tiles (reads equal the algorithmic panel
+# bytes there; part of the writes may still be in L2 when the kernel ends).
+# Kernels without a capture of their current version report None.
 OCT_TRAFFIC_PER_TILE = {
-    ("heat", "f64", 64): (69.219328e6 + 27.585536e6) / 1024,
+    ("heat", "f64", 64): ((69.219072e6 + 27.767552e6) / 1024, 2048),
+    ("heat_kahan", "f32", 64): ((69.225728e6 + 21.248512e6) / 1024, 2048),
+    ("heat_kahan", "bf16", 64): ((34.620416e6 + 0.21504e6) / 1024, 2048),
+    ("euler_rk2", "f64", 32): ((570.50624e6 + 534.359296e6) / 4096, 2048),
+    ("euler_kahan", "f32", 32): ((427.944448e6 + 393.367296e6) / 4096, 2048),
+    ("euler_kahan", "bf16", 32): ((213.97376e6 + 162.021888e6) / 4096, 2048),
+    ("wave", "f64", 32): ((35.664896e6 + 2.827776e6) / 1024, 1024),
 }
 
 # Algorithmic work of one point update (one point advanced one sub-step),
@@ -439,13 +445,13 @@ def roofline(w, kern, peaks, esize, nvars):
     upd = octahedron_updates(n) * tiles            # point updates (sub-steps) per launch
     hbm_bytes = 2 * 4 * (n * n // 2 + n) * nvars * esize * tiles
     total_ms = sum(v[1] for v in kern.values())
-    per_tile = OCT_TRAFFIC_PER_TILE.get((w.op, w.dtype, n))
+    per_tile, cap_grid = OCT_TRAFFIC_PER_TILE.get((w.op, w.dtype, n), (None, None))
     out = {"kernel": "octahedron", "avg_launch_ms": avg_ms, "updates_per_launch": upd,
            "hbm_bytes_per_launch": hbm_bytes,
            "share_of_kernel_time": ms / total_ms if total_ms else None,
            "traffic": per_tile * tiles if per_tile else None,
            "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the same "
-                              "kernel at 2048x2048, scaled by tiles")
+                              f"kernel at {cap_grid}x{cap_grid}, scaled by tiles")
            if per_tile else None}
     out.update(bounds(w, esize, upd, hbm_bytes, avg_ms * 1e-3, peaks))
     bl, bms = kern["bridge"]
