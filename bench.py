@@ -25,6 +25,10 @@ class, against the batched naive path and against looping single-grid runs);
 batch1024_euler (the same 1,024 grid sizes with the binary32 Euler form, each
 grid's own time step, 2,000 steps).
 
+The default run (headline workload, N = 1, no size flags) then measures the
+other workloads, each in a child process with the same timing rules, and adds
+their results to the line as ``secondary`` (``--no-secondary`` skips them).
+
 With N > 1 (torchrun, one process per GPU) every rank advances its own
 independent grid ("replicas only"), the timed region is bracketed by a barrier,
 the time is the max over ranks and ``value`` counts the cells of all ranks.
@@ -132,6 +136,9 @@ def parse():
                    help="run each advance (swept and naive) as a captured CUDA graph")
     p.add_argument("--persistent", action="store_true",
                    help="swept arm: one persistent launch per advance")
+    p.add_argument("--no-secondary", action="store_true",
+                   help="default run: skip the other workloads' lines (each measured in a "
+                        "child process of its own)")
     p.add_argument("--launch-per-phase", action="store_true",
                    help="swept arm: one launch per phase (the default of most workloads)")
     a = p.parse_args()
@@ -645,7 +652,67 @@ def main():
         dist.barrier()
         dist.destroy_process_group()
     if result is not None:
+        if world == 1 and args.workload == DEFAULT_WORKLOAD and not args.no_secondary and \
+                not any(f"--{k}" in sys.argv for k in ("grid", "nsteps", "tile", "threads")):
+            result["secondary"] = secondary_lines()
         print(json.dumps(result), flush=True)
+
+
+# The other workloads, measured after the headline by the default run, each by
+# this script in a child process with the same timing rules (3 warm-up and 3
+# timed steps, L2 flushed between them, clocks sampled) in the workload's
+# default form. The long runs take fewer steps than the workload names: the
+# time per step does not depend on the step count (one first Up and one final
+# Down per advance). The state is compared with the CPU oracle over the first
+# steps (--quick-check); the headline line carries the full-length comparison.
+DEFAULT_WORKLOAD = "heat4096"
+SECONDARY = (
+    ("heat64", ()), ("heat64", ("--graph",)),
+    ("heat2048_f32", ("--nsteps", "10000")), ("heat2048_bf16", ("--nsteps", "10000")),
+    ("wave1024", ()),
+    ("euler2048", ("--nsteps", "500")), ("euler2048_f32", ("--nsteps", "500")),
+    ("euler2048_bf16", ("--nsteps", "500")),
+    ("batch1024", ("--nsteps", "2000")), ("batch1024_euler", ("--nsteps", "200")),
+)
+
+
+def secondary_lines(timeout_s=300):
+    import subprocess
+    out = []
+    for name, extra in SECONDARY:
+        cmd = [sys.executable, os.path.abspath(__file__), "--workload", name, "--no-cpu",
+               "--quick-check", "--no-secondary", "--steps", "3", "--warmup", "3", *extra]
+        entry = {"workload": name, "args": " ".join(extra)}
+        try:
+            r = subprocess.run(cmd, capture_output=True, text=True, timeout=timeout_s,
+                               cwd=ROOT)
+            lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+            if r.returncode != 0 or not lines:
+                entry["error"] = f"exit {r.returncode}: {r.stderr.strip()[-300:]}"
+                out.append(entry)
+                continue
+            d = json.loads(lines[-1])
+        except (subprocess.TimeoutExpired, ValueError) as e:
+            entry["error"] = f"{type(e).__name__}: {e}"[:300]
+            out.append(entry)
+            continue
+        rf = d.get("roofline") or {}
+        cfg = d.get("config") or {}
+        entry.update({
+            "describe": cfg.get("workload"), "nsteps": cfg.get("nsteps"),
+            "tile": cfg.get("tile"), "persistent": cfg.get("persistent"),
+            "cuda_graph": cfg.get("cuda_graph"), "value": d.get("value"), "unit": d.get("unit"),
+            "ms_per_step": d.get("ms_per_step"),
+            "naive": (d.get("naive") or {}).get("value"),
+            "speedup_vs_naive": d.get("speedup_vs_naive"),
+            "swept_equals_naive_bitwise": d.get("swept_equals_naive_bitwise"),
+            "roofline": {k: rf.get(k) for k in ("bound", "frac", "unit", "traffic")} if rf else None,
+            "error_vs_fp64": d.get("error_vs_fp64"),
+            "e2e": (d.get("e2e") or {}).get("value"),
+            "clocks": d.get("clocks"),
+        })
+        out.append(entry)
+    return out
 
 
 def rel_errors(got, ref, u0):

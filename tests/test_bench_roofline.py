@@ -66,3 +66,45 @@ def test_relative_error_uses_the_larger_of_the_solution_and_the_start():
     mx, l2 = bench.rel_errors(got, ref, u0)
     assert mx == pytest.approx(1e-17)
     assert l2 == pytest.approx(1e-17 / np.linalg.norm(ref))
+
+
+def test_secondary_lines_summarise_each_child_run(monkeypatch):
+    """The default run's other workloads: one child process per entry of
+    SECONDARY, its last JSON line summarised; a failing child is recorded as
+    an error and does not stop the others."""
+    import json
+    import subprocess
+    calls = []
+
+    class Done:
+        def __init__(self, rc, out, err=""):
+            self.returncode, self.stdout, self.stderr = rc, out, err
+
+    def fake_run(cmd, **kw):
+        calls.append(cmd)
+        name = cmd[cmd.index("--workload") + 1]
+        if name == "wave1024":
+            return Done(1, "", "boom")
+        line = {"value": 10.0, "unit": "Gcell-updates/s", "ms_per_step": 5.0,
+                "config": {"workload": name, "nsteps": 7, "tile": 16, "persistent": False,
+                           "cuda_graph": False},
+                "naive": {"value": 8.0}, "speedup_vs_naive": 1.25,
+                "swept_equals_naive_bitwise": True,
+                "roofline": {"bound": "fp64", "frac": 0.5, "unit": "Gop/s", "traffic": None,
+                             "extra": 1},
+                "error_vs_fp64": {"max_rel": 0.0}, "e2e": {"value": 9.0},
+                "clocks": {"sm_mhz": 2070.0}}
+        return Done(0, "noise\n" + json.dumps(line) + "\n")
+
+    monkeypatch.setattr(subprocess, "run", fake_run)
+    out = bench.secondary_lines()
+    assert [e["workload"] for e in out] == [n for n, _ in bench.SECONDARY]
+    for cmd, (name, extra) in zip(calls, bench.SECONDARY):
+        assert cmd[cmd.index("--steps") + 1] == "3" and cmd[cmd.index("--warmup") + 1] == "3"
+        assert "--no-secondary" in cmd and "--no-cpu" in cmd
+        assert cmd[-len(extra):] == list(extra) if extra else True
+    bad = [e for e in out if e["workload"] == "wave1024"]
+    assert bad and "boom" in bad[0]["error"]
+    good = [e for e in out if "error" not in e]
+    assert good and all(e["value"] == 10.0 and e["speedup_vs_naive"] == 1.25 for e in good)
+    assert good[0]["roofline"] == {"bound": "fp64", "frac": 0.5, "unit": "Gop/s", "traffic": None}
