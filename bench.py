@@ -105,7 +105,7 @@ WORKLOADS = {
                                 "time step, 2000 steps"),
     "wave1024": Workload("wave", "f64", 1024, 10_000, 32, (0.3,), "source", 0,
                          "wave 1024x1024 FP64 leapfrog, Courant 0.3, Gaussian source at the "
-                         "centre, 10000 steps", persistent=True),
+                         "centre, 10000 steps"),
 }
 
 
@@ -709,6 +709,7 @@ def secondary_lines(timeout_s=300):
             "roofline": {k: rf.get(k) for k in ("bound", "frac", "unit", "traffic")} if rf else None,
             "error_vs_fp64": d.get("error_vs_fp64"),
             "e2e": (d.get("e2e") or {}).get("value"),
+            "looped_single_grid": (d.get("looped_single_grid") or {}).get("value"),
             "clocks": d.get("clocks"),
         })
         out.append(entry)
