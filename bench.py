@@ -136,6 +136,10 @@ def parse():
                    help="run each advance (swept and naive) as a captured CUDA graph")
     p.add_argument("--persistent", action="store_true",
                    help="swept arm: one persistent launch per advance")
+    p.add_argument("--batch-tiles", default="16,32,64",
+                   help="batches: candidate tile sides for the autotuner")
+    p.add_argument("--one-launch", action="store_true",
+                   help="batches, with --persistent: one persistent launch for every tile class")
     p.add_argument("--no-secondary", action="store_true",
                    help="default run: skip the other workloads' lines (each measured in a "
                         "child process of its own)")
@@ -941,8 +945,9 @@ def run_batch(args, w, world, rank, local):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     torch.cuda.synchronize()
     nsteps = w.nsteps
+    cand = tuple(int(t) for t in args.batch_tiles.split(","))
     tiles, class_tuning, tune_table = autotune_batch(nx, ny, w.op, w.params, dtype=w.dtype,
-                                                     stream=stream)
+                                                     stream=stream, tiles=cand)
     stage = {str(k): v for k, v in class_tuning.items()}
 
     def timed(b, mode, k, wu):
@@ -971,10 +976,15 @@ def run_batch(args, w, world, rank, local):
     with ClockSampler(local) as clocks:
         with SweptBatch(nx, ny, tiles, op=w.op, params=w.params, stream=stream,
                         dtype=w.dtype) as sb:
-            for tile_n, (thr, stg) in class_tuning.items():
-                sb.set_tuning(thr, stg, tile=tile_n)
-            sw_mode = "persistent" if args.persistent else "swept"
-            ms_sw, launches = timed(sb, sw_mode, args.steps, max(1, args.warmup // 3))
+            if args.persistent and args.one_launch:
+                # one block shape for every class (the batch-wide tuning)
+                sb.set_tuning(args.threads or 256, args.stage or 0)
+            else:
+                for tile_n, (thr, stg) in class_tuning.items():
+                    sb.set_tuning(thr, stg, tile=tile_n)
+            sw_mode = ("persistent_one" if args.one_launch else "persistent") \
+                if args.persistent else "swept"
+            ms_sw, launches = timed(sb, sw_mode, args.steps, args.warmup)
             out_sw = sb.get_state()
             h_in = torch.from_numpy(flat.copy()).pin_memory()
             h_out = torch.empty_like(h_in).pin_memory()
@@ -988,7 +998,7 @@ def run_batch(args, w, world, rank, local):
         if not args.no_naive:
             with SweptBatch(nx, ny, [0] * count, op=w.op, params=w.params, stream=stream,
                             dtype=w.dtype) as nb:
-                naive_ms, _ = timed(nb, "naive", 1, 1)
+                naive_ms, _ = timed(nb, "naive", args.steps, args.warmup)
                 same = bool(np.array_equal(out_sw, nb.get_state()))
         # looping single-grid swept runs, one handle per grid, on a random sample
         rng = np.random.default_rng(11)
@@ -1051,7 +1061,9 @@ def run_batch(args, w, world, rank, local):
             "warmup": max(1, args.warmup // 3), "ms_per_step": ms_sw, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": w.dtype, "data": "synthetic",
             "config": {"workload": w.describe, "grids": count, "cells": cells,
-                       "tiles_chosen": class_counts, "persistent": bool(args.persistent), "class_tuning (threads, stage)": stage,
+                       "tiles_chosen": class_counts, "persistent": bool(args.persistent),
+                       "one_launch": bool(args.persistent and args.one_launch),
+                       "class_tuning (threads, stage)": stage,
                        "autotune": tune_table,
                        "cuda_graph": True, "l2": "flushed (256 MB write) between timed steps"},
             "naive_batched": {"value": naive_value, "unit": UNIT, "ms_per_step": naive_ms,

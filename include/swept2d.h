@@ -125,6 +125,19 @@ typedef struct swept2d swept2d_t;
  * the previous phase), instead of two launches per half cycle. Uses the
  * handle's tuning (threads, staging); same bits. */
 #define SWEPT2D_PERSISTENT 0x200
+/* Batches only, OR-ed with SWEPT2D_SWEPT | SWEPT2D_PERSISTENT: one persistent
+ * launch covers the half cycles of every tile class (each class's items after
+ * the previous class's, one 64-bit counter handing them out; each class keeps
+ * its own tile side, half-cycle count and neighbourhood counters), instead of
+ * one persistent launch per class. The launch takes the batch-wide tuning of
+ * swept2d_batch_set_tuning (default 256 threads, no staging; threads above 256
+ * are taken as 256) and the shared memory of the largest tile side; staging is
+ * dropped if that does not fit. One block shape serves every class, so the
+ * small-tile classes run with the largest class's shared memory. Naive tails
+ * (steps that do not fill a half cycle of a class) follow as before. Same bits.
+ * EINVAL without SWEPT2D_PERSISTENT, for a single-grid handle, or with more than
+ * 16 classes. */
+#define SWEPT2D_ONE_LAUNCH 0x400
 
 /*
  * Create a handle for an nx x ny grid.
@@ -276,7 +289,8 @@ int swept2d_measure_fp64_rate(void *stream, double *ops_per_s);
  * of ny[i] x nx[i]. Modes: SWEPT2D_SWEPT or SWEPT2D_NAIVE, optionally OR-ed with
  * SWEPT2D_GRAPH (not for HASH); SWEPT2D_SWEPT may also be OR-ed with
  * SWEPT2D_PERSISTENT (one persistent launch per tile class runs all of the
- * class's half cycles, waiting per grid on each tile's 3 x 3 neighbourhood).
+ * class's half cycles, waiting per grid on each tile's 3 x 3 neighbourhood),
+ * and that with SWEPT2D_ONE_LAUNCH (one persistent launch for all classes).
  * Every call returns a status; messages through
  * swept2d_batch_last_error (NULL batch: the last failed create on this thread).
  */

@@ -97,6 +97,70 @@ __global__ void __launch_bounds__(256) batch_persistent_kernel(
                                  up, br, stage, queue, H, g0, err, 0, kPersistSpinLimit);
 }
 
+// One persistent launch over every tile class: each class's items (its own tile
+// table, counters, tile side and number of half cycles) follow the previous
+// class's in one order, handed out by a 64-bit counter. A class's items depend
+// only on that class's earlier items, all handed out before them, so the
+// lowest unfinished item can always run, as in one class's launch; the
+// classes overlap where one class's last phases and the next one's first
+// items share the GPU.
+struct ClassRun {
+    const int2 *tiles;      // the class's tile table
+    int *stage;             // its per-tile item counters (zeroed)
+    int ntiles, n, H;       // tiles, tile side, half cycles
+    long long first;        // its first item in the launch's order
+};
+constexpr int kMaxClassRuns = 16;
+// passed by value (a kernel parameter, so a captured graph keeps its own copy)
+struct ClassRuns {
+    ClassRun r[kMaxClassRuns];
+    int count;
+};
+
+template <class Op, bool STG, int NC>
+__device__ __forceinline__ bool class_item(const GridDesc *grids, const ClassRun &c,
+                                           typename Op::S *state, typename Op::S *up,
+                                           typename Op::S *br, u64 g0, int *err, int item) {
+    return persistent_item<Op, STG, NC>(Op(grids[0].c), GridTiles{grids, c.tiles}, c.ntiles, c.n,
+                                        state, up, br, c.stage, c.H, g0, err, item,
+                                        kPersistSpinLimit, nullptr);
+}
+
+template <class Op, bool STG>
+__global__ void __launch_bounds__(256) batch_persistent_all_kernel(
+    const GridDesc *grids, const ClassRuns runs, long long nitems, typename Op::S *state,
+    typename Op::S *up, typename Op::S *br, unsigned long long *queue, u64 g0, int *err) {
+    __shared__ long long s_item;
+    __shared__ ClassRun s_run;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            long long it = (long long)atomicAdd(queue, 1ULL);
+            if (ld_relaxed(err)) it = nitems;        // another block's failure ends this one
+            int c = 0;
+            while (c + 1 < runs.count && it >= runs.r[c + 1].first) ++c;
+            s_item = it;
+            s_run = runs.r[c];
+        }
+        __syncthreads();
+        const long long it = s_item;
+        if (it >= nitems) return;
+        const ClassRun c = s_run;
+        const int item = (int)(it - c.first);
+        bool ok;
+        if constexpr (FixedTiles<Op>::value) {
+            switch (c.n) {
+                case 16: ok = class_item<Op, STG, 16>(grids, c, state, up, br, g0, err, item); break;
+                case 32: ok = class_item<Op, STG, 32>(grids, c, state, up, br, g0, err, item); break;
+                case 64: ok = class_item<Op, STG, 64>(grids, c, state, up, br, g0, err, item); break;
+                default: ok = class_item<Op, STG, 0>(grids, c, state, up, br, g0, err, item); break;
+            }
+        } else {
+            ok = class_item<Op, STG, 0>(grids, c, state, up, br, g0, err, item);
+        }
+        if (!ok) return;
+    }
+}
+
 // One sub-step of every grid in a block table: block b covers a 32 x 8 patch of
 // its grid (the same per-point update as the single-grid naive kernel).
 template <class Op>
@@ -146,6 +210,12 @@ struct BatchTable {
     cudaError_t (*persistent)(const GridDesc *, const int2 *tile_grid, int ntiles, int n,
                               void *state, void *up, void *br, int *sched, int H, u64 g0,
                               int *err, const Tuning &, cudaStream_t);
+    // every class's half cycles as one persistent launch (runs: the classes in
+    // item order, counters zeroed; queue: 64-bit counter, zeroed)
+    cudaError_t (*persistent_all)(const GridDesc *, const ClassRuns &runs, long long nitems,
+                                  long long total_tiles, int max_n, void *state, void *up,
+                                  void *br, unsigned long long *queue, u64 g0, int *err,
+                                  const Tuning &, cudaStream_t);
 };
 
 template <class Op>
@@ -257,10 +327,40 @@ struct BatchLaunch {
                         : persistent_t<false>(d, tg, ntiles, n, state, upp, br, sched, H, g0,
                                               err, tn.threads, st);
     }
+    template <bool STG>
+    static cudaError_t persistent_all_t(const GridDesc *d, const ClassRuns &runs,
+                                        long long nitems, long long tiles, int max_n,
+                                        void *state, void *upp, void *br,
+                                        unsigned long long *queue, u64 g0, int *err, int threads,
+                                        cudaStream_t st) {
+        const size_t sm = down_smem<Op>(max_n, STG);   // the largest class's block
+        const auto kern = batch_persistent_all_kernel<Op, STG>;
+        cudaError_t e = allow_smem(kern, sm);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0, dev = 0, nsm = 0;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, sm)) !=
+            cudaSuccess)
+            return e;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        const long long grid = persistent_grid(per_sm, nsm, tiles, nitems);
+        kern<<<(int)grid, threads, sm, st>>>(d, runs, nitems, (S *)state, (S *)upp, (S *)br,
+                                             queue, g0, err);
+        return cudaGetLastError();
+    }
+    static cudaError_t persistent_all(const GridDesc *d, const ClassRuns &runs, long long nitems,
+                                      long long tiles, int max_n, void *state, void *upp,
+                                      void *br, unsigned long long *queue, u64 g0, int *err,
+                                      const Tuning &tn, cudaStream_t st) {
+        return tn.stage ? persistent_all_t<true>(d, runs, nitems, tiles, max_n, state, upp, br,
+                                                 queue, g0, err, tn.threads, st)
+                        : persistent_all_t<false>(d, runs, nitems, tiles, max_n, state, upp, br,
+                                                  queue, g0, err, tn.threads, st);
+    }
     static const BatchTable *table() {
         static const BatchTable t = {Op::NV, Op::NST, (int)sizeof(S), Op::STAGE,
                                      &swept_smem_for<Op>, &naive, &up, &bridge, &octahedron,
-                                     &down, &persistent};
+                                     &down, &persistent, &persistent_all};
         return &t;
     }
 };

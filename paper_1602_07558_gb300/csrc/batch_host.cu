@@ -70,6 +70,7 @@ struct swept2d_batch {
     bool has_state = false;
     swept::Tuning tune;
     std::vector<BatchGraph> graphs;
+    unsigned long long *d_queue = nullptr;      // one-launch persistent form: item counter
     std::string err;
 };
 
@@ -101,6 +102,7 @@ void batch_free(swept2d_batch *b) {
         if (c.d_blocks) cudaFree(c.d_blocks);
         if (c.d_sched) cudaFree(c.d_sched);
     }
+    if (b->d_queue) cudaFree(b->d_queue);
     for (void *p : {(void *)b->d_grids, (void *)b->d_all_blocks, b->state, b->state2, b->up, b->br,
                     (void *)b->errword, (void *)b->d_amax})
         if (p) cudaFree(p);
@@ -133,9 +135,31 @@ int batch_naive(swept2d_batch *b, const int2 *d_blocks, int nblocks, long long c
     return SWEPT2D_OK;
 }
 
+// The launch shape of the one-launch persistent form: the batch-wide tuning
+// (swept2d_batch_set_tuning; the per-class tunings serve the per-class
+// launches), threads at most 256, staging dropped if the largest class's
+// staged block does not fit; max_n: the largest tile side.
+swept::Tuning one_launch_tuning(const swept2d_batch *b, int *max_n, long long *tiles) {
+    swept::Tuning tn = b->tune;
+    *max_n = 0;
+    *tiles = 0;
+    for (const auto &c : b->classes) {
+        if (!c.n) continue;
+        *tiles += (long long)c.tiles.size();
+        if (c.n > *max_n) *max_n = c.n;
+    }
+    if (tn.threads > 256) tn.threads = 256;
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (tn.stage && b->bt->smem_for(*max_n, true) > (size_t)optin) tn.stage = false;
+    return tn;
+}
+
 int batch_run(swept2d_batch *b, long long total, int mode) {
     const bool persistent = (mode & SWEPT2D_PERSISTENT) != 0;
-    mode &= ~SWEPT2D_PERSISTENT;
+    const bool one_launch = (mode & SWEPT2D_ONE_LAUNCH) != 0;
+    mode &= ~(SWEPT2D_PERSISTENT | SWEPT2D_ONE_LAUNCH);
     const u64 g_start = (u64)b->substeps;
     if (mode == SWEPT2D_NAIVE) {
         void *cur = b->state, *other = b->state2;
@@ -147,6 +171,39 @@ int batch_run(swept2d_batch *b, long long total, int mode) {
         b->substeps += total;
         return SWEPT2D_OK;
     }
+    if (persistent && one_launch) {
+        // every class's half cycles in one launch; the tails follow per class
+        swept::ClassRuns runs{};
+        long long nitems = 0;
+        for (auto &c : b->classes) {
+            const long long H = c.n > 0 ? total / (c.n / 2) : 0;
+            if (H <= 0) continue;
+            const int nt = (int)c.tiles.size();
+            cudaError_t e = cudaMemsetAsync(c.d_sched, 0, (size_t)nt * sizeof(int), b->stream);
+            if (e != cudaSuccess) return bcuda(b, e, "persistent schedule reset");
+            swept::ClassRun &r = runs.r[runs.count++];
+            r.tiles = c.d_tiles;
+            r.stage = c.d_sched;
+            r.ntiles = nt;
+            r.n = c.n;
+            r.H = (int)H;
+            r.first = nitems;
+            nitems += swept::persistent_items(nt, H);
+        }
+        if (runs.count > 0) {
+            cudaError_t e = cudaMemsetAsync(b->d_queue, 0, sizeof(unsigned long long), b->stream);
+            if (e != cudaSuccess) return bcuda(b, e, "persistent queue reset");
+            int max_n = 0;
+            long long tiles = 0;
+            const swept::Tuning tn = one_launch_tuning(b, &max_n, &tiles);
+            int rc = blaunch(b, "batched one-launch persistent kernel", [&] {
+                return b->bt->persistent_all(b->d_grids, runs, nitems, tiles, max_n, b->state,
+                                             b->up, b->br, b->d_queue, g_start, b->errword, tn,
+                                             b->stream);
+            });
+            if (rc) return rc;
+        }
+    }
     for (auto &c : b->classes) {
         long long H = 0, rem = total;
         if (c.n > 0) {
@@ -155,7 +212,9 @@ int batch_run(swept2d_batch *b, long long total, int mode) {
             rem = total - H * half;
         }
         const int nt = (int)c.tiles.size();
-        if (H > 0 && persistent) {
+        if (H > 0 && persistent && one_launch) {
+            // (run above, with every other class)
+        } else if (H > 0 && persistent) {
             cudaError_t e = cudaMemsetAsync(c.d_sched, 0, ((size_t)nt + 1) * sizeof(int), b->stream);
             if (e != cudaSuccess) return bcuda(b, e, "persistent schedule reset");
             int rc = blaunch(b, "batched persistent kernel", [&] {
@@ -444,13 +503,24 @@ int swept2d_batch_advance(swept2d_batch_t *b, long long nsteps, int mode) {
     if (!b->has_state) return bfail(b, SWEPT2D_ESTATE, "advance: no state set");
     const bool graph = (mode & SWEPT2D_GRAPH) != 0;
     const int persistent = mode & SWEPT2D_PERSISTENT;
-    mode &= ~(SWEPT2D_GRAPH | SWEPT2D_PERSISTENT);
+    const int one_launch = mode & SWEPT2D_ONE_LAUNCH;
+    mode &= ~(SWEPT2D_GRAPH | SWEPT2D_PERSISTENT | SWEPT2D_ONE_LAUNCH);
     if (mode != SWEPT2D_SWEPT && mode != SWEPT2D_NAIVE) return bfail(b, SWEPT2D_EINVAL, "advance: bad mode");
+    if (one_launch && !persistent)
+        return bfail(b, SWEPT2D_EINVAL, "advance: the one-launch form needs SWEPT2D_PERSISTENT");
     if (persistent) {
         if (mode != SWEPT2D_SWEPT) return bfail(b, SWEPT2D_EINVAL, "advance: persistent needs the swept mode");
+        int swept_classes = 0;
+        for (auto &c : b->classes) swept_classes += c.n ? 1 : 0;
+        if (one_launch && swept_classes > swept::kMaxClassRuns)
+            return bfail(b, SWEPT2D_EINVAL, "advance: the one-launch form takes at most 16 classes");
+        if (one_launch && !b->d_queue) {
+            cudaError_t e = cudaMalloc(&b->d_queue, sizeof(unsigned long long));
+            if (e != cudaSuccess) return bcuda(b, e, "persistent queue allocation");
+        }
         for (auto &c : b->classes) {
             if (!c.n) continue;
-            if (c.tune.threads > 256)
+            if (c.tune.threads > 256 && !one_launch)
                 return bfail(b, SWEPT2D_EINVAL, "advance: the persistent form takes at most 256 threads");
             const long long H = nsteps * b->bt->nst / (c.n / 2);
             if (swept::persistent_items((long long)c.tiles.size(), H) >= (1LL << 31))
@@ -460,7 +530,7 @@ int swept2d_batch_advance(swept2d_batch_t *b, long long nsteps, int mode) {
                 if (e != cudaSuccess) return bcuda(b, e, "persistent schedule allocation");
             }
         }
-        mode |= persistent;
+        mode |= persistent | one_launch;
     }
     if (graph) {
         if (!b->stream) return bfail(b, SWEPT2D_EINVAL, "advance: graph mode needs a created stream");

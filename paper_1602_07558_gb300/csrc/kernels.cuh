@@ -1121,107 +1121,123 @@ __host__ __device__ inline long long persistent_items(long long NT, long long H)
 // `trace` (nullptr: none) receives, per work item, the SM clock cycles its
 // block spent waiting for the item's neighbourhood (trace[2 item]) and running
 // the item up to its release (trace[2 item + 1]).
+// One work item of the persistent form (every thread of the block calls it
+// with the same item): wait for the item's neighbourhood, run it, count it.
+// Returns false when a wait gave up (the block must stop).
+template <class Op, bool STG, int NC = 0, class Loc>
+__device__ __forceinline__ bool persistent_item(const Op &op, const Loc &at, int NT, int n,
+                                                typename Op::S *state, typename Op::S *upp,
+                                                typename Op::S *br, int *stage, int H, u64 g0,
+                                                int *err, int item, long long spin_limit,
+                                                unsigned *trace) {
+    __shared__ int s_fail;
+    long long t_start = 0, t_ready = 0;
+    const int h = (NC > 0 ? NC : n) / 2;
+    // decode: kind 0 first Up, 1 bridge (xb: x-bridge), 2 octahedron or Down
+    int kind, t, j = 0, need = 0;
+    bool xb = false;
+    if (item < NT) {
+        kind = 0;
+        t = item;
+    } else {
+        const int r = item - NT;
+        j = r / (3 * NT);
+        const int q = r - j * 3 * NT;
+        if (q < 2 * NT) {
+            kind = 1;
+            t = q >> 1;
+            xb = (q & 1) != 0;
+            need = 1 + 3 * j;
+        } else {
+            kind = 2;
+            t = q - 2 * NT;
+            need = 3 + 3 * j;
+        }
+    }
+    const TileAt w = at(t);
+    const Geom G = fixed_tile<NC>(w.G);
+    const int I = w.I, J = w.J;
+    const Op opi = w.c ? Op(w.c) : op;
+    if (threadIdx.x == 0) s_fail = 0;
+    if (trace && threadIdx.x == 0) t_start = clock64();
+    if (kind != 0 && threadIdx.x < 32) {
+        // lanes 0..8 wait for one tile each of the periodic 3 x 3 neighbourhood
+        bool bad = false;
+        if (threadIdx.x < 9) {
+            const int dj = (int)threadIdx.x / 3 - 1, di = (int)threadIdx.x % 3 - 1;
+            const int jj = J + dj < 0 ? G.Q - 1 : (J + dj == G.Q ? 0 : J + dj);
+            const int ii = I + di < 0 ? G.T - 1 : (I + di == G.T ? 0 : I + di);
+            const int *flag = stage + w.base + jj * G.T + ii;
+            long long it = 0;
+            while (ld_acquire(flag) < need) {
+                // give up after the bound, or at once when another block
+                // has already recorded a failure
+                if (++it > spin_limit || ((it & 255) == 0 && ld_relaxed(err) != 0)) {
+                    bad = true;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        bad = __any_sync(0xffffffffu, bad);
+        if (threadIdx.x == 0 && bad) {
+            atomicExch(err, 2);
+            s_fail = 1;
+        }
+    }
+    __syncthreads();
+    if (s_fail) return false;
+    if (trace && threadIdx.x == 0) t_ready = clock64();
+    // the acquired panels are read next by bulk copies (the async proxy)
+    if (threadIdx.x == 0) asm volatile("fence.proxy.async.global;\n" ::: "memory");
+    typename Op::S *st = state + w.soff, *u = upp + w.poff, *b = br + w.poff;
+    const u64 gj = g0 + (u64)j * h;
+    const int o = (j & 1) ? h : 0;
+    if (kind == 0) {
+        up_tile(opi, G, st, u, 0, g0, I, J);
+    } else if (kind == 1) {                     // one bridge of half cycle j
+        bridge_tile<Op, STG>(opi, G, u, b, gj, err, I, J, xb);
+    } else if (j + 1 < H) {
+        octahedron_tile<Op, STG>(opi, G, b, u, o, gj, err, I, J);
+    } else {
+        down_tile<Op, STG>(opi, G, b, st, o, gj, err, I, J);
+    }
+    // make this item's panel (and state) stores visible, to the generic and
+    // the async proxy, before the release of its count; order this item's
+    // shared-memory accesses before the next item's bulk copies into it
+    asm volatile("fence.proxy.async.global;\n" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (trace) {
+            trace[2 * (size_t)item] = (unsigned)(t_ready - t_start);
+            trace[2 * (size_t)item + 1] = (unsigned)(clock64() - t_ready);
+        }
+        add_release(stage + t, 1);
+    }
+    return true;
+}
+
 template <class Op, bool STG, int NC = 0, class Loc>
 __device__ __forceinline__ void persistent_loop(const Op &op, const Loc &at, int NT, int n,
                                                 typename Op::S *state, typename Op::S *upp,
                                                 typename Op::S *br, int *stage, int *queue, int H,
                                                 u64 g0, int *err, int first, long long spin_limit,
                                                 unsigned *trace = nullptr) {
-    __shared__ int s_item, s_fail;
-    long long t_start = 0, t_ready = 0;
-    const int h = (NC > 0 ? NC : n) / 2;
+    __shared__ int s_item;
     const int nitems = (int)persistent_items(NT, H);
     for (;;) {
         if (threadIdx.x == 0) {
             const int it = atomicAdd(queue, 1) + first;
             s_item = ld_relaxed(err) ? nitems : it;   // another block's failure ends this one
-            s_fail = 0;
         }
         __syncthreads();
         const int item = s_item;
         if (item >= nitems) return;
-        // decode: kind 0 first Up, 1 bridge (xb: x-bridge), 2 octahedron or Down
-        int kind, t, j = 0, need = 0;
-        bool xb = false;
-        if (item < NT) {
-            kind = 0;
-            t = item;
-        } else {
-            const int r = item - NT;
-            j = r / (3 * NT);
-            const int q = r - j * 3 * NT;
-            if (q < 2 * NT) {
-                kind = 1;
-                t = q >> 1;
-                xb = (q & 1) != 0;
-                need = 1 + 3 * j;
-            } else {
-                kind = 2;
-                t = q - 2 * NT;
-                need = 3 + 3 * j;
-            }
-        }
-        const TileAt w = at(t);
-        const Geom G = fixed_tile<NC>(w.G);
-        const int I = w.I, J = w.J;
-        const Op opi = w.c ? Op(w.c) : op;
-        if (trace && threadIdx.x == 0) t_start = clock64();
-        if (kind != 0 && threadIdx.x < 32) {
-            // lanes 0..8 wait for one tile each of the periodic 3 x 3 neighbourhood
-            bool bad = false;
-            if (threadIdx.x < 9) {
-                const int dj = (int)threadIdx.x / 3 - 1, di = (int)threadIdx.x % 3 - 1;
-                const int jj = J + dj < 0 ? G.Q - 1 : (J + dj == G.Q ? 0 : J + dj);
-                const int ii = I + di < 0 ? G.T - 1 : (I + di == G.T ? 0 : I + di);
-                const int *flag = stage + w.base + jj * G.T + ii;
-                long long it = 0;
-                while (ld_acquire(flag) < need) {
-                    // give up after the bound, or at once when another block
-                    // has already recorded a failure
-                    if (++it > spin_limit || ((it & 255) == 0 && ld_relaxed(err) != 0)) {
-                        bad = true;
-                        break;
-                    }
-                    __nanosleep(64);
-                }
-            }
-            bad = __any_sync(0xffffffffu, bad);
-            if (threadIdx.x == 0 && bad) {
-                atomicExch(err, 2);
-                s_fail = 1;
-            }
-        }
-        __syncthreads();
-        if (s_fail) return;
-        if (trace && threadIdx.x == 0) t_ready = clock64();
-        // the acquired panels are read next by bulk copies (the async proxy)
-        if (threadIdx.x == 0) asm volatile("fence.proxy.async.global;\n" ::: "memory");
-        typename Op::S *st = state + w.soff, *u = upp + w.poff, *b = br + w.poff;
-        const u64 gj = g0 + (u64)j * h;
-        const int o = (j & 1) ? h : 0;
-        if (kind == 0) {
-            up_tile(opi, G, st, u, 0, g0, I, J);
-        } else if (kind == 1) {                     // one bridge of half cycle j
-            bridge_tile<Op, STG>(opi, G, u, b, gj, err, I, J, xb);
-        } else if (j + 1 < H) {
-            octahedron_tile<Op, STG>(opi, G, b, u, o, gj, err, I, J);
-        } else {
-            down_tile<Op, STG>(opi, G, b, st, o, gj, err, I, J);
-        }
-        // make this item's panel (and state) stores visible, to the generic and
-        // the async proxy, before the release of its count; order this item's
-        // shared-memory accesses before the next item's bulk copies into it
-        asm volatile("fence.proxy.async.global;\n" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        __threadfence();
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            if (trace) {
-                trace[2 * (size_t)item] = (unsigned)(t_ready - t_start);
-                trace[2 * (size_t)item + 1] = (unsigned)(clock64() - t_ready);
-            }
-            add_release(stage + t, 1);
-        }
+        if (!persistent_item<Op, STG, NC>(op, at, NT, n, state, upp, br, stage, H, g0, err, item,
+                                          spin_limit, trace))
+            return;
     }
 }
 

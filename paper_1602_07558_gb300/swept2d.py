@@ -38,7 +38,8 @@ OP_SHAPE = {
     "wave": (2, 1, "f64"),
     "euler_kahan": (12, 2, "f32"),
 }
-MODES = {"swept": 0, "naive": 1, "persistent": 0x200}
+MODES = {"swept": 0, "naive": 1, "persistent": 0x200,
+         "persistent_one": 0x600}   # batches: one persistent launch for every tile class
 GRAPH = 0x100
 Q = {"dt": 0, "wavespeed": 1, "substeps": 2, "launches": 3, "state_bytes": 4,
      "panel_bytes": 5, "smem_bytes": 6, "cells": 7, "threads": 8, "stage": 9}

@@ -49,7 +49,7 @@ def _oracle(oracle_lib, op, dtype, s, nsteps):
 
 @pytest.mark.parametrize("op,dtype", [("heat", "f64"), ("hash", "u64"),
                                       ("heat_kahan", "f32"), ("heat_kahan", "bf16")])
-@pytest.mark.parametrize("mode", ["swept", "naive", "persistent"])
+@pytest.mark.parametrize("mode", ["swept", "naive", "persistent", "persistent_one"])
 def test_batch_equals_the_oracle_for_every_grid(oracle_lib, op, dtype, mode):
     nsteps = 37                           # odd tails for every class
     states = _states(op, dtype, seed=len(op) + len(mode))
@@ -77,10 +77,11 @@ def test_batch_graph_and_split_advances_match(op, dtype):
         for _ in range(3):
             b.advance(21, graph=True)
         got = b.split(b.get_state())
-        b.set_state(states)
-        for _ in range(3):
-            b.advance(21, mode="persistent", graph=True)
-        assert all(np.array_equal(x, y) for x, y in zip(got, b.split(b.get_state())))
+        for mode in ("persistent", "persistent_one"):
+            b.set_state(states)
+            for _ in range(3):
+                b.advance(21, mode=mode, graph=True)
+            assert all(np.array_equal(x, y) for x, y in zip(got, b.split(b.get_state())))
     with SweptBatch([s[0] for s in SIZES], [s[1] for s in SIZES], [s[2] for s in SIZES],
                     **kw) as b:
         b.set_state(states)
@@ -115,7 +116,7 @@ def _euler_states(dtype, seed):
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
-@pytest.mark.parametrize("mode", ["swept", "naive", "persistent"])
+@pytest.mark.parametrize("mode", ["swept", "naive", "persistent", "persistent_one"])
 def test_batch_euler_every_grid_has_its_own_time_step(oracle_lib, dtype, mode):
     """Euler grids of uneven sizes in one batch: each grid's wave speed and
     time step come from its own state and spacing (exactly the oracle's), and
@@ -149,7 +150,7 @@ def test_batch_tuning_gives_identical_bits():
     states = _states("heat_kahan", "f32", seed=3)
     outs = []
     for threads, stage in [(256, False), (128, True), (64, False), (32, False), (32, True)]:
-        for mode in ("swept", "persistent"):
+        for mode in ("swept", "persistent", "persistent_one"):
             with SweptBatch([s[0] for s in SIZES], [s[1] for s in SIZES], [s[2] for s in SIZES],
                             op="heat_kahan", params=(0.2,), dtype="f32") as b:
                 b.set_tuning(threads, stage)
@@ -157,3 +158,14 @@ def test_batch_tuning_gives_identical_bits():
                 b.advance(45, mode=mode)
                 outs.append(b.get_state())
     assert all(np.array_equal(outs[0], o) for o in outs[1:])
+
+
+def test_one_launch_needs_the_persistent_form():
+    """SWEPT2D_ONE_LAUNCH alone (without SWEPT2D_PERSISTENT) is refused."""
+    from paper_1602_07558_gb300.swept2d import SweptError, lib
+    states = _states("heat", "f64", seed=1)
+    with SweptBatch([s[0] for s in SIZES], [s[1] for s in SIZES], [s[2] for s in SIZES],
+                    op="heat", params=(0.2,), dtype="f64") as b:
+        b.set_state(states)
+        rc = lib().swept2d_batch_advance(b._h, 5, 0x400)
+        assert rc == -1 and "PERSISTENT" in lib().swept2d_batch_last_error(b._h).decode()

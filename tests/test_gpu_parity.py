@@ -125,7 +125,8 @@ def _euler_u0(nx, ny, seed, literal=False):
     return np.concatenate([U, U]), U
 
 
-@pytest.mark.parametrize("nx,ny,tile,nsteps", [(64, 48, 16, 40), (32, 32, 8, 13), (64, 64, 32, 20)])
+@pytest.mark.parametrize("nx,ny,tile,nsteps", [(64, 48, 16, 40), (32, 32, 8, 13), (64, 64, 32, 20),
+                                               (60, 40, 10, 17)])   # n = 2 mod 4: wider flux pitch
 def test_euler_swept_equals_naive_and_oracle(oracle_lib, nx, ny, tile, nsteps):
     u0, U = _euler_u0(nx, ny, seed=2)
     a, dt = oracle_lib.euler_setup(U, GAMMA, CFL)
@@ -153,6 +154,7 @@ def _to_bf16_bits(a):
 @pytest.mark.parametrize("storage", ["f32", "bf16"])
 @pytest.mark.parametrize("nx,ny,tile,nsteps", [
     (96, 64, 32, 77), (64, 64, 16, 40), (32, 48, 8, 23), (128, 64, 64, 70),
+    (60, 40, 10, 23),      # a tile side built only with the run-time side
 ])
 def test_heat_kahan_swept_equals_naive_and_oracle(oracle_lib, storage, nx, ny, tile, nsteps):
     """Binary32 arithmetic, Kahan-compensated update, binary32 or bfloat16
@@ -216,7 +218,8 @@ def test_tuning_gives_identical_bits(op, dtype, params, threads, stage):
 
 # ----------------------------------------------------------------------- wave
 
-@pytest.mark.parametrize("nx,ny,tile,nsteps", [(64, 64, 16, 100), (96, 64, 32, 45), (48, 32, 8, 19)])
+@pytest.mark.parametrize("nx,ny,tile,nsteps", [(64, 64, 16, 100), (96, 64, 32, 45), (48, 32, 8, 19),
+                                               (60, 40, 10, 21)])
 def test_wave_swept_equals_naive_and_oracle(oracle_lib, nx, ny, tile, nsteps):
     """Leapfrog wave (Section 6's experiment, Courant number 0.3): the 2-value
     point state (u^n, u^{n-1}) through every swept component, bitwise."""
@@ -236,7 +239,8 @@ def _euler_kahan_state(nx, ny, storage, seed):
 
 
 @pytest.mark.parametrize("storage", ["f32", "bf16"])
-@pytest.mark.parametrize("nx,ny,tile,nsteps", [(64, 48, 16, 21), (32, 32, 8, 13), (64, 64, 32, 20)])
+@pytest.mark.parametrize("nx,ny,tile,nsteps", [(64, 48, 16, 21), (32, 32, 8, 13), (64, 64, 32, 20),
+                                               (60, 40, 10, 17), (36, 24, 6, 11)])
 def test_euler_kahan_swept_equals_naive_and_oracle(oracle_lib, storage, nx, ny, tile, nsteps):
     """Euler in binary32 arithmetic with compensated update and binary32 /
     bfloat16 storage: all 12 planes (U, U*, C) bit for bit the oracle's, and
