@@ -677,6 +677,12 @@ SECONDARY = (
     ("euler2048", ("--nsteps", "500")), ("euler2048_f32", ("--nsteps", "500")),
     ("euler2048_bf16", ("--nsteps", "500")),
     ("batch1024", ("--nsteps", "2000")), ("batch1024_euler", ("--nsteps", "200")),
+    # one persistent launch for the whole batch (every grid at tile 16: one
+    # block shape serves every class, and a one-warp block suits tile 16)
+    ("batch1024", ("--nsteps", "2000", "--persistent", "--one-launch", "--batch-tiles", "16",
+                   "--threads", "32")),
+    ("batch1024_euler", ("--nsteps", "200", "--persistent", "--one-launch", "--batch-tiles",
+                         "16", "--threads", "64")),
 )
 
 
@@ -705,9 +711,9 @@ def secondary_lines(timeout_s=300):
         entry.update({
             "describe": cfg.get("workload"), "nsteps": cfg.get("nsteps"),
             "tile": cfg.get("tile"), "persistent": cfg.get("persistent"),
-            "cuda_graph": cfg.get("cuda_graph"), "value": d.get("value"), "unit": d.get("unit"),
+            "one_launch": cfg.get("one_launch"), "cuda_graph": cfg.get("cuda_graph"), "value": d.get("value"), "unit": d.get("unit"),
             "ms_per_step": d.get("ms_per_step"),
-            "naive": (d.get("naive") or {}).get("value"),
+            "naive": (d.get("naive") or d.get("naive_batched") or {}).get("value"),
             "speedup_vs_naive": d.get("speedup_vs_naive"),
             "swept_equals_naive_bitwise": d.get("swept_equals_naive_bitwise"),
             "roofline": {k: rf.get(k) for k in ("bound", "frac", "unit", "traffic")} if rf else None,
