@@ -6,6 +6,9 @@
 // per-tile bodies as the single-grid kernels, on that grid's slice of the
 // pooled state and panel buffers.
 #pragma once
+#include <algorithm>
+#include <type_traits>
+
 #include "launch.cuh"
 
 namespace swept {
@@ -97,18 +100,21 @@ __global__ void __launch_bounds__(256) batch_persistent_kernel(
                                  up, br, stage, queue, H, g0, err, 0, kPersistSpinLimit);
 }
 
-// One persistent launch over every tile class: each class's items (its own tile
-// table, counters, tile side and number of half cycles) follow the previous
-// class's in one order, handed out by a 64-bit counter. A class's items depend
-// only on that class's earlier items, all handed out before them, so the
-// lowest unfinished item can always run, as in one class's launch; the
-// classes overlap where one class's last phases and the next one's first
-// items share the GPU.
+// One persistent launch over every tile class. Every block takes the classes
+// in order; within a class its teams (TeamOf<T>: T threads with their own
+// barrier and shared-memory slice, or the whole block) each take the class's
+// items, one at a time, from the class's own counter, and run them as that
+// class's own launch would (its tile table, counters, tile side and number of
+// half cycles; the tile side fixed at compile time for 16, 32 and 64). A block
+// goes on to the next class once its teams find the class's counter past its
+// last item, so the classes overlap at the class boundaries. An item waits
+// only for the same class's earlier items, handed out before it and held by
+// teams that never wait at a block barrier while they hold an item, so the
+// lowest unfinished item can always run, as in one class's launch.
 struct ClassRun {
     const int2 *tiles;      // the class's tile table
-    int *stage;             // its per-tile item counters (zeroed)
+    int *stage;             // its per-tile item counters, then its item counter (zeroed)
     int ntiles, n, H;       // tiles, tile side, half cycles
-    long long first;        // its first item in the launch's order
 };
 constexpr int kMaxClassRuns = 16;
 // passed by value (a kernel parameter, so a captured graph keeps its own copy)
@@ -117,47 +123,79 @@ struct ClassRuns {
     int count;
 };
 
-template <class Op, bool STG, int NC>
-__device__ __forceinline__ bool class_item(const GridDesc *grids, const ClassRun &c,
-                                           typename Op::S *state, typename Op::S *up,
-                                           typename Op::S *br, u64 g0, int *err, int item) {
-    return persistent_item<Op, STG, NC>(Op(grids[0].c), GridTiles{grids, c.tiles}, c.ntiles, c.n,
-                                        state, up, br, c.stage, c.H, g0, err, item,
-                                        kPersistSpinLimit, nullptr);
+// Threads of the one-launch kernel's blocks, and the team that runs one item
+// of a class with tile side n (0: the whole block): small tiles, whose levels
+// are short, run one per warp or two; the largest classes take the block.
+constexpr int kOneLaunchThreads = 256;
+template <class Op>
+__host__ __device__ constexpr int one_launch_team(int n) {
+    if constexpr (std::is_same<Op, HeatKahanOp<float>>::value ||
+                  std::is_same<Op, HeatKahanOp<__nv_bfloat16>>::value)
+        return n <= 16 ? 32 : (n <= 32 ? 128 : 0);
+    else
+        return n <= 16 ? 64 : 0;
+}
+// Shared memory of a one-launch block for a class of tile side n: its teams'
+// slices, or one swept block.
+template <class Op, bool STG>
+inline size_t one_launch_class_smem(int n) {
+    const int T = one_launch_team<Op>(n);
+    return T ? (size_t)(kOneLaunchThreads / T) * team_slice<Op, STG>(n) : down_smem<Op>(n, STG);
+}
+
+template <class Op, bool STG, int NC, class Tm>
+__device__ __forceinline__ bool run_class(const GridDesc *grids, const ClassRun &c,
+                                          typename Op::S *state, typename Op::S *up,
+                                          typename Op::S *br, u64 g0, int *err) {
+    __shared__ int s_item[kMaxTeams];
+    int &mine = s_item[Tm::index()];
+    const int nitems = (int)persistent_items(c.ntiles, c.H);
+    int *queue = c.stage + c.ntiles;
+    for (;;) {
+        if (Tm::rank() == 0) {
+            const int it = atomicAdd(queue, 1);
+            mine = ld_relaxed(err) ? nitems : it;     // another team's failure ends this one
+        }
+        Tm::sync();
+        const int item = mine;
+        if (item >= nitems) return true;
+        if (!persistent_item<Op, STG, NC, Tm>(Op(grids[0].c), GridTiles{grids, c.tiles},
+                                              c.ntiles, c.n, state, up, br, c.stage, c.H, g0,
+                                              err, item, kPersistSpinLimit, nullptr))
+            return false;
+    }
+}
+
+// The team for tile side N (a compile-time case of the class's side)
+template <class Op, bool STG, int N>
+__device__ __forceinline__ bool run_class_n(const GridDesc *grids, const ClassRun &c,
+                                            typename Op::S *state, typename Op::S *up,
+                                            typename Op::S *br, u64 g0, int *err) {
+    constexpr int NC = FixedTiles<Op>::value ? N : 0;
+    constexpr int T = one_launch_team<Op>(N);
+    if constexpr (T > 0 && T < kOneLaunchThreads)
+        return run_class<Op, STG, NC, TeamOf<T>>(grids, c, state, up, br, g0, err);
+    else
+        return run_class<Op, STG, NC, BlockTeam>(grids, c, state, up, br, g0, err);
 }
 
 template <class Op, bool STG>
-__global__ void __launch_bounds__(256) batch_persistent_all_kernel(
-    const GridDesc *grids, const ClassRuns runs, long long nitems, typename Op::S *state,
-    typename Op::S *up, typename Op::S *br, unsigned long long *queue, u64 g0, int *err) {
-    __shared__ long long s_item;
-    __shared__ ClassRun s_run;
-    for (;;) {
-        if (threadIdx.x == 0) {
-            long long it = (long long)atomicAdd(queue, 1ULL);
-            if (ld_relaxed(err)) it = nitems;        // another block's failure ends this one
-            int c = 0;
-            while (c + 1 < runs.count && it >= runs.r[c + 1].first) ++c;
-            s_item = it;
-            s_run = runs.r[c];
-        }
-        __syncthreads();
-        const long long it = s_item;
-        if (it >= nitems) return;
-        const ClassRun c = s_run;
-        const int item = (int)(it - c.first);
+__global__ void __launch_bounds__(kOneLaunchThreads) batch_persistent_all_kernel(
+    const GridDesc *grids, const ClassRuns runs, typename Op::S *state, typename Op::S *up,
+    typename Op::S *br, u64 g0, int *err) {
+    for (int k = 0; k < runs.count; ++k) {
+        const ClassRun c = runs.r[k];
         bool ok;
-        if constexpr (FixedTiles<Op>::value) {
-            switch (c.n) {
-                case 16: ok = class_item<Op, STG, 16>(grids, c, state, up, br, g0, err, item); break;
-                case 32: ok = class_item<Op, STG, 32>(grids, c, state, up, br, g0, err, item); break;
-                case 64: ok = class_item<Op, STG, 64>(grids, c, state, up, br, g0, err, item); break;
-                default: ok = class_item<Op, STG, 0>(grids, c, state, up, br, g0, err, item); break;
-            }
-        } else {
-            ok = class_item<Op, STG, 0>(grids, c, state, up, br, g0, err, item);
+        switch (c.n) {
+            case 16: ok = run_class_n<Op, STG, 16>(grids, c, state, up, br, g0, err); break;
+            case 32: ok = run_class_n<Op, STG, 32>(grids, c, state, up, br, g0, err); break;
+            case 64: ok = run_class_n<Op, STG, 64>(grids, c, state, up, br, g0, err); break;
+            default:
+                ok = run_class<Op, STG, 0, BlockTeam>(grids, c, state, up, br, g0, err);
+                break;
         }
-        if (!ok) return;
+        // every team of the block leaves the class before the team shape changes
+        if (__syncthreads_or(!ok)) return;
     }
 }
 
@@ -211,11 +249,12 @@ struct BatchTable {
                               void *state, void *up, void *br, int *sched, int H, u64 g0,
                               int *err, const Tuning &, cudaStream_t);
     // every class's half cycles as one persistent launch (runs: the classes in
-    // item order, counters zeroed; queue: 64-bit counter, zeroed)
-    cudaError_t (*persistent_all)(const GridDesc *, const ClassRuns &runs, long long nitems,
-                                  long long total_tiles, int max_n, void *state, void *up,
-                                  void *br, unsigned long long *queue, u64 g0, int *err,
+    // order, each class's counters and item counter zeroed)
+    cudaError_t (*persistent_all)(const GridDesc *, const ClassRuns &runs, long long total_tiles,
+                                  void *state, void *up, void *br, u64 g0, int *err,
                                   const Tuning &, cudaStream_t);
+    // dynamic shared memory of the one-launch kernel's blocks (largest class)
+    size_t (*one_launch_smem)(const int *tile_sides, int count, bool stage);
 };
 
 template <class Op>
@@ -328,39 +367,45 @@ struct BatchLaunch {
                                               err, tn.threads, st);
     }
     template <bool STG>
-    static cudaError_t persistent_all_t(const GridDesc *d, const ClassRuns &runs,
-                                        long long nitems, long long tiles, int max_n,
-                                        void *state, void *upp, void *br,
-                                        unsigned long long *queue, u64 g0, int *err, int threads,
+    static size_t one_launch_smem_t(const int *sides, int count) {
+        size_t sm = 0;
+        for (int i = 0; i < count; ++i) sm = std::max(sm, one_launch_class_smem<Op, STG>(sides[i]));
+        return sm;
+    }
+    static size_t one_launch_smem(const int *sides, int count, bool stage) {
+        return stage ? one_launch_smem_t<true>(sides, count) : one_launch_smem_t<false>(sides, count);
+    }
+    template <bool STG>
+    static cudaError_t persistent_all_t(const GridDesc *d, const ClassRuns &runs, long long tiles,
+                                        void *state, void *upp, void *br, u64 g0, int *err,
                                         cudaStream_t st) {
-        const size_t sm = down_smem<Op>(max_n, STG);   // the largest class's block
+        int sides[kMaxClassRuns];
+        for (int i = 0; i < runs.count; ++i) sides[i] = runs.r[i].n;
+        const size_t sm = one_launch_smem_t<STG>(sides, runs.count);
         const auto kern = batch_persistent_all_kernel<Op, STG>;
         cudaError_t e = allow_smem(kern, sm);
         if (e != cudaSuccess) return e;
         int per_sm = 0, dev = 0, nsm = 0;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, sm)) !=
-            cudaSuccess)
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kOneLaunchThreads,
+                                                               sm)) != cudaSuccess)
             return e;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        const long long grid = persistent_grid(per_sm, nsm, tiles, nitems);
-        kern<<<(int)grid, threads, sm, st>>>(d, runs, nitems, (S *)state, (S *)upp, (S *)br,
-                                             queue, g0, err);
+        const long long grid = persistent_grid(per_sm, nsm, tiles, 3 * tiles);
+        kern<<<(int)grid, kOneLaunchThreads, sm, st>>>(d, runs, (S *)state, (S *)upp, (S *)br, g0,
+                                                       err);
         return cudaGetLastError();
     }
-    static cudaError_t persistent_all(const GridDesc *d, const ClassRuns &runs, long long nitems,
-                                      long long tiles, int max_n, void *state, void *upp,
-                                      void *br, unsigned long long *queue, u64 g0, int *err,
+    static cudaError_t persistent_all(const GridDesc *d, const ClassRuns &runs, long long tiles,
+                                      void *state, void *upp, void *br, u64 g0, int *err,
                                       const Tuning &tn, cudaStream_t st) {
-        return tn.stage ? persistent_all_t<true>(d, runs, nitems, tiles, max_n, state, upp, br,
-                                                 queue, g0, err, tn.threads, st)
-                        : persistent_all_t<false>(d, runs, nitems, tiles, max_n, state, upp, br,
-                                                  queue, g0, err, tn.threads, st);
+        return tn.stage ? persistent_all_t<true>(d, runs, tiles, state, upp, br, g0, err, st)
+                        : persistent_all_t<false>(d, runs, tiles, state, upp, br, g0, err, st);
     }
     static const BatchTable *table() {
         static const BatchTable t = {Op::NV, Op::NST, (int)sizeof(S), Op::STAGE,
                                      &swept_smem_for<Op>, &naive, &up, &bridge, &octahedron,
-                                     &down, &persistent, &persistent_all};
+                                     &down, &persistent, &persistent_all, &one_launch_smem};
         return &t;
     }
 };

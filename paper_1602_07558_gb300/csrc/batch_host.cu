@@ -70,7 +70,6 @@ struct swept2d_batch {
     bool has_state = false;
     swept::Tuning tune;
     std::vector<BatchGraph> graphs;
-    unsigned long long *d_queue = nullptr;      // one-launch persistent form: item counter
     std::string err;
 };
 
@@ -102,7 +101,6 @@ void batch_free(swept2d_batch *b) {
         if (c.d_blocks) cudaFree(c.d_blocks);
         if (c.d_sched) cudaFree(c.d_sched);
     }
-    if (b->d_queue) cudaFree(b->d_queue);
     for (void *p : {(void *)b->d_grids, (void *)b->d_all_blocks, b->state, b->state2, b->up, b->br,
                     (void *)b->errword, (void *)b->d_amax})
         if (p) cudaFree(p);
@@ -135,25 +133,24 @@ int batch_naive(swept2d_batch *b, const int2 *d_blocks, int nblocks, long long c
     return SWEPT2D_OK;
 }
 
-// The launch shape of the one-launch persistent form: the batch-wide tuning
-// (swept2d_batch_set_tuning; the per-class tunings serve the per-class
-// launches), threads at most 256, staging dropped if the largest class's
-// staged block does not fit; max_n: the largest tile side.
-swept::Tuning one_launch_tuning(const swept2d_batch *b, int *max_n, long long *tiles) {
-    swept::Tuning tn = b->tune;
-    *max_n = 0;
+// The one-launch persistent form's tile sides (classes that take swept steps)
+// and its staging: the batch-wide tuning's (swept2d_batch_set_tuning), dropped
+// if the staged blocks do not fit. Returns false if not even unstaged blocks
+// fit.
+bool one_launch_shape(const swept2d_batch *b, bool *stage, long long *tiles) {
+    int sides[swept::kMaxClassRuns], count = 0;
     *tiles = 0;
-    for (const auto &c : b->classes) {
-        if (!c.n) continue;
-        *tiles += (long long)c.tiles.size();
-        if (c.n > *max_n) *max_n = c.n;
-    }
-    if (tn.threads > 256) tn.threads = 256;
+    for (const auto &c : b->classes)
+        if (c.n && count < swept::kMaxClassRuns) {
+            sides[count++] = c.n;
+            *tiles += (long long)c.tiles.size();
+        }
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (tn.stage && b->bt->smem_for(*max_n, true) > (size_t)optin) tn.stage = false;
-    return tn;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        optin = 227 * 1024;
+    *stage = b->tune.stage && b->bt->one_launch_smem(sides, count, true) <= (size_t)optin;
+    return b->bt->one_launch_smem(sides, count, *stage) <= (size_t)optin;
 }
 
 int batch_run(swept2d_batch *b, long long total, int mode) {
@@ -174,12 +171,11 @@ int batch_run(swept2d_batch *b, long long total, int mode) {
     if (persistent && one_launch) {
         // every class's half cycles in one launch; the tails follow per class
         swept::ClassRuns runs{};
-        long long nitems = 0;
         for (auto &c : b->classes) {
             const long long H = c.n > 0 ? total / (c.n / 2) : 0;
             if (H <= 0) continue;
             const int nt = (int)c.tiles.size();
-            cudaError_t e = cudaMemsetAsync(c.d_sched, 0, (size_t)nt * sizeof(int), b->stream);
+            cudaError_t e = cudaMemsetAsync(c.d_sched, 0, ((size_t)nt + 1) * sizeof(int), b->stream);
             if (e != cudaSuccess) return bcuda(b, e, "persistent schedule reset");
             swept::ClassRun &r = runs.r[runs.count++];
             r.tiles = c.d_tiles;
@@ -187,19 +183,16 @@ int batch_run(swept2d_batch *b, long long total, int mode) {
             r.ntiles = nt;
             r.n = c.n;
             r.H = (int)H;
-            r.first = nitems;
-            nitems += swept::persistent_items(nt, H);
         }
         if (runs.count > 0) {
-            cudaError_t e = cudaMemsetAsync(b->d_queue, 0, sizeof(unsigned long long), b->stream);
-            if (e != cudaSuccess) return bcuda(b, e, "persistent queue reset");
-            int max_n = 0;
+            bool stage = false;
             long long tiles = 0;
-            const swept::Tuning tn = one_launch_tuning(b, &max_n, &tiles);
+            one_launch_shape(b, &stage, &tiles);
+            swept::Tuning tn = b->tune;
+            tn.stage = stage;
             int rc = blaunch(b, "batched one-launch persistent kernel", [&] {
-                return b->bt->persistent_all(b->d_grids, runs, nitems, tiles, max_n, b->state,
-                                             b->up, b->br, b->d_queue, g_start, b->errword, tn,
-                                             b->stream);
+                return b->bt->persistent_all(b->d_grids, runs, tiles, b->state, b->up, b->br,
+                                             g_start, b->errword, tn, b->stream);
             });
             if (rc) return rc;
         }
@@ -514,9 +507,11 @@ int swept2d_batch_advance(swept2d_batch_t *b, long long nsteps, int mode) {
         for (auto &c : b->classes) swept_classes += c.n ? 1 : 0;
         if (one_launch && swept_classes > swept::kMaxClassRuns)
             return bfail(b, SWEPT2D_EINVAL, "advance: the one-launch form takes at most 16 classes");
-        if (one_launch && !b->d_queue) {
-            cudaError_t e = cudaMalloc(&b->d_queue, sizeof(unsigned long long));
-            if (e != cudaSuccess) return bcuda(b, e, "persistent queue allocation");
+        if (one_launch) {
+            bool stage = false;
+            long long tiles = 0;
+            if (!one_launch_shape(b, &stage, &tiles))
+                return bfail(b, SWEPT2D_EINVAL, "advance: the one-launch blocks do not fit in shared memory");
         }
         for (auto &c : b->classes) {
             if (!c.n) continue;

@@ -192,19 +192,82 @@ __device__ __forceinline__ void mbar_inval(unsigned long long *bar) {
     asm volatile("mbarrier.inval.shared::cta.b64 [%0];\n" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// Every thread waits for phase 0 of `bar`; returns false (the same for the
-// whole block) if the wait gave up, after recording it in *err.
+// The threads that run one tile work item: the whole block (BlockTeam: every
+// kernel of the single-grid and per-class paths), or one of the block's teams
+// of T threads (TeamOf<T>: the one-launch batch kernel, whose blocks, sized for
+// the largest tile class, run several small tiles at once). rank() and size()
+// take the place of threadIdx.x and blockDim.x, sync() of the block barrier
+// (a warp barrier, or a named barrier per team), index() picks the team's
+// slice of shared memory.
+struct BlockTeam {
+    static constexpr int kSize = 0;
+    __device__ __forceinline__ static unsigned rank() { return threadIdx.x; }
+    __device__ __forceinline__ static unsigned size() { return blockDim.x; }
+    __device__ __forceinline__ static int index() { return 0; }
+    __device__ __forceinline__ static void sync() { __syncthreads(); }
+    __device__ __forceinline__ static int sync_or(int p) { return __syncthreads_or(p); }
+};
+constexpr int kMaxTeams = 15;   // named barriers 1..15 (0 is the block's)
+template <int T>
+struct TeamOf {
+    static_assert(T >= 32 && T % 32 == 0, "a team is whole warps");
+    static constexpr int kSize = T;
+    __device__ __forceinline__ static unsigned rank() { return threadIdx.x % T; }
+    __device__ __forceinline__ static unsigned size() { return T; }
+    __device__ __forceinline__ static int index() { return (int)threadIdx.x / T; }
+    __device__ __forceinline__ static void sync() {
+        if constexpr (T == 32)
+            __syncwarp();
+        else
+            asm volatile("bar.sync %0, %1;\n" ::"r"(1 + index()), "n"(T) : "memory");
+    }
+    __device__ __forceinline__ static int sync_or(int p) {
+        if constexpr (T == 32) {
+            __syncwarp();
+            return __any_sync(0xffffffffu, p);
+        } else {
+            int r;
+            asm volatile(
+                "{\n .reg .pred q, o;\n setp.ne.s32 q, %1, 0;\n"
+                " bar.red.or.pred o, %2, %3, q;\n selp.s32 %0, 1, 0, o;\n}\n"
+                : "=r"(r)
+                : "r"(p), "r"(1 + index()), "n"(T)
+                : "memory");
+            return r;
+        }
+    }
+};
+
+// A team's slice of the block's dynamic shared memory at tile side n: the
+// largest swept block's plan (four staged panel segments when STG), rounded
+// up to 128 bytes; the whole of it for a BlockTeam.
+template <class Op, bool STG>
+__host__ __device__ inline size_t team_slice(int n) {
+    return (smem_plan<Op>(n, 4, STG).total + 127) & ~(size_t)127;
+}
+template <class Op, bool STG, class Tm>
+__device__ __forceinline__ unsigned char *team_smem(int n) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if constexpr (Tm::kSize == 0)
+        return smem_raw;
+    else
+        return smem_raw + (size_t)Tm::index() * team_slice<Op, STG>(n);
+}
+
+// Every thread of the team waits for phase 0 of `bar`; returns false (the same
+// for the whole team) if the wait gave up, after recording it in *err.
+template <class Tm = BlockTeam>
 __device__ __forceinline__ bool block_wait_bulk(unsigned long long *bar, int *err) {
     bool ok = false;
     for (long long it = 0; it < kSpinLimit && !ok; ++it) ok = mbar_try_wait(bar, 0);
-    const int bad = __syncthreads_or(!ok);
+    const int bad = Tm::sync_or(!ok);
     if (bad) {
-        if (threadIdx.x == 0) {
+        if (Tm::rank() == 0) {
             if (err) atomicExch(err, 1);
             for (long long it = 0; it < kSpinLimit; ++it)   // let copies in flight land
                 if (mbar_try_wait(bar, 0)) break;
         }
-        __syncthreads();
+        Tm::sync();
         return false;
     }
     return true;
@@ -228,11 +291,10 @@ __device__ __forceinline__ float recip_small(int d) { return __fdividef(1.0f, (f
 
 struct LinearWalk {
     int xx, yy, dq, dr;
-    __device__ __forceinline__ explicit LinearWalk(int W) {
-        const int T = blockDim.x;
+    __device__ __forceinline__ LinearWalk(int W, int t, int T) {
         const float rw = recip_small(W);
-        yy = div_small((int)threadIdx.x, rw);
-        xx = (int)threadIdx.x - yy * W;
+        yy = div_small(t, rw);
+        xx = t - yy * W;
         dq = div_small(T, rw);
         dr = T - dq * W;
     }
@@ -255,13 +317,14 @@ struct LinearWalk {
 // order. (The shape rule is where a bank-count model of both orders at the
 // stencil's five offsets favours column pairs for 4-byte elements; 8- and
 // 2-byte elements measured no faster, and take row order: PAIRS = false.)
-template <bool PAIRS, class F>
+template <bool PAIRS, class Tm = BlockTeam, class F>
 __device__ __forceinline__ void for_each_point(int W, int H, F &&f) {
     if (PAIRS && W < 32 && (H >= 14 || (W <= 10 && H >= 6))) {
-        for (LinearWalk w(2 * H); w.yy < (W >> 1); w.next(2 * H))
+        for (LinearWalk w(2 * H, (int)Tm::rank(), (int)Tm::size()); w.yy < (W >> 1);
+             w.next(2 * H))
             f(2 * w.yy + (w.xx & 1), w.xx >> 1);
     } else {
-        for (LinearWalk w(W); w.yy < H; w.next(W)) f(w.xx, w.yy);
+        for (LinearWalk w(W, (int)Tm::rank(), (int)Tm::size()); w.yy < H; w.next(W)) f(w.xx, w.yy);
     }
 }
 
@@ -301,7 +364,7 @@ struct GlobalAcc {
 // Apply the point update on the local rectangle [x0, x0+W) x [y0, y0+H) of the
 // level buffer src, writing dst. Threads take consecutive points of the
 // rectangle so that warps stay full.
-template <class Op>
+template <class Tm = BlockTeam, class Op>
 __device__ __forceinline__ void compute_rect(const Op &op, int stage, u64 g,
                                              const typename Op::S *src, typename Op::S *dst,
                                              typename Op::S * /*aux*/, int P, int x0, int y0,
@@ -309,7 +372,7 @@ __device__ __forceinline__ void compute_rect(const Op &op, int stage, u64 g,
     typedef typename Op::S S;
     const int plane = P * P;
     if (W <= 0) return;
-    for (LinearWalk w(W); w.yy < H; w.next(W)) {
+    for (LinearWalk w(W, (int)Tm::rank(), (int)Tm::size()); w.yy < H; w.next(W)) {
         const int off = (y0 + w.yy + 1) * P + (x0 + w.xx + 1);
         SmemAcc<S> acc{src + off, P, plane};
         S out[Op::NV];
@@ -330,7 +393,7 @@ __device__ __forceinline__ void compute_rect(const Op &op, int stage, u64 g,
 // no neighbour value of the level is read any more. The pair sums of a level
 // are packed with row pitch W + 1 (entry e of pass 1 at aux[e]), so the aux
 // buffer needs only the largest (W + 1)(H + 1) of the block's levels.
-template <class Mid>
+template <class Tm = BlockTeam, class Mid>
 __device__ __forceinline__ void compute_rect_mid(const HeatOp &op, int, u64, const double *src,
                                                  double *dst, double *aux, int P, int x0, int y0,
                                                  int W, int H, Mid &&mid) {
@@ -338,15 +401,15 @@ __device__ __forceinline__ void compute_rect_mid(const HeatOp &op, int, u64, con
     // points per thread visible to the scheduler better than a carried walk)
     const int W1 = W + 1, cnt1 = W1 * (H + 1);
     const float rw1 = recip_small(W1), rw = recip_small(W);
-    for (int e = threadIdx.x; e < cnt1; e += blockDim.x) {
+    for (int e = Tm::rank(); e < cnt1; e += Tm::size()) {
         const int yy = div_small(e, rw1), xx = e - yy * W1;
         const int off = (y0 + yy) * P + (x0 + xx);      // point (x0-1+xx, y0-1+yy)
         aux[e] = __dadd_rn(src[off + 1], src[off + P]);
     }
-    __syncthreads();
+    Tm::sync();
     mid();
     const int cnt = W * H;
-    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+    for (int e = Tm::rank(); e < cnt; e += Tm::size()) {
         const int yy = div_small(e, rw), xx = e - yy * W;
         const int off = (y0 + yy + 1) * P + (x0 + xx + 1);
         const int a = e + yy;                            // Pr(x-1, y-1); Pr(x, y) at a + W + 2
@@ -386,7 +449,7 @@ __device__ __forceinline__ void heat_kahan_strip(const HeatKahanOp<SS> &op,
                       dst[plane + off + r * P]);
 }
 
-template <class SS>
+template <class Tm = BlockTeam, class SS>
 __device__ __forceinline__ void compute_rect(const HeatKahanOp<SS> &op, int, u64,
                                              const SS *__restrict__ src, SS *__restrict__ dst,
                                              SS *, int P, int x0, int y0, int W, int H) {
@@ -394,7 +457,7 @@ __device__ __forceinline__ void compute_rect(const HeatKahanOp<SS> &op, int, u64
     const int plane = P * P;
     if (W <= 0 || H <= 0) return;
     const int nb = (H + R - 1) / R;
-    for (LinearWalk w(W); w.yy < nb; w.next(W)) {
+    for (LinearWalk w(W, (int)Tm::rank(), (int)Tm::size()); w.yy < nb; w.next(W)) {
         const int yb = w.yy * R;
         const int rows = H - yb;
         const int off = (y0 + yb + 1) * P + (x0 + w.xx + 1);
@@ -419,13 +482,14 @@ __device__ __forceinline__ void compute_rect(const HeatKahanOp<SS> &op, int, u64
 // The aux planes of a level are packed: row pitch A = flux_pitch(W), plane
 // pitch A (H + 2), so the aux buffer needs only the largest such rectangle of
 // the block's levels (a bridge's levels are far smaller than a tile).
+template <class Tm = BlockTeam>
 __device__ __forceinline__ void compute_rect(const EulerOp &op, int stage, u64, const double *src,
                                              double *dst, double *aux, int P, int x0, int y0,
                                              int W, int H) {
     const int plane = P * P, w0 = stage == 0 ? 0 : 4;
     if (W <= 0 || H <= 0) return;
     const int A = flux_pitch(W), fp = A * (H + 2);
-    for_each_point<false>(W + 2, H + 2, [&](int xx, int yy) {
+    for_each_point<false, Tm>(W + 2, H + 2, [&](int xx, int yy) {
         const int off = (y0 + yy) * P + (x0 + xx);     // point (x0-1+xx, y0-1+yy)
         const int a = yy * A + xx;
         double u, v, pr, Ep;
@@ -436,8 +500,8 @@ __device__ __forceinline__ void compute_rect(const EulerOp &op, int stage, u64, 
         aux[2 * fp + a] = pr;
         aux[3 * fp + a] = Ep;
     });
-    __syncthreads();
-    for_each_point<false>(W, H, [&](int xx, int yy) {
+    Tm::sync();
+    for_each_point<false, Tm>(W, H, [&](int xx, int yy) {
         const int off = (y0 + yy + 1) * P + (x0 + xx + 1);
         const int a = (yy + 1) * A + xx + 1;
         const double *M = src + (w0 + 1) * plane + off, *Q = src + (w0 + 2) * plane + off;
@@ -472,7 +536,7 @@ __device__ __forceinline__ void compute_rect(const EulerOp &op, int stage, u64, 
 // EulerOp (binary32 primitives of the grown rectangle in the aux planes, then
 // the per-point fluxes and combination). Same values as
 // EulerKahanOp::operator().
-template <class SS>
+template <class Tm = BlockTeam, class SS>
 __device__ __forceinline__ void compute_rect(const EulerKahanOp<SS> &op, int stage, u64,
                                              const SS *src, SS *dst, SS *aux_s, int P, int x0,
                                              int y0, int W, int H) {
@@ -481,7 +545,7 @@ __device__ __forceinline__ void compute_rect(const EulerKahanOp<SS> &op, int sta
     const int plane = P * P, w0 = stage == 0 ? 0 : 4;
     if (W <= 0 || H <= 0) return;
     const int A = flux_pitch(W), fp = A * (H + 2);   // packed as for EulerOp
-    for_each_point<sizeof(SS) == 4>(W + 2, H + 2, [&](int xx, int yy) {
+    for_each_point<sizeof(SS) == 4, Tm>(W + 2, H + 2, [&](int xx, int yy) {
         const int off = (y0 + yy) * P + (x0 + xx);     // point (x0-1+xx, y0-1+yy)
         const int a = yy * A + xx;
         float u, v, pr, Ep;
@@ -493,8 +557,8 @@ __device__ __forceinline__ void compute_rect(const EulerKahanOp<SS> &op, int sta
         aux[2 * fp + a] = pr;
         aux[3 * fp + a] = Ep;
     });
-    __syncthreads();
-    for_each_point<sizeof(SS) == 4>(W, H, [&](int xx, int yy) {
+    Tm::sync();
+    for_each_point<sizeof(SS) == 4, Tm>(W, H, [&](int xx, int yy) {
         const int off = (y0 + yy + 1) * P + (x0 + xx + 1);
         const int a = (yy + 1) * A + xx + 1;
         const SS *M = src + (w0 + 1) * plane + off, *Q = src + (w0 + 2) * plane + off;
@@ -537,22 +601,22 @@ __device__ __forceinline__ void compute_rect(const EulerKahanOp<SS> &op, int sta
 // u' = (2u - u_old) + C^2 d, u_old' = u. Pass 2 reads only the centre's two
 // values and the pair sums, so it may write the level in place; `mid` runs
 // between the passes.
-template <class Mid>
+template <class Tm = BlockTeam, class Mid>
 __device__ __forceinline__ void compute_rect_mid(const WaveOp &op, int, u64, const double *src,
                                                  double *dst, double *aux, int P, int x0, int y0,
                                                  int W, int H, Mid &&mid) {
     const int plane = P * P;
     const int W1 = W + 1, cnt1 = W1 * (H + 1);
     const float rw1 = recip_small(W1), rw = recip_small(W);
-    for (int e = threadIdx.x; e < cnt1; e += blockDim.x) {
+    for (int e = Tm::rank(); e < cnt1; e += Tm::size()) {
         const int yy = div_small(e, rw1), xx = e - yy * W1;
         const int off = (y0 + yy) * P + (x0 + xx);      // point (x0-1+xx, y0-1+yy)
         aux[e] = __dadd_rn(src[off + 1], src[off + P]);
     }
-    __syncthreads();
+    Tm::sync();
     mid();
     const int cnt = W * H;
-    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+    for (int e = Tm::rank(); e < cnt; e += Tm::size()) {
         const int yy = div_small(e, rw), xx = e - yy * W;
         const int off = (y0 + yy + 1) * P + (x0 + xx + 1);
         const int a = e + yy;                            // packed as for the heat update
@@ -568,16 +632,16 @@ __device__ __forceinline__ void compute_rect_mid(const WaveOp &op, int, u64, con
 // the next level's ring or strip into `nxt`: for INPLACE_AFTER_AUX updates
 // after the level's first pass (it overwrites neighbour values that pass
 // reads), otherwise before the computation (the caller's prefetch).
-template <class Op, class Next>
+template <class Tm = BlockTeam, class Op, class Next>
 __device__ __forceinline__ void level_step(const Op &op, int stage, u64 g,
                                            const typename Op::S *cur, typename Op::S *nxt,
                                            typename Op::S *aux, int P,
                                            int x0, int y0, int W, int H, Next &&next) {
     if constexpr (Op::INPLACE_AFTER_AUX) {
-        compute_rect_mid(op, stage, g, cur, nxt, aux, P, x0, y0, W, H, next);
+        compute_rect_mid<Tm>(op, stage, g, cur, nxt, aux, P, x0, y0, W, H, next);
     } else {
         next();
-        compute_rect(op, stage, g, cur, nxt, aux, P, x0, y0, W, H);
+        compute_rect<Tm>(op, stage, g, cur, nxt, aux, P, x0, y0, W, H);
     }
 }
 
@@ -595,14 +659,14 @@ __device__ __forceinline__ void up_panel_xy(int side, int n, int k, int d, int p
 // The block's threads take the level's 4 sides x 2 lines x L elements in
 // order (element e: line e div L, position e mod L), so short lines at deep
 // levels or small tiles do not leave most lanes idle.
-template <class S, int NV>
+template <class S, int NV, class Tm = BlockTeam>
 __device__ __forceinline__ void write_up_panels(const S *cur, int P, const Geom &G, int k,
                                                 S *up, int slot) {
     const int n = G.n, L = n - 2 * k, plane = P * P;
     const int off = 2 * k * (n - k + 1);
     const float rl = recip_small(L);
     S *tile = up + (size_t)slot * 4 * NV * G.PS + off;
-    for (int e = threadIdx.x; e < 8 * L; e += blockDim.x) {
+    for (int e = Tm::rank(); e < 8 * L; e += Tm::size()) {
         const int q = div_small(e, rl);          // side * 2 + line
         const int p = e - q * L, side = q >> 1, d = q & 1;
         int a, b;
@@ -696,7 +760,7 @@ __global__ void __launch_bounds__(256) naive_heat_kahan_kernel(HeatKahanOp<SS> o
 // ------------------------------------------------------- UpwardPyramid (Alg. 1)
 // Shared body: tile at level 0 of half cycle g0 is in buffer 0; builds levels
 // 1..h-1 and writes the up panels of levels 0..h-1 to slot `slot`.
-template <class Op>
+template <class Op, class Tm = BlockTeam>
 __device__ __forceinline__ void up_body(const Op &op, const Geom &G, typename Op::S *buf0,
                                         typename Op::S *buf1, typename Op::S *aux, int P, u64 g0,
                                         typename Op::S *up, int slot, int first_parity) {
@@ -706,32 +770,32 @@ __device__ __forceinline__ void up_body(const Op &op, const Geom &G, typename Op
         const int par = (first_parity + k) & 1;
         const S *cur = par ? buf1 : buf0;
         S *nxt = par ? buf0 : buf1;
-        write_up_panels<S, Op::NV>(cur, P, G, k, up, slot);
+        write_up_panels<S, Op::NV, Tm>(cur, P, G, k, up, slot);
         // panels read before the level is overwritten (INPLACE_AFTER_AUX updates
         // overwrite it only after the barrier between their two passes)
-        if constexpr (Op::INPLACE) __syncthreads();
+        if constexpr (Op::INPLACE) Tm::sync();
         if (k + 1 < h) {
             const u64 g = g0 + k;
-            level_step(op, (int)(g % Op::NST), g, cur, nxt, aux, P, k + 1, k + 1, n - 2 * k - 2,
+            level_step<Tm>(op, (int)(g % Op::NST), g, cur, nxt, aux, P, k + 1, k + 1, n - 2 * k - 2,
                        n - 2 * k - 2, [] {});
         }
-        __syncthreads();
+        Tm::sync();
     }
 }
 
 // K1: first upward pyramid of an advance, frame offset o, reading the state.
-template <class Op>
+template <class Op, class Tm = BlockTeam, bool STG = false>
 __device__ __forceinline__ void up_tile(const Op &op, const Geom &G, const typename Op::S *state,
                                         typename Op::S *up, int o, u64 g0, int I, int J) {
     typedef typename Op::S S;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char *smem_raw = team_smem<Op, STG, Tm>(G.n);
     const int n = G.n, P = n + 2, plane = P * P;
     S *buf0 = reinterpret_cast<S *>(smem_raw);
     S *buf1 = one_buffer<Op>() ? buf0 : buf0 + Op::NV * plane;   // one buffer for in-place levels
     S *aux = buf1 + Op::NV * plane;
     const size_t gplane = (size_t)G.nx * G.ny;
     const int x0 = o + I * n, y0 = o + J * n;
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    for (int e = Tm::rank(); e < n * n; e += Tm::size()) {
         const int b = e / n, a = e - b * n;
         int x = x0 + a; x -= x >= G.nx ? G.nx : 0;
         int y = y0 + b; y -= y >= G.ny ? G.ny : 0;
@@ -739,8 +803,8 @@ __device__ __forceinline__ void up_tile(const Op &op, const Geom &G, const typen
         for (int v = 0; v < Op::NV; ++v)
             buf0[v * plane + (b + 1) * P + (a + 1)] = state[v * gplane + (size_t)y * G.nx + x];
     }
-    __syncthreads();
-    up_body(op, G, buf0, buf1, aux, P, g0, up, J * G.T + I, 0);
+    Tm::sync();
+    up_body<Op, Tm>(op, G, buf0, buf1, aux, P, g0, up, J * G.T + I, 0);
 }
 
 template <class Op, int NC = 0>
@@ -755,13 +819,13 @@ up_kernel(Op op, Geom G, const typename Op::S *state, typename Op::S *up, int o,
 // and Up(I+1,J), frame (o+h, o). Both run levels 1..h-1 of half cycle g0.
 // In "along/across" coordinates (u along the bridge, w across it) the two are
 // the same; (x, y) = (u, w) for the y-bridge and (w, u) for the x-bridge.
-template <class Op, bool STG>
+template <class Op, bool STG, class Tm = BlockTeam>
 __device__ __forceinline__ void bridge_tile(const Op &op, const Geom &G, const typename Op::S *up,
                                             typename Op::S *br, u64 g0, int *err, int I, int J,
                                             bool xb) {
     typedef typename Op::S S;
     constexpr int NV = Op::NV;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char *smem_raw = team_smem<Op, STG, Tm>(G.n);
     const int n = G.n, h = n / 2, P = n + 2, plane = P * P;
     S *bufs[2];
     bufs[0] = reinterpret_cast<S *>(smem_raw);
@@ -787,24 +851,24 @@ __device__ __forceinline__ void bridge_tile(const Op &op, const Geom &G, const t
         const SmemPlan pl = smem_plan<Op>(n, 2, true, true);
         S *st = reinterpret_cast<S *>(smem_raw + pl.stage_off);
         unsigned long long *bar = reinterpret_cast<unsigned long long *>(smem_raw + pl.bar_off);
-        if (threadIdx.x == 0) mbar_init(bar, 1);
-        __syncthreads();
-        if (threadIdx.x == 0) {
+        if (Tm::rank() == 0) mbar_init(bar, 1);
+        Tm::sync();
+        if (Tm::rank() == 0) {
             const unsigned bytes = (unsigned)(G.PS * sizeof(S));
             mbar_expect_tx(bar, 2 * NV * bytes);
             for (int w = 0; w < 2; ++w)
                 for (int v = 0; v < NV; ++v)
                     bulk_g2s(st + (w * NV + v) * G.PS, seg[w] + (size_t)v * G.PS, bytes, bar);
         }
-        if (!block_wait_bulk(bar, err)) return;
-        if (threadIdx.x == 0) mbar_inval(bar);   // the block may stage again (persistent form)
+        if (!block_wait_bulk<Tm>(bar, err)) return;
+        if (Tm::rank() == 0) mbar_inval(bar);   // the block may stage again (persistent form)
         stg = st;
     }
     auto load_strips = [&](int k, S *dst) {
         const int L = n - 2 * k;
         const int off = 2 * k * (n - k + 1);
         const float rl = recip_small(L);
-        for (int e = threadIdx.x; e < 4 * L; e += blockDim.x) {   // 2 strips x 2 lines x L
+        for (int e = Tm::rank(); e < 4 * L; e += Tm::size()) {   // 2 strips x 2 lines x L
             const int q = div_small(e, rl);
             const int p = e - q * L, which = q >> 1, d = q & 1;
             const int ww = which ? h + k + d : h - 1 - k - d;
@@ -835,7 +899,7 @@ __device__ __forceinline__ void bridge_tile(const Op &op, const Geom &G, const t
         for (int k = 0; k < h; ++k) load_strips(k, bufs[k & 1]);
     }
     if constexpr (!STG) async_wait();
-    __syncthreads();
+    Tm::sync();
     for (int k = 0; k < h; ++k) {
         S *cur = bufs[k & 1];
         S *nxt = bufs[(k + 1) & 1];
@@ -844,7 +908,7 @@ __device__ __forceinline__ void bridge_tile(const Op &op, const Geom &G, const t
             const int L = 2 * k + 2;
             const int off = 2 * k * (k + 1);
             const float rl = recip_small(L);
-            for (int e = threadIdx.x; e < 4 * L; e += blockDim.x) {
+            for (int e = Tm::rank(); e < 4 * L; e += Tm::size()) {
                 const int q = div_small(e, rl);
                 const int p = e - q * L, which = q >> 1, d = q & 1;
                 const int uu = which ? n - 1 - k - d : k + d;
@@ -859,7 +923,7 @@ __device__ __forceinline__ void bridge_tile(const Op &op, const Geom &G, const t
         }
         // panels read before the strip copy below (INPLACE_AFTER_AUX updates
         // copy it only after the barrier between their two passes)
-        if constexpr (Op::INPLACE) __syncthreads();
+        if constexpr (Op::INPLACE) Tm::sync();
         if (k + 1 < h) {
             // the next strip lies outside the rectangle below; it overlaps the
             // rectangle's outermost neighbours: INPLACE updates keep the planes
@@ -871,12 +935,12 @@ __device__ __forceinline__ void bridge_tile(const Op &op, const Geom &G, const t
             const u64 g = g0 + k;
             const int u0 = k + 1, uw = n - 2 * k - 2, w0 = h - k - 1, ww = 2 * k + 2;
             if (xb)
-                level_step(op, (int)(g % Op::NST), g, cur, nxt, aux, P, w0, u0, ww, uw, next);
+                level_step<Tm>(op, (int)(g % Op::NST), g, cur, nxt, aux, P, w0, u0, ww, uw, next);
             else
-                level_step(op, (int)(g % Op::NST), g, cur, nxt, aux, P, u0, w0, uw, ww, next);
+                level_step<Tm>(op, (int)(g % Op::NST), g, cur, nxt, aux, P, u0, w0, uw, ww, next);
             if constexpr (per_level && !STG) async_wait();
         }
-        __syncthreads();
+        Tm::sync();
     }
 }
 
@@ -890,7 +954,7 @@ bridge_kernel(Op op, Geom G, const typename Op::S *up, typename Op::S *br, u64 g
 // --------------------------------------------- DownwardPyramid (Algorithm 5)
 // Down(I,J) in frame (o+h, o+h): levels 1..h of half cycle g0 from the bridge
 // panels. Ends with the full tile at level h in buffer (h & 1).
-template <class Op, bool STG>
+template <class Op, bool STG, class Tm = BlockTeam>
 __device__ __forceinline__ bool down_body(const Op &op, const Geom &G, unsigned char *smem_raw,
                                           typename Op::S *buf0, typename Op::S *buf1,
                                           typename Op::S *aux, int P, const typename Op::S *br,
@@ -910,24 +974,24 @@ __device__ __forceinline__ bool down_body(const Op &op, const Geom &G, unsigned 
         const SmemPlan pl = smem_plan<Op>(n, 4, true);
         S *st = reinterpret_cast<S *>(smem_raw + pl.stage_off);
         unsigned long long *bar = reinterpret_cast<unsigned long long *>(smem_raw + pl.bar_off);
-        if (threadIdx.x == 0) mbar_init(bar, 1);
-        __syncthreads();
-        if (threadIdx.x == 0) {
+        if (Tm::rank() == 0) mbar_init(bar, 1);
+        Tm::sync();
+        if (Tm::rank() == 0) {
             const unsigned bytes = (unsigned)(G.PS * sizeof(S));
             mbar_expect_tx(bar, 4 * NV * bytes);
             for (int side = 0; side < 4; ++side)
                 for (int v = 0; v < NV; ++v)
                     bulk_g2s(st + (side * NV + v) * G.PS, seg[side] + (size_t)v * G.PS, bytes, bar);
         }
-        if (!block_wait_bulk(bar, err)) return false;
-        if (threadIdx.x == 0) mbar_inval(bar);
+        if (!block_wait_bulk<Tm>(bar, err)) return false;
+        if (Tm::rank() == 0) mbar_inval(bar);
         stg = st;
     }
     auto load_ring = [&](int k, S *dst) {
         const int L = 2 * k + 2;
         const int off = 2 * k * (k + 1);
         const float rl = recip_small(L);
-        for (int e = threadIdx.x; e < 8 * L; e += blockDim.x) {   // 4 sides x 2 lines x L
+        for (int e = Tm::rank(); e < 8 * L; e += Tm::size()) {   // 4 sides x 2 lines x L
             const int q = div_small(e, rl);
             const int p = e - q * L, side = q >> 1, d = q & 1;
             // (x, y) of element p: x = bx + p ax, y = by + p ay
@@ -962,7 +1026,7 @@ __device__ __forceinline__ bool down_body(const Op &op, const Geom &G, unsigned 
         for (int k = 0; k < h; ++k) load_ring(k, (k & 1) ? buf1 : buf0);
     }
     if constexpr (!STG) async_wait();
-    __syncthreads();
+    Tm::sync();
     for (int k = 0; k < h; ++k) {
         S *cur = (k & 1) ? buf1 : buf0;
         S *nxt = (k & 1) ? buf0 : buf1;
@@ -975,34 +1039,34 @@ __device__ __forceinline__ bool down_body(const Op &op, const Geom &G, unsigned 
                 if (k + 1 < h) load_ring(k + 1, nxt);
         };
         const u64 g = g0 + k;
-        level_step(op, (int)(g % Op::NST), g, cur, nxt, aux, P, h - k - 1, h - k - 1, 2 * k + 2,
+        level_step<Tm>(op, (int)(g % Op::NST), g, cur, nxt, aux, P, h - k - 1, h - k - 1, 2 * k + 2,
                    2 * k + 2, next);
         if constexpr (per_level && !STG) async_wait();
-        __syncthreads();
+        Tm::sync();
     }
     return true;
 }
 
 // K3: octahedron = Down of half cycle g0 (frame o+h) fused with the Up of half
 // cycle g0+h in the same tile and frame; writes the next up panels.
-template <class Op, bool STG>
+template <class Op, bool STG, class Tm = BlockTeam>
 __device__ __forceinline__ void octahedron_tile(const Op &op, const Geom &G,
                                                 const typename Op::S *br, typename Op::S *up,
                                                 int o, u64 g0, int *err, int I, int J) {
     typedef typename Op::S S;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char *smem_raw = team_smem<Op, STG, Tm>(G.n);
     const int n = G.n, h = n / 2, P = n + 2, plane = P * P;
     S *buf0 = reinterpret_cast<S *>(smem_raw);
     S *buf1 = one_buffer<Op>() ? buf0 : buf0 + Op::NV * plane;   // one buffer for in-place levels
     S *aux = buf1 + Op::NV * plane;
-    if (!down_body<Op, STG>(op, G, smem_raw, buf0, buf1, aux, P, br, g0, err, I, J)) return;
+    if (!down_body<Op, STG, Tm>(op, G, smem_raw, buf0, buf1, aux, P, br, g0, err, I, J)) return;
     // Down(I,J) in frame o+h is Up(I,J) of frame h when o = 0, and Up(I+1,J+1)
     // of frame 0 when o = h.
     if (o != 0) {
         I = I + 1 == G.T ? 0 : I + 1;
         J = J + 1 == G.Q ? 0 : J + 1;
     }
-    up_body(op, G, buf0, buf1, aux, P, g0 + h, up, J * G.T + I, h & 1);
+    up_body<Op, Tm>(op, G, buf0, buf1, aux, P, g0 + h, up, J * G.T + I, h & 1);
 }
 
 template <class Op, bool STG, int NC = 0>
@@ -1013,21 +1077,21 @@ octahedron_kernel(Op op, Geom G, const typename Op::S *br, typename Op::S *up, i
 }
 
 // K4: final Down of an advance; writes the tile at level h to the state.
-template <class Op, bool STG>
+template <class Op, bool STG, class Tm = BlockTeam>
 __device__ __forceinline__ void down_tile(const Op &op, const Geom &G, const typename Op::S *br,
                                           typename Op::S *state, int o, u64 g0, int *err, int I,
                                           int J) {
     typedef typename Op::S S;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char *smem_raw = team_smem<Op, STG, Tm>(G.n);
     const int n = G.n, h = n / 2, P = n + 2, plane = P * P;
     S *buf0 = reinterpret_cast<S *>(smem_raw);
     S *buf1 = one_buffer<Op>() ? buf0 : buf0 + Op::NV * plane;   // one buffer for in-place levels
     S *aux = buf1 + Op::NV * plane;
-    if (!down_body<Op, STG>(op, G, smem_raw, buf0, buf1, aux, P, br, g0, err, I, J)) return;
+    if (!down_body<Op, STG, Tm>(op, G, smem_raw, buf0, buf1, aux, P, br, g0, err, I, J)) return;
     const S *fin = (h & 1) ? buf1 : buf0;
     const size_t gplane = (size_t)G.nx * G.ny;
     const int x0 = o + h + I * n, y0 = o + h + J * n;
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    for (int e = Tm::rank(); e < n * n; e += Tm::size()) {
         const int b = e / n, a = e - b * n;
         int x = x0 + a; x -= x >= G.nx ? G.nx : 0;
         int y = y0 + b; y -= y >= G.ny ? G.ny : 0;
@@ -1121,16 +1185,17 @@ __host__ __device__ inline long long persistent_items(long long NT, long long H)
 // `trace` (nullptr: none) receives, per work item, the SM clock cycles its
 // block spent waiting for the item's neighbourhood (trace[2 item]) and running
 // the item up to its release (trace[2 item + 1]).
-// One work item of the persistent form (every thread of the block calls it
+// One work item of the persistent form (every thread of the team calls it
 // with the same item): wait for the item's neighbourhood, run it, count it.
-// Returns false when a wait gave up (the block must stop).
-template <class Op, bool STG, int NC = 0, class Loc>
+// Returns false when a wait gave up (the team must stop).
+template <class Op, bool STG, int NC = 0, class Tm = BlockTeam, class Loc>
 __device__ __forceinline__ bool persistent_item(const Op &op, const Loc &at, int NT, int n,
                                                 typename Op::S *state, typename Op::S *upp,
                                                 typename Op::S *br, int *stage, int H, u64 g0,
                                                 int *err, int item, long long spin_limit,
                                                 unsigned *trace) {
-    __shared__ int s_fail;
+    __shared__ int s_fail_team[kMaxTeams];
+    int &s_fail = s_fail_team[Tm::index()];
     long long t_start = 0, t_ready = 0;
     const int h = (NC > 0 ? NC : n) / 2;
     // decode: kind 0 first Up, 1 bridge (xb: x-bridge), 2 octahedron or Down
@@ -1158,13 +1223,13 @@ __device__ __forceinline__ bool persistent_item(const Op &op, const Loc &at, int
     const Geom G = fixed_tile<NC>(w.G);
     const int I = w.I, J = w.J;
     const Op opi = w.c ? Op(w.c) : op;
-    if (threadIdx.x == 0) s_fail = 0;
-    if (trace && threadIdx.x == 0) t_start = clock64();
-    if (kind != 0 && threadIdx.x < 32) {
+    if (Tm::rank() == 0) s_fail = 0;
+    if (trace && Tm::rank() == 0) t_start = clock64();
+    if (kind != 0 && Tm::rank() < 32) {
         // lanes 0..8 wait for one tile each of the periodic 3 x 3 neighbourhood
         bool bad = false;
-        if (threadIdx.x < 9) {
-            const int dj = (int)threadIdx.x / 3 - 1, di = (int)threadIdx.x % 3 - 1;
+        if (Tm::rank() < 9) {
+            const int dj = (int)Tm::rank() / 3 - 1, di = (int)Tm::rank() % 3 - 1;
             const int jj = J + dj < 0 ? G.Q - 1 : (J + dj == G.Q ? 0 : J + dj);
             const int ii = I + di < 0 ? G.T - 1 : (I + di == G.T ? 0 : I + di);
             const int *flag = stage + w.base + jj * G.T + ii;
@@ -1180,27 +1245,27 @@ __device__ __forceinline__ bool persistent_item(const Op &op, const Loc &at, int
             }
         }
         bad = __any_sync(0xffffffffu, bad);
-        if (threadIdx.x == 0 && bad) {
+        if (Tm::rank() == 0 && bad) {
             atomicExch(err, 2);
             s_fail = 1;
         }
     }
-    __syncthreads();
+    Tm::sync();
     if (s_fail) return false;
-    if (trace && threadIdx.x == 0) t_ready = clock64();
+    if (trace && Tm::rank() == 0) t_ready = clock64();
     // the acquired panels are read next by bulk copies (the async proxy)
-    if (threadIdx.x == 0) asm volatile("fence.proxy.async.global;\n" ::: "memory");
+    if (Tm::rank() == 0) asm volatile("fence.proxy.async.global;\n" ::: "memory");
     typename Op::S *st = state + w.soff, *u = upp + w.poff, *b = br + w.poff;
     const u64 gj = g0 + (u64)j * h;
     const int o = (j & 1) ? h : 0;
     if (kind == 0) {
-        up_tile(opi, G, st, u, 0, g0, I, J);
+        up_tile<Op, Tm, STG>(opi, G, st, u, 0, g0, I, J);
     } else if (kind == 1) {                     // one bridge of half cycle j
-        bridge_tile<Op, STG>(opi, G, u, b, gj, err, I, J, xb);
+        bridge_tile<Op, STG, Tm>(opi, G, u, b, gj, err, I, J, xb);
     } else if (j + 1 < H) {
-        octahedron_tile<Op, STG>(opi, G, b, u, o, gj, err, I, J);
+        octahedron_tile<Op, STG, Tm>(opi, G, b, u, o, gj, err, I, J);
     } else {
-        down_tile<Op, STG>(opi, G, b, st, o, gj, err, I, J);
+        down_tile<Op, STG, Tm>(opi, G, b, st, o, gj, err, I, J);
     }
     // make this item's panel (and state) stores visible, to the generic and
     // the async proxy, before the release of its count; order this item's
@@ -1208,8 +1273,8 @@ __device__ __forceinline__ bool persistent_item(const Op &op, const Loc &at, int
     asm volatile("fence.proxy.async.global;\n" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
+    Tm::sync();
+    if (Tm::rank() == 0) {
         if (trace) {
             trace[2 * (size_t)item] = (unsigned)(t_ready - t_start);
             trace[2 * (size_t)item + 1] = (unsigned)(clock64() - t_ready);
