@@ -97,7 +97,8 @@ WORKLOADS = {
     "batch1024": Workload("heat_kahan", "f32", 0, 20_000, 0, (0.2,), "batch", 3,
                           "1024 independent periodic grids, nx and ny uniform in {32,48,...,512} "
                           "(seed 3), heat with binary32 storage and Kahan-compensated update, "
-                          "r=0.2, 20000 steps"),
+                          "r=0.2, 20000 steps", persistent=True,
+                          extra={"one_launch": True, "batch_tiles": "16,32"}),
     "batch1024_euler": Workload("euler_kahan", "f32", 0, 2_000, 0, (GAMMA, CFL, KAPPA), "batch",
                                 3, "1024 independent periodic grids, nx and ny uniform in "
                                 "{32,48,...,512} (seed 3), Euler with binary32 storage and "
@@ -136,8 +137,9 @@ def parse():
                    help="run each advance (swept and naive) as a captured CUDA graph")
     p.add_argument("--persistent", action="store_true",
                    help="swept arm: one persistent launch per advance")
-    p.add_argument("--batch-tiles", default="16,32,64",
-                   help="batches: candidate tile sides for the autotuner")
+    p.add_argument("--batch-tiles", default=None,
+                   help="batches: candidate tile sides for the autotuner (default 16,32,64; "
+                        "the heat batch's one-launch form: 16,32)")
     p.add_argument("--one-launch", action="store_true",
                    help="batches, with --persistent: one persistent launch for every tile class")
     p.add_argument("--no-secondary", action="store_true",
@@ -149,6 +151,10 @@ def parse():
     w = WORKLOADS[a.workload]
     if not a.persistent and not a.launch_per_phase:
         a.persistent = w.persistent
+        # the workload's default form (the heat batch: one launch for every class)
+        a.one_launch = a.one_launch or (a.persistent and w.extra.get("one_launch", False))
+    if a.batch_tiles is None:
+        a.batch_tiles = w.extra.get("batch_tiles", "16,32,64")
     for k in ("grid", "nsteps", "tile"):
         if getattr(a, k) is not None:
             setattr(w, k, getattr(a, k))
@@ -677,12 +683,11 @@ SECONDARY = (
     ("euler2048", ("--nsteps", "500")), ("euler2048_f32", ("--nsteps", "500")),
     ("euler2048_bf16", ("--nsteps", "500")),
     ("batch1024", ("--nsteps", "2000")), ("batch1024_euler", ("--nsteps", "200")),
-    # one persistent launch for the whole batch (every grid at tile 16: one
-    # block shape serves every class, and a one-warp block suits tile 16)
-    ("batch1024", ("--nsteps", "2000", "--persistent", "--one-launch", "--batch-tiles", "16",
-                   "--threads", "32")),
+    # the other batch form of each: heat per class (one launch per tile class
+    # and phase, graph), Euler in one persistent launch
+    ("batch1024", ("--nsteps", "2000", "--launch-per-phase", "--batch-tiles", "16,32,64")),
     ("batch1024_euler", ("--nsteps", "200", "--persistent", "--one-launch", "--batch-tiles",
-                         "16", "--threads", "64")),
+                         "16,32")),
 )
 
 

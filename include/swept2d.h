@@ -126,17 +126,16 @@ typedef struct swept2d swept2d_t;
  * handle's tuning (threads, staging); same bits. */
 #define SWEPT2D_PERSISTENT 0x200
 /* Batches only, OR-ed with SWEPT2D_SWEPT | SWEPT2D_PERSISTENT: one persistent
- * launch covers the half cycles of every tile class (each class's items after
- * the previous class's, one 64-bit counter handing them out; each class keeps
- * its own tile side, half-cycle count and neighbourhood counters), instead of
- * one persistent launch per class. The launch takes the batch-wide tuning of
- * swept2d_batch_set_tuning (default 256 threads, no staging; threads above 256
- * are taken as 256) and the shared memory of the largest tile side; staging is
- * dropped if that does not fit. One block shape serves every class, so the
- * small-tile classes run with the largest class's shared memory. Naive tails
- * (steps that do not fill a half cycle of a class) follow as before. Same bits.
- * EINVAL without SWEPT2D_PERSISTENT, for a single-grid handle, or with more than
- * 16 classes. */
+ * launch covers the half cycles of every tile class, instead of one persistent
+ * launch per class. Its blocks (256 threads, shared memory for the largest
+ * class) take the classes in order; the tile-16 and tile-32 classes run in
+ * teams of warps (one small tile per team), larger ones one tile per block;
+ * each class keeps its own tile side, half-cycle count, counters and item
+ * counter. Staging follows swept2d_batch_set_tuning and is dropped if the
+ * staged blocks do not fit; the thread count of that tuning is not used. Naive
+ * tails (steps that do not fill a half cycle of a class) follow as before.
+ * Same bits. EINVAL without SWEPT2D_PERSISTENT, for a single-grid handle, with
+ * more than 16 classes, or if even unstaged blocks do not fit. */
 #define SWEPT2D_ONE_LAUNCH 0x400
 
 /*
