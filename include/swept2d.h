@@ -212,7 +212,8 @@ int swept2d_query(const swept2d_t *h, int what, double *out);
 
 /* Launch shape of the swept kernels of a handle (a tuning knob, not a change
  * of results: every setting gives the same bits). threads: 32, 64, 128, 256 or 512
- * per block (default 256; the persistent form also takes up to 512). stage: 1 =
+ * per block (default 256; the persistent form also takes up to 512; the bridge
+ * launches of the launch-per-phase form take at most 256). stage: 1 =
  * the bridge and downward-pyramid blocks bring their whole input panel set
  * into shared memory with TMA bulk copies at block start; 0 = they copy every
  * level's strip or ring from device memory straight into its level buffer with

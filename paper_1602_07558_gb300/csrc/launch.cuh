@@ -175,10 +175,16 @@ struct Launch {
             return cudaGetLastError();
         });
     }
+    // A bridge's levels are thin rectangles (W + H = n), and its block is
+    // smaller than a pyramid's, so bridges take at most 256 threads: more,
+    // smaller blocks share an SM (the 4096² FP64 heat bridge at n = 64: five
+    // blocks of 256 per SM, 1.44 ms per launch, against four of 512, 1.48 ms).
+    static constexpr int kMaxBridgeThreads = 256;
     static cudaError_t bridge(const Geom &G, const double *c, const void *up, void *br, u64 g0,
                               int *err, const Tuning &tn, cudaStream_t st) {
-        return tn.stage ? bridge_t<true>(G, c, up, br, g0, err, tn.threads, st)
-                        : bridge_t<false>(G, c, up, br, g0, err, tn.threads, st);
+        const int thr = tn.threads > kMaxBridgeThreads ? kMaxBridgeThreads : tn.threads;
+        return tn.stage ? bridge_t<true>(G, c, up, br, g0, err, thr, st)
+                        : bridge_t<false>(G, c, up, br, g0, err, thr, st);
     }
     template <bool STG>
     static cudaError_t octahedron_t(const Geom &G, const double *c, const void *br, void *up,
