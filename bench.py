@@ -960,6 +960,28 @@ def run_batch(args, w, world, rank, local):
     tiles, class_tuning, tune_table = autotune_batch(nx, ny, w.op, w.params, dtype=w.dtype,
                                                      stream=stream, tiles=cand)
     stage = {str(k): v for k, v in class_tuning.items()}
+    sw_mode = ("persistent_one" if args.one_launch else "persistent") \
+        if args.persistent else "swept"
+
+    def tuned(sb):
+        if args.persistent and args.one_launch:
+            # one block shape for every class (the batch-wide tuning)
+            sb.set_tuning(args.threads or 256, args.stage or 0)
+        else:
+            for tile_n, (thr, stg) in class_tuning.items():
+                sb.set_tuning(thr, stg, tile=tile_n)
+
+    if args.profile_case:             # one short advance in the default form, for ncu
+        with SweptBatch(nx, ny, tiles, op=w.op, params=w.params, stream=stream,
+                        dtype=w.dtype) as sb:
+            tuned(sb)
+            with torch.cuda.stream(stream):
+                sb.set_state(dev)
+                sb.advance(64, mode=sw_mode)
+            torch.cuda.synchronize()
+        print(json.dumps({"profile_case": True, "workload": w.describe, "mode": sw_mode}),
+              flush=True)
+        return
 
     def timed(b, mode, k, wu):
         ev0 = torch.cuda.Event(enable_timing=True)
@@ -987,14 +1009,7 @@ def run_batch(args, w, world, rank, local):
     with ClockSampler(local) as clocks:
         with SweptBatch(nx, ny, tiles, op=w.op, params=w.params, stream=stream,
                         dtype=w.dtype) as sb:
-            if args.persistent and args.one_launch:
-                # one block shape for every class (the batch-wide tuning)
-                sb.set_tuning(args.threads or 256, args.stage or 0)
-            else:
-                for tile_n, (thr, stg) in class_tuning.items():
-                    sb.set_tuning(thr, stg, tile=tile_n)
-            sw_mode = ("persistent_one" if args.one_launch else "persistent") \
-                if args.persistent else "swept"
+            tuned(sb)
             ms_sw, launches = timed(sb, sw_mode, args.steps, args.warmup)
             out_sw = sb.get_state()
             h_in = torch.from_numpy(flat.copy()).pin_memory()
