@@ -176,10 +176,12 @@ struct Launch {
         });
     }
     // A bridge's levels are thin rectangles (W + H = n), and its block is
-    // smaller than a pyramid's, so bridges take at most 256 threads: more,
-    // smaller blocks share an SM (the 4096² FP64 heat bridge at n = 64: five
-    // blocks of 256 per SM, 1.44 ms per launch, against four of 512, 1.48 ms).
-    static constexpr int kMaxBridgeThreads = 256;
+    // smaller than a pyramid's, so bridges take at most 256 threads (128 for
+    // the wave update): more, smaller blocks share an SM (the 4096² FP64 heat
+    // bridge at n = 64: five blocks of 256 per SM, 1.44 ms per launch, against
+    // four of 512, 1.48 ms; the 1024² wave bridge at n = 32: 82 against 86 µs
+    // with 128 threads; the Euler bridges measured slower at 128).
+    static constexpr int kMaxBridgeThreads = std::is_same<Op, WaveOp>::value ? 128 : 256;
     static cudaError_t bridge(const Geom &G, const double *c, const void *up, void *br, u64 g0,
                               int *err, const Tuning &tn, cudaStream_t st) {
         const int thr = tn.threads > kMaxBridgeThreads ? kMaxBridgeThreads : tn.threads;
