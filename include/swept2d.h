@@ -141,9 +141,11 @@ typedef struct swept2d swept2d_t;
 /*
  * Create a handle for an nx x ny grid.
  *   tile   side n of the square tiles for the swept mode: even, >= 4, dividing
- *          nx and ny, and small enough that two (n+2)^2 x nvars level buffers
- *          (plus one (n+2)^2 plane of pair sums for HEAT) fit in shared memory;
- *          0 = naive mode only.
+ *          nx and ny, and small enough that a swept block's shared memory fits
+ *          (the (n+2)^2 x nvars level buffer, two for the updates not computed
+ *          in place, plus the level's scratch values: heat and wave one plane
+ *          of pair sums, Euler four planes of primitives; SWEPT2D_Q_SMEM_BYTES
+ *          gives the figure); 0 = naive mode only.
  *   params op parameters (see above); nparams their count.
  *   stream a cudaStream_t (NULL = legacy default stream).
  * Allocates the device state and, if tile > 0, two panel buffers of

@@ -27,12 +27,15 @@
 // north <- S of x-bridge(I,J), south <- N of x-bridge(I,J+1).
 //
 // Shared memory per block: two level buffers (Algorithm 1's U and D), each NV
-// planes of (n+2) x (n+2) with the tile at offset (1, 1), plus Op::AUX planes of
-// the same shape for point updates that stage partial results (heat: pair sums).
-// With staging (template flag STG) a block also gets its whole input panel set
-// (every level) in shared memory, brought in by TMA bulk copies at block start
-// on one mbarrier, so the level loop touches no global memory for its inputs;
-// without it, the next level's panel strip is prefetched with cp.async.
+// planes of (n+2) x (n+2) with the tile at offset (1, 1), or one for the updates
+// computed in place (one_buffer), plus Op::AUX planes of scratch values that a
+// level packs for its own rectangle (heat and wave: pair sums; Euler: the
+// primitives; see aux_elems). With staging (template flag STG) a block also
+// gets its whole input panel set (every level) in shared memory, brought in by
+// TMA bulk copies at block start on one mbarrier, so the level loop touches no
+// global memory for its inputs; without it, the panel strips are copied with
+// cp.async. The tile bodies run on a team of threads (BlockTeam: the block;
+// TeamOf<T>: a team of T threads with its own barrier and shared-memory slice).
 #pragma once
 #include <cuda_runtime.h>
 
