@@ -658,17 +658,47 @@ __device__ __forceinline__ void up_panel_xy(int side, int n, int k, int d, int p
     }
 }
 
+// One 16-byte store of two consecutive 8-byte panel elements (dst 16-byte
+// aligned: every panel line of 8-byte elements starts at an even element and
+// has an even length, and panels start on 64 bytes).
+template <class S>
+__device__ __forceinline__ void store_pair(S *dst, S a, S b) {
+    static_assert(sizeof(S) == 8, "pairs of 8-byte elements");
+    unsigned long long x, y;
+    memcpy(&x, &a, 8);
+    memcpy(&y, &b, 8);
+    asm volatile("st.global.v2.b64 [%0], {%1, %2};\n" ::"l"(dst), "l"(x), "l"(y) : "memory");
+}
+
 // Write level k of the 4 up panels of the tile held in cur to slot `slot`.
 // The block's threads take the level's 4 sides x 2 lines x L elements in
 // order (element e: line e div L, position e mod L), so short lines at deep
-// levels or small tiles do not leave most lanes idle.
+// levels or small tiles do not leave most lanes idle; 8-byte elements go out
+// in pairs, one 16-byte store each (L = n - 2k is even).
 template <class S, int NV, class Tm = BlockTeam>
 __device__ __forceinline__ void write_up_panels(const S *cur, int P, const Geom &G, int k,
                                                 S *up, int slot) {
     const int n = G.n, L = n - 2 * k, plane = P * P;
     const int off = 2 * k * (n - k + 1);
-    const float rl = recip_small(L);
     S *tile = up + (size_t)slot * 4 * NV * G.PS + off;
+    if constexpr (sizeof(S) == 8) {
+        const int Lh = L >> 1;
+        const float rh = recip_small(Lh);
+        for (int e = Tm::rank(); e < 4 * L; e += Tm::size()) {
+            const int q = div_small(e, rh);      // side * 2 + line
+            const int p = 2 * (e - q * Lh), side = q >> 1, d = q & 1;
+            int a, b;
+            up_panel_xy(side, n, k, d, p, a, b);
+            const S *src = cur + (b + 1) * P + (a + 1);
+            const int step = side < 2 ? 1 : P;   // N, S lines run along x; W, E along y
+            S *dst = tile + side * NV * G.PS + d * L + p;
+#pragma unroll
+            for (int v = 0; v < NV; ++v)
+                store_pair(dst + v * G.PS, src[v * plane], src[v * plane + step]);
+        }
+        return;
+    }
+    const float rl = recip_small(L);
     for (int e = Tm::rank(); e < 8 * L; e += Tm::size()) {
         const int q = div_small(e, rl);          // side * 2 + line
         const int p = e - q * L, side = q >> 1, d = q & 1;
@@ -906,8 +936,27 @@ __device__ __forceinline__ void bridge_tile(const Op &op, const Geom &G, const t
     for (int k = 0; k < h; ++k) {
         S *cur = bufs[k & 1];
         S *nxt = bufs[(k + 1) & 1];
-        // bridge panels of level k (2 sides x 2 lines x L, threads in order)
-        {
+        // bridge panels of level k (2 sides x 2 lines x L, threads in order;
+        // 8-byte elements in pairs, one 16-byte store each: L = 2k + 2 is even)
+        if constexpr (sizeof(S) == 8) {
+            const int L = 2 * k + 2, Lh = k + 1;
+            const int off = 2 * k * (k + 1);
+            const float rh = recip_small(Lh);
+            const int step = xb ? 1 : P;      // a line runs along the across axis
+            for (int e = Tm::rank(); e < 2 * L; e += Tm::size()) {
+                const int q = div_small(e, rh);
+                const int p = 2 * (e - q * Lh), which = q >> 1, d = q & 1;
+                const int uu = which ? n - 1 - k - d : k + d;
+                const int ww = h - k + (which ? hi_w_shift : lo_w_shift) + p;
+                const int x = xb ? ww : uu, y = xb ? uu : ww;
+                S *dst = br + ((size_t)slot * 4 + (which ? out_hi : out_lo)) * NV * G.PS + off +
+                         d * L + p;
+                const S *src = cur + (y + 1) * P + (x + 1);
+#pragma unroll
+                for (int v = 0; v < NV; ++v)
+                    store_pair(dst + (size_t)v * G.PS, src[v * plane], src[v * plane + step]);
+            }
+        } else {
             const int L = 2 * k + 2;
             const int off = 2 * k * (k + 1);
             const float rl = recip_small(L);

@@ -192,3 +192,20 @@ def test_packed_flux_planes_fit_index_and_keep_column_pairs_on_distinct_banks(n)
 def test_bridge_plan_is_not_larger_than_the_pyramids(n):
     for pair_sums in (True, False):
         assert aux_elems(n, True, pair_sums) <= aux_elems(n, False, pair_sums)
+
+
+@pytest.mark.parametrize("n", EVEN_SIZES)
+def test_panel_lines_of_8_byte_elements_start_on_16_bytes(n):
+    """The pair stores of 8-byte panel elements (two per 16-byte store) need
+    every line to start at an even element with an even length: up lines
+    L = n - 2k at 2k(n-k+1) + dL, bridge lines L = 2k + 2 at 2k(k+1) + dL, and
+    every panel at a multiple of panel_stride(n) (a multiple of 8 elements)."""
+    h = n // 2
+    ps = ((n * n // 2 + n) + 7) & ~7
+    assert ps % 8 == 0 and ps >= n * n // 2 + n
+    for k in range(h):
+        for L, off in ((n - 2 * k, 2 * k * (n - k + 1)), (2 * k + 2, 2 * k * (k + 1))):
+            assert L % 2 == 0
+            for d in (0, 1):
+                start = off + d * L
+                assert start % 2 == 0 and start + L <= n * n // 2 + n
