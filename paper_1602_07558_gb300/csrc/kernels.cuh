@@ -658,30 +658,47 @@ __device__ __forceinline__ void up_panel_xy(int side, int n, int k, int d, int p
     }
 }
 
-// One 16-byte store of two consecutive 8-byte panel elements (dst 16-byte
-// aligned: every panel line of 8-byte elements starts at an even element and
-// has an even length, and panels start on 64 bytes).
+// Panel writes in element pairs, one store per pair (else one per element).
+template <class S>
+__host__ __device__ constexpr bool pair_stores() { return true; }
+
+// One store of two consecutive panel elements: 16 bytes for 8-byte elements,
+// 8 for 4-byte, 4 for 2-byte (dst aligned to the pair: every panel line starts
+// at an even element and has an even length, and panels start on 64 bytes).
 template <class S>
 __device__ __forceinline__ void store_pair(S *dst, S a, S b) {
-    static_assert(sizeof(S) == 8, "pairs of 8-byte elements");
-    unsigned long long x, y;
-    memcpy(&x, &a, 8);
-    memcpy(&y, &b, 8);
-    asm volatile("st.global.v2.b64 [%0], {%1, %2};\n" ::"l"(dst), "l"(x), "l"(y) : "memory");
+    if constexpr (sizeof(S) == 8) {
+        unsigned long long x, y;
+        memcpy(&x, &a, 8);
+        memcpy(&y, &b, 8);
+        asm volatile("st.global.v2.b64 [%0], {%1, %2};\n" ::"l"(dst), "l"(x), "l"(y) : "memory");
+    } else if constexpr (sizeof(S) == 4) {
+        unsigned x, y;
+        memcpy(&x, &a, 4);
+        memcpy(&y, &b, 4);
+        asm volatile("st.global.v2.b32 [%0], {%1, %2};\n" ::"l"(dst), "r"(x), "r"(y) : "memory");
+    } else {
+        static_assert(sizeof(S) == 2, "2-, 4- or 8-byte elements");
+        unsigned short x, y;
+        memcpy(&x, &a, 2);
+        memcpy(&y, &b, 2);
+        const unsigned xy = (unsigned)x | ((unsigned)y << 16);   // a at the lower address
+        asm volatile("st.global.b32 [%0], %1;\n" ::"l"(dst), "r"(xy) : "memory");
+    }
 }
 
 // Write level k of the 4 up panels of the tile held in cur to slot `slot`.
 // The block's threads take the level's 4 sides x 2 lines x L elements in
 // order (element e: line e div L, position e mod L), so short lines at deep
-// levels or small tiles do not leave most lanes idle; 8-byte elements go out
-// in pairs, one 16-byte store each (L = n - 2k is even).
+// levels or small tiles do not leave most lanes idle; the elements go out in
+// pairs, one store each (L = n - 2k is even): 16 bytes for 8-byte elements.
 template <class S, int NV, class Tm = BlockTeam>
 __device__ __forceinline__ void write_up_panels(const S *cur, int P, const Geom &G, int k,
                                                 S *up, int slot) {
     const int n = G.n, L = n - 2 * k, plane = P * P;
     const int off = 2 * k * (n - k + 1);
     S *tile = up + (size_t)slot * 4 * NV * G.PS + off;
-    if constexpr (sizeof(S) == 8) {
+    if constexpr (pair_stores<S>()) {
         const int Lh = L >> 1;
         const float rh = recip_small(Lh);
         for (int e = Tm::rank(); e < 4 * L; e += Tm::size()) {
@@ -937,8 +954,8 @@ __device__ __forceinline__ void bridge_tile(const Op &op, const Geom &G, const t
         S *cur = bufs[k & 1];
         S *nxt = bufs[(k + 1) & 1];
         // bridge panels of level k (2 sides x 2 lines x L, threads in order;
-        // 8-byte elements in pairs, one 16-byte store each: L = 2k + 2 is even)
-        if constexpr (sizeof(S) == 8) {
+        // elements in pairs, one store each: L = 2k + 2 is even)
+        if constexpr (pair_stores<S>()) {
             const int L = 2 * k + 2, Lh = k + 1;
             const int off = 2 * k * (k + 1);
             const float rh = recip_small(Lh);
