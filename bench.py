@@ -377,13 +377,13 @@ def bridge_updates(n):
 # bytes there; part of the writes may still be in L2 when the kernel ends).
 # Kernels without a capture of their current version report None.
 OCT_TRAFFIC_PER_TILE = {
-    ("heat", "f64", 64): ((69.219072e6 + 27.767552e6) / 1024, 2048),
-    ("heat_kahan", "f32", 64): ((69.225728e6 + 21.248512e6) / 1024, 2048),
-    ("heat_kahan", "bf16", 64): ((34.620416e6 + 0.21504e6) / 1024, 2048),
-    ("euler_rk2", "f64", 32): ((570.50624e6 + 534.359296e6) / 4096, 2048),
-    ("euler_kahan", "f32", 32): ((427.944448e6 + 393.367296e6) / 4096, 2048),
-    ("euler_kahan", "bf16", 32): ((213.97376e6 + 162.021888e6) / 4096, 2048),
-    ("wave", "f64", 32): ((35.664896e6 + 2.827776e6) / 1024, 1024),
+    ("heat", "f64", 64): ((69.218e6 + 27.145e6) / 1024, 2048),
+    ("heat_kahan", "f32", 64): ((69.242e6 + 21.500e6) / 1024, 2048),
+    ("heat_kahan", "bf16", 64): ((34.620e6 + 0.181e6) / 1024, 2048),
+    ("euler_rk2", "f64", 32): ((570.552e6 + 533.881e6) / 4096, 2048),
+    ("euler_kahan", "f32", 32): ((428.327e6 + 394.044e6) / 4096, 2048),
+    ("euler_kahan", "bf16", 32): ((213.962e6 + 161.597e6) / 4096, 2048),
+    ("wave", "f64", 32): ((35.673e6 + 3.069e6) / 1024, 1024),
 }
 
 # Algorithmic work of one point update (one point advanced one sub-step),
