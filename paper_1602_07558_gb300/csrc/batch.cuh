@@ -124,8 +124,10 @@ struct ClassRuns {
 };
 
 // Threads of the one-launch kernel's blocks, and the team that runs one item
-// of a class with tile side n (0: the whole block): small tiles, whose levels
-// are short, run one per warp or two; the largest classes take the block.
+// of a class with tile side n (0: the whole block). Small tiles, whose levels
+// are short, run several per block: heat in binary32 / bfloat16 one warp per
+// tile-16 item and four per tile-32 item; the other updates two warps per
+// tile-16 item (their tile-16 slice is 4x larger). Larger tiles take the block.
 constexpr int kOneLaunchThreads = 256;
 template <class Op>
 __host__ __device__ constexpr int one_launch_team(int n) {
