@@ -452,13 +452,11 @@ __device__ __forceinline__ void heat_kahan_strip(const HeatKahanOp<SS> &op,
                       dst[plane + off + r * P]);
 }
 
-template <class Tm = BlockTeam, class SS>
-__device__ __forceinline__ void compute_rect(const HeatKahanOp<SS> &op, int, u64,
-                                             const SS *__restrict__ src, SS *__restrict__ dst,
-                                             SS *, int P, int x0, int y0, int W, int H) {
-    constexpr int R = 4;
+template <class Tm, int R, class SS>
+__device__ __forceinline__ void heat_kahan_rect(const HeatKahanOp<SS> &op,
+                                                const SS *__restrict__ src, SS *__restrict__ dst,
+                                                int P, int x0, int y0, int W, int H) {
     const int plane = P * P;
-    if (W <= 0 || H <= 0) return;
     const int nb = (H + R - 1) / R;
     for (LinearWalk w(W, (int)Tm::rank(), (int)Tm::size()); w.yy < nb; w.next(W)) {
         const int yb = w.yy * R;
@@ -469,6 +467,20 @@ __device__ __forceinline__ void compute_rect(const HeatKahanOp<SS> &op, int, u64
         else
             heat_kahan_strip<SS, R, false>(op, src, dst, P, plane, off, rows);
     }
+}
+// Strips of 4 points at tile 64, of 2 on smaller tiles, whose short levels
+// have fewer strips to share among the threads (measured: the 1,024-grid
+// batch at tiles 16 and 32 247 -> 262 G updates/s with strips of 2, the 2048²
+// grid at tile 64 421 -> 410 with strips of 2 and 379 with strips of 8).
+template <class Tm = BlockTeam, class SS>
+__device__ __forceinline__ void compute_rect(const HeatKahanOp<SS> &op, int, u64,
+                                             const SS *__restrict__ src, SS *__restrict__ dst,
+                                             SS *, int P, int x0, int y0, int W, int H) {
+    if (W <= 0 || H <= 0) return;
+    if (P > 34)
+        heat_kahan_rect<Tm, 4>(op, src, dst, P, x0, y0, W, H);
+    else
+        heat_kahan_rect<Tm, 2>(op, src, dst, P, x0, y0, W, H);
 }
 
 // Euler: the primitives (u, v, p, E + p) of every point of the rectangle grown
