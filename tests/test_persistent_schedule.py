@@ -6,7 +6,9 @@ an octahedron or final Down item). Random interleavings of concurrent items
 (each a start event, reads at any time while it runs, and an end event that
 writes and counts) must never let an item read a panel slot that is not the
 version it needs, nor let a writer overwrite a slot that a running item still
-reads.
+reads. The one-launch batch form is modelled too: several classes, each with
+its own items and counter, run by blocks of teams that take the classes in
+order and wait at a block barrier between classes.
 
 Items (the launch-per-phase schedule of Algorithm 4 on one GPU, as work items;
 panel slots are per tile and side group):
@@ -139,3 +141,96 @@ def test_a_smaller_neighbourhood_is_not_enough():
         done[(I, J)] += 1
         pending.remove(k)
     assert failures > 0
+
+
+# ---- the one-launch batch form: several classes, blocks of teams
+
+def run_one_launch_model(classes, blocks, teams, rng):
+    """classes: list of (T, Q, H). Every block takes the classes in order;
+    each of its teams takes the current class's items one at a time from the
+    class's counter, waits for the item's neighbourhood counts, runs it (start
+    and end events, reads checked against the versions the item needs), and
+    when the counter is past the class's last item waits at the block's
+    barrier; once all of a block's teams wait there, the block moves on to the
+    next class. Returns when every item of every class has ended; asserts that
+    some action is always possible (no deadlock)."""
+    cls = []
+    for (T, Q, H) in classes:
+        items = items_of(T, Q, H)
+        cls.append(dict(T=T, Q=Q, items=items, next=0,
+                        done={(I, J): 0 for J in range(Q) for I in range(T)}, version={}))
+    # team state: (block, team) -> ("fetch" | ("hold", k, started) | "barrier", class index)
+    state = {(b, t): ["fetch", 0] for b in range(blocks) for t in range(teams)}
+    running = {c: [] for c in range(len(cls))}   # items started, not ended
+    finished = 0
+    total = sum(len(c["items"]) for c in cls)
+    while finished < total:
+        actions = []
+        for key, (st, c) in state.items():
+            if c >= len(cls):
+                continue
+            C = cls[c]
+            if st == "fetch":
+                actions.append(("fetch", key))
+            elif st == "barrier":
+                b = key[0]
+                if all(state[(b, t)][0] == "barrier" and state[(b, t)][1] == c
+                       for t in range(teams)):
+                    actions.append(("release", key))
+            else:
+                _, k, started = st
+                p, I, J, reads, writes, need = C["items"][k]
+                if not started:
+                    if all(C["done"][((I + di) % C["T"], (J + dj) % C["Q"])] >= need
+                           for di in (-1, 0, 1) for dj in (-1, 0, 1)):
+                        actions.append(("start", key))
+                else:
+                    actions.append(("end", key))
+        assert actions, "deadlock"
+        what, key = rng.choice(actions)
+        st, c = state[key]
+        C = cls[c] if c < len(cls) else None
+        if what == "fetch":
+            if C["next"] < len(C["items"]):
+                state[key] = [("hold", C["next"], False), c]
+                C["next"] += 1
+            else:
+                state[key] = ["barrier", c]
+        elif what == "release":
+            b = key[0]
+            for t in range(teams):
+                state[(b, t)] = ["fetch", c + 1]
+        elif what == "start":
+            _, k, _ = st
+            p, I, J, reads, writes, need = C["items"][k]
+            for slot in reads:
+                assert C["version"].get(slot) == needed_version(p, slot[0]), (c, p, I, J, slot)
+            running[c].append(k)
+            state[key] = [("hold", k, True), c]
+        else:
+            _, k, _ = st
+            p, I, J, reads, writes, need = C["items"][k]
+            for slot in writes:
+                for r in running[c]:
+                    if r != k:
+                        assert slot not in C["items"][r][3], ("overwrite while read", c, p, slot)
+                C["version"][slot] = p
+            running[c].remove(k)
+            C["done"][(I, J)] += 1
+            finished += 1
+            state[key] = ["fetch", c]
+    return True
+
+
+@pytest.mark.parametrize("blocks,teams", [(1, 1), (1, 3), (2, 2), (3, 4)])
+def test_one_launch_classes_and_teams_never_deadlock_or_race(blocks, teams):
+    """Several tile classes (their own grids, half cycles and counters) run by
+    blocks of teams that wait at a block barrier between classes: every item
+    still sees the panel versions it needs, no writer overwrites a slot being
+    read, and the launch always finishes, even with a single team in a single
+    block."""
+    rng = random.Random(97 * blocks + teams)
+    for classes in ([(2, 2, 3), (3, 1, 2)], [(1, 1, 2), (2, 3, 1), (3, 3, 2)]):
+        for _ in range(15):
+            run_one_launch_model(classes, blocks, teams, rng)
+
