@@ -108,3 +108,13 @@ def test_secondary_lines_summarise_each_child_run(monkeypatch):
     good = [e for e in out if "error" not in e]
     assert good and all(e["value"] == 10.0 and e["speedup_vs_naive"] == 1.25 for e in good)
     assert good[0]["roofline"] == {"bound": "fp64", "frac": 0.5, "unit": "Gop/s", "traffic": None}
+
+
+def test_the_default_run_measures_every_workload():
+    """The headline plus the secondary list cover every workload the bench
+    defines, each batch in both of its forms."""
+    names = {n for n, _ in bench.SECONDARY} | {bench.DEFAULT_WORKLOAD}
+    assert names == set(bench.WORKLOADS)
+    batch_forms = [(n, a) for n, a in bench.SECONDARY if n.startswith("batch")]
+    for n in ("batch1024", "batch1024_euler"):
+        assert len([1 for m, _ in batch_forms if m == n]) == 2
