@@ -93,6 +93,35 @@ __host__ __device__ inline size_t aux_elems(int n, bool bridge) {
 struct SmemPlan {
     size_t stage_off, bar_off, total;
 };
+// The downward pyramid's staged panels in two parts: rings 0..k1-1, then
+// rings k1..h-1, brought in by a second bulk copy once the first part's rings
+// are in the level buffer, so the staging area holds the larger part, not the
+// whole panel set. k1 makes the parts most even among the levels whose ring
+// offset 2 k1 (k1 + 1) starts on 16 bytes; 0: one part (no such level).
+template <class S>
+__host__ __device__ inline int stage_split(int n) {
+    const int h = n / 2, ps = panel_stride(n);
+    int best = 0, best_span = ps;
+    for (int k = 1; k < h; ++k) {
+        const int off = 2 * k * (k + 1);
+        if ((off * (int)sizeof(S)) % 16) continue;
+        const int span = off > ps - off ? off : ps - off;
+        if (span < best_span) {
+            best = k;
+            best_span = span;
+        }
+    }
+    return best;
+}
+// Elements of one (side, plane) slot of the downward pyramid's staging area.
+template <class S>
+__host__ __device__ inline int stage_span(int n) {
+    const int k1 = stage_split<S>(n), ps = panel_stride(n);
+    if (!k1) return ps;
+    const int off = 2 * k1 * (k1 + 1);
+    return off > ps - off ? off : ps - off;
+}
+
 template <class Op>
 __host__ __device__ inline SmemPlan smem_plan(int n, int stage_segments, bool staged,
                                               bool bridge = false) {
@@ -102,9 +131,11 @@ __host__ __device__ inline SmemPlan smem_plan(int n, int stage_segments, bool st
                            (size_t)Op::AUX * aux_elems<Op>(n, bridge)) * sizeof(S);
     SmemPlan pl;
     pl.stage_off = (levels + 15) & ~(size_t)15;
-    const size_t stage = staged ? (size_t)stage_segments * Op::NV * panel_stride(n) * sizeof(S) : 0;
+    // the downward pyramid (4 segments) stages its panels in two parts
+    const size_t span = stage_segments == 4 ? (size_t)stage_span<S>(n) : (size_t)panel_stride(n);
+    const size_t stage = staged ? (size_t)stage_segments * Op::NV * span * sizeof(S) : 0;
     pl.bar_off = (pl.stage_off + stage + 7) & ~(size_t)7;
-    pl.total = pl.bar_off + (staged && stage_segments ? 8 : 0);
+    pl.total = pl.bar_off + (staged && stage_segments ? 16 : 0);   // two mbarriers
     return pl;
 }
 
@@ -158,6 +189,12 @@ struct SweptBounds {
 template <>
 struct SweptBounds<HeatOp> {
     static constexpr int kThreads = kMaxSweptThreads, kMinBlocks = 4;
+};
+// The compensated Euler kernels keep to 64 registers (two 512-thread blocks'
+// worth), so three 256-thread blocks per SM are never short of registers.
+template <class SS>
+struct SweptBounds<EulerKahanOp<SS>> {
+    static constexpr int kThreads = kMaxSweptThreads, kMinBlocks = 2;
 };
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) {
@@ -1051,19 +1088,33 @@ __device__ __forceinline__ bool down_body(const Op &op, const Geom &G, unsigned 
     const S *seg[4] = {br + ((size_t)slot * 4 + 3) * NV * G.PS, br + ((size_t)east * 4 + 2) * NV * G.PS,
                        br + ((size_t)slot * 4 + 1) * NV * G.PS, br + ((size_t)south * 4 + 0) * NV * G.PS};
     const S *stg = nullptr;
+    // staged panels: part 0 (rings 0..k1-1, or all of them) at block start,
+    // part 1 (rings k1..h-1) once part 0's last ring is in the level buffer
+    int k1 = 0, span = 0, base = 0;
+    unsigned long long *bar = nullptr;
+    S *st = nullptr;
+    auto stage_part = [&](int part) {   // called by the team's rank 0
+        const int lo = part ? 2 * k1 * (k1 + 1) : 0;
+        const int hi = (part || !k1) ? G.PS : 2 * k1 * (k1 + 1);
+        const unsigned bytes = (unsigned)((hi - lo) * sizeof(S));
+        mbar_expect_tx(bar + part, 4 * NV * bytes);
+        for (int side = 0; side < 4; ++side)
+            for (int v = 0; v < NV; ++v)
+                bulk_g2s(st + (side * NV + v) * span, seg[side] + (size_t)v * G.PS + lo, bytes,
+                         bar + part);
+    };
     if constexpr (STG) {
         const SmemPlan pl = smem_plan<Op>(n, 4, true);
-        S *st = reinterpret_cast<S *>(smem_raw + pl.stage_off);
-        unsigned long long *bar = reinterpret_cast<unsigned long long *>(smem_raw + pl.bar_off);
-        if (Tm::rank() == 0) mbar_init(bar, 1);
-        Tm::sync();
+        st = reinterpret_cast<S *>(smem_raw + pl.stage_off);
+        bar = reinterpret_cast<unsigned long long *>(smem_raw + pl.bar_off);
+        k1 = stage_split<S>(n);
+        span = stage_span<S>(n);
         if (Tm::rank() == 0) {
-            const unsigned bytes = (unsigned)(G.PS * sizeof(S));
-            mbar_expect_tx(bar, 4 * NV * bytes);
-            for (int side = 0; side < 4; ++side)
-                for (int v = 0; v < NV; ++v)
-                    bulk_g2s(st + (side * NV + v) * G.PS, seg[side] + (size_t)v * G.PS, bytes, bar);
+            mbar_init(bar, 1);
+            mbar_init(bar + 1, 1);
         }
+        Tm::sync();
+        if (Tm::rank() == 0) stage_part(0);
         if (!block_wait_bulk<Tm>(bar, err)) return false;
         if (Tm::rank() == 0) mbar_inval(bar);
         stg = st;
@@ -1085,9 +1136,9 @@ __device__ __forceinline__ bool down_body(const Op &op, const Geom &G, unsigned 
             }
             S *dd = dst + (by + 1 + p * ay) * P + (bx + 1 + p * ax);
             if constexpr (STG) {
-                const S *src = stg + side * NV * G.PS + off + d * L + p;
+                const S *src = stg + side * NV * span + (off - base) + d * L + p;
 #pragma unroll
-                for (int v = 0; v < NV; ++v) dd[v * plane] = src[v * G.PS];
+                for (int v = 0; v < NV; ++v) dd[v * plane] = src[v * span];
             } else {
                 const S *src = seg[side] + off + d * L + p;
 #pragma unroll
@@ -1101,8 +1152,32 @@ __device__ __forceinline__ bool down_body(const Op &op, const Geom &G, unsigned 
     // outside every earlier level's square and reads, so the copies' latency
     // is paid once per tile
     constexpr bool per_level = STG || one_buffer<Op>();
+    bool failed = false;
+    // staged in two parts: once ring r (the last of part 0) is copied, the
+    // staging area is free for part 1; ring k1 waits for part 1
+    auto after_ring = [&](int r) {
+        if constexpr (STG) {
+            if (k1 && r == k1 - 1) {
+                // this team's reads of the staging area come before the bulk
+                // copy that overwrites it (generic -> async proxy)
+                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                Tm::sync();
+                if (Tm::rank() == 0) stage_part(1);
+            }
+        }
+    };
+    auto before_ring = [&](int r) {
+        if constexpr (STG) {
+            if (k1 && r == k1) {
+                if (!block_wait_bulk<Tm>(bar + 1, err)) failed = true;
+                if (Tm::rank() == 0) mbar_inval(bar + 1);
+                base = 2 * k1 * (k1 + 1);
+            }
+        }
+    };
     if constexpr (per_level) {
         load_ring(0, buf0);
+        after_ring(0);
     } else {
         for (int k = 0; k < h; ++k) load_ring(k, (k & 1) ? buf1 : buf0);
     }
@@ -1117,13 +1192,18 @@ __device__ __forceinline__ bool down_body(const Op &op, const Geom &G, unsigned 
         // once those neighbours are read
         auto next = [&] {
             if constexpr (per_level)
-                if (k + 1 < h) load_ring(k + 1, nxt);
+                if (k + 1 < h) {
+                    before_ring(k + 1);
+                    load_ring(k + 1, nxt);
+                    after_ring(k + 1);
+                }
         };
         const u64 g = g0 + k;
         level_step<Tm>(op, (int)(g % Op::NST), g, cur, nxt, aux, P, h - k - 1, h - k - 1, 2 * k + 2,
                    2 * k + 2, next);
         if constexpr (per_level && !STG) async_wait();
         Tm::sync();
+        if (failed) return false;
     }
     return true;
 }
