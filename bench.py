@@ -379,10 +379,10 @@ def bridge_updates(n):
 OCT_TRAFFIC_PER_TILE = {
     ("heat", "f64", 64): ((69.218e6 + 27.145e6) / 1024, 2048),
     ("heat_kahan", "f32", 64): ((69.242e6 + 21.500e6) / 1024, 2048),
-    ("heat_kahan", "bf16", 64): ((34.620e6 + 0.181e6) / 1024, 2048),
+    ("heat_kahan", "bf16", 64): ((34.622e6 + 0.215e6) / 1024, 2048),
     ("euler_rk2", "f64", 32): ((570.552e6 + 533.881e6) / 4096, 2048),
     ("euler_kahan", "f32", 32): ((428.327e6 + 394.044e6) / 4096, 2048),
-    ("euler_kahan", "bf16", 32): ((213.962e6 + 161.597e6) / 4096, 2048),
+    ("euler_kahan", "bf16", 32): ((213.992e6 + 160.476e6) / 4096, 2048),
     ("wave", "f64", 32): ((35.673e6 + 3.069e6) / 1024, 1024),
 }
 
