@@ -17,6 +17,8 @@ against the squares and rectangles each level computes and reads.
   packed for its own rectangle; every level of a block fits the block's aux
   buffer, the second pass finds each neighbour's value where the first pass
   put it, and the flux pitch keeps a column-pair walk conflict-free.
+* Panel lines start on even elements (pair stores), and the downward
+  pyramid's two-part staging keeps every ring in one part with 16-byte copies.
 """
 import pytest
 
@@ -209,3 +211,44 @@ def test_panel_lines_of_8_byte_elements_start_on_16_bytes(n):
             for d in (0, 1):
                 start = off + d * L
                 assert start % 2 == 0 and start + L <= n * n // 2 + n
+
+
+def stage_split(n, esize):
+    """The downward pyramid's two-part staging, restated: the level k1 whose
+    ring offset 2 k1 (k1 + 1) starts on 16 bytes and makes the larger part
+    smallest (0: one part)."""
+    h, ps = n // 2, ((n * n // 2 + n) + 7) & ~7
+    best, best_span = 0, ps
+    for k in range(1, h):
+        off = 2 * k * (k + 1)
+        if (off * esize) % 16:
+            continue
+        span = max(off, ps - off)
+        if span < best_span:
+            best, best_span = k, span
+    return best, best_span, ps
+
+
+@pytest.mark.parametrize("n", [8, 16, 32, 64, 128])
+@pytest.mark.parametrize("esize", [2, 4, 8])
+def test_two_part_staging_keeps_rings_whole_and_copies_aligned(n, esize):
+    """Each ring lies wholly in one part; both parts start on 16 bytes and
+    their byte counts are multiples of 16 (bulk copies); each fits the
+    staging slot; and every part-1 ring is read at an offset within it."""
+    h = n // 2
+    k1, span, ps = stage_split(n, esize)
+    assert (span * esize) % 16 == 0 and span <= ps
+    if not k1:
+        return
+    cut = 2 * k1 * (k1 + 1)
+    assert (cut * esize) % 16 == 0 and ((ps - cut) * esize) % 16 == 0
+    assert cut <= span and ps - cut <= span
+    for k in range(h):
+        off, L = 2 * k * (k + 1), 2 * k + 2
+        lo, hi = off, off + 2 * L                 # the ring's two lines
+        if k < k1:
+            assert hi <= cut
+        else:
+            assert lo >= cut and hi - cut <= span
+    # the staging area is smaller than the whole panel set
+    assert span < ps
