@@ -216,8 +216,10 @@ int swept2d_query(const swept2d_t *h, int what, double *out);
  * of results: every setting gives the same bits). threads: 32, 64, 128, 256 or 512
  * per block (default 256; the persistent form also takes up to 512; the bridge
  * launches of the launch-per-phase form take at most 256). stage: 1 =
- * the bridge and downward-pyramid blocks bring their whole input panel set
- * into shared memory with TMA bulk copies at block start; 0 = they copy every
+ * the bridge and downward-pyramid blocks bring their input panel set into
+ * shared memory with TMA bulk copies (a bridge's at block start, a downward
+ * pyramid's in two parts, the second once the first part's levels have taken
+ * their rings); 0 = they copy every
  * level's strip or ring from device memory straight into its level buffer with
  * cp.async at block start (default: 1 for HEAT_KAHAN with BF16 storage, 0
  * otherwise, and 0 wherever the staged panels do not fit).
